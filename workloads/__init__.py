@@ -1,0 +1,194 @@
+"""Seeded synthetic workloads: planted low-multilinear-rank tensors plus noise.
+
+This module only *draws inputs*. It holds none of the ALS method's arithmetic
+and is shared, read-only, by the FP64 oracle tests, the GPU parity tests and
+the benchmark, so that both sides of every comparison see identical values.
+
+Recipe (stands in for the paper's synthetic experiments, Sec. 6.1, and for
+the workloads the benchmark times):
+
+* factors ``U_n`` (``I_n x R_n``): Haar-random orthonormal columns -- the Q
+  factor of a Gaussian matrix with column signs fixed so that ``diag(R) > 0``
+  (Mezzadri 2007, "How to generate random matrices from the classical compact
+  groups");
+* core ``C`` (``R_1 x ... x R_N``), one of
+    - ``"gauss"``: i.i.d. N(0, 1);
+    - ``"inv_k"``: Gaussian ``Z`` scaled by ``1/k`` along every mode
+      (``Z x_n diag(1, 1/2, ..., 1/R_n)``), a ``1/k`` mode spectrum;
+    - ``"ratio"``: Gaussian ``Z`` scaled by ``rho^(k-1)`` along every mode;
+    - ``"uniform510"``: i.i.d. U[5, 10], the core of the paper's Tucker-model
+      experiment (Sec. 6.1.2);
+* base ``A0 = C x_1 U_1 x_2 ... x_N U_N`` (the Tucker model, Sec. 2);
+* noise ``E`` i.i.d. N(0, 1), rescaled so that ``||E||_F = nu * ||A0||_F``
+  (relative Frobenius noise);
+* ``A = A0 + E``, cast to the requested dtype. Consumers that need FP64 read
+  ``float64(A)`` so that every side sees the same numbers.
+
+Seeds follow ``2004025830 + cfg`` for the named configurations.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Sequence
+
+import numpy as np
+
+SEED_BASE = 2004025830
+
+
+def _haar(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    g = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(g)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s
+
+
+def _apply_along(x: np.ndarray, mat: np.ndarray, axis: int) -> np.ndarray:
+    # y[..., a, ...] = sum_b mat[a, b] x[..., b, ...]; generator-only helper.
+    y = np.tensordot(mat, x, axes=([1], [axis]))
+    return np.moveaxis(y, 0, axis)
+
+
+def _core(rng: np.random.Generator, ranks: Sequence[int], kind: str,
+          ratio: float) -> np.ndarray:
+    if kind == "uniform510":
+        return rng.uniform(5.0, 10.0, size=tuple(ranks))
+    z = rng.standard_normal(tuple(ranks))
+    if kind == "gauss":
+        return z
+    for n, r in enumerate(ranks):
+        k = np.arange(1, r + 1, dtype=np.float64)
+        if kind == "inv_k":
+            d = 1.0 / k
+        elif kind == "ratio":
+            d = ratio ** (k - 1.0)
+        else:
+            raise ValueError(f"unknown core kind {kind!r}")
+        shape = [1] * len(ranks)
+        shape[n] = r
+        z = z * d.reshape(shape)
+    return z
+
+
+@dataclasses.dataclass
+class Planted:
+    A: np.ndarray            # the input tensor, in the requested dtype
+    A0: np.ndarray           # noiseless base (float64 or float32 for big ones)
+    core: np.ndarray
+    factors: List[np.ndarray]
+    noise_rel: float
+    seed: int
+
+
+def planted(seed: int, dims: Sequence[int], ranks: Sequence[int],
+            core: str = "gauss", noise_rel: float = 1e-2,
+            dtype=np.float32, ratio: float = 0.8,
+            work_dtype=None) -> Planted:
+    """Planted rank-(R_1..R_N) tensor plus relative Gaussian noise.
+
+    ``work_dtype`` is the precision the base tensor and the noise are built in
+    (float64 by default; float32 keeps memory down for the multi-GB shapes).
+    """
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    if len(dims) != len(ranks):
+        raise ValueError("dims and ranks differ in length")
+    if work_dtype is None:
+        work_dtype = np.float64 if int(np.prod(dims)) <= (1 << 26) else np.float32
+    rng = np.random.Generator(np.random.PCG64(seed))
+    factors = [_haar(rng, d, r) for d, r in zip(dims, ranks)]
+    c = _core(rng, ranks, core, ratio)
+    a0 = c.astype(work_dtype)
+    for n, u in enumerate(factors):
+        a0 = _apply_along(a0, u.astype(work_dtype), n)
+    a0 = np.ascontiguousarray(a0, dtype=work_dtype)
+    if noise_rel > 0:
+        e = rng.standard_normal(a0.shape, dtype=np.float32 if work_dtype == np.float32
+                                else np.float64)
+        scale = noise_rel * np.sqrt(np.sum(a0.astype(np.float64) ** 2)) / \
+            np.sqrt(np.sum(e.astype(np.float64) ** 2))
+        e *= scale
+        a = a0 + e.astype(work_dtype)
+        del e
+    else:
+        a = a0.copy()
+    return Planted(A=np.ascontiguousarray(a, dtype=dtype), A0=a0, core=c,
+                   factors=factors, noise_rel=noise_rel, seed=seed)
+
+
+def uniform_tensor(seed: int, dims: Sequence[int], dtype=np.float32) -> np.ndarray:
+    """Plain U[-1, 1) tensor (gradient and projection tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-1.0, 1.0, size=tuple(dims)).astype(dtype)
+
+
+def orthonormal(seed: int, rows: int, cols: int, dtype=np.float32) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return _haar(rng, rows, cols).astype(dtype)
+
+
+# ---------------------------------------------------------------------------
+# Named configurations (the five workloads of the benchmark/parity suite)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    name: str
+    dims: tuple
+    ranks: tuple
+    core: str
+    noise_rel: float
+    eta: float
+    dtype: str        # "f64" or "f32"
+    seed: int
+
+
+CONFIGS = {
+    # 64^3 FP64, multilinear rank (8,8,8), Gaussian core, 1e-3 noise, eta 1e-8
+    "st64_f64": Config("st64_f64", (64, 64, 64), (8, 8, 8), "gauss", 1e-3, 1e-8,
+                       "f64", SEED_BASE + 0),
+    # 512^3 FP32, rank (32,32,32), 1/k core spectrum, 1e-2 noise, eta 1e-6
+    "c512_f32": Config("c512_f32", (512, 512, 512), (32, 32, 32), "inv_k", 1e-2,
+                       1e-6, "f32", SEED_BASE + 1),
+    # 128^4 FP32, rank (16,16,16,16), 0.8^k spectrum, 1e-3 noise
+    "q128_f32": Config("q128_f32", (128, 128, 128, 128), (16, 16, 16, 16), "ratio",
+                       1e-3, 1e-6, "f32", SEED_BASE + 2),
+    # 1024x1024x512 FP32, rank (64,64,32), 1/k spectrum, 1e-2 noise
+    "d1024_f32": Config("d1024_f32", (1024, 1024, 512), (64, 64, 32), "inv_k", 1e-2,
+                        1e-6, "f32", SEED_BASE + 4),
+}
+
+
+def make(cfg: Config, **kw) -> Planted:
+    dt = np.float64 if cfg.dtype == "f64" else np.float32
+    return planted(cfg.seed, cfg.dims, cfg.ranks, cfg.core, cfg.noise_rel, dtype=dt, **kw)
+
+
+def batched_shapes(seed: int, count: int, lo: int = 16, hi: int = 96,
+                   rlo: int = 4, rhi: int = 16):
+    """Uneven third-order shapes and ranks for the batched workload.
+
+    Mode sizes ~ U{lo..hi}, ranks ~ U{rlo..rhi} clipped to the mode size and to
+    the product of the other ranks (so every sequential truncation is feasible).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        dims = [int(x) for x in rng.integers(lo, hi + 1, size=3)]
+        ranks = [int(min(x, d)) for x, d in zip(rng.integers(rlo, rhi + 1, size=3), dims)]
+        for n in range(3):
+            other = int(np.prod([ranks[m] for m in range(3) if m != n]))
+            ranks[n] = min(ranks[n], other)
+        out.append((tuple(dims), tuple(ranks)))
+    return out
+
+
+def batched(seed: int, count: int, noise_rel: float = 1e-2, **kw):
+    """List of (A float32, dims, ranks) for the batched workload."""
+    shapes = batched_shapes(seed, count, **kw)
+    res = []
+    for t, (dims, ranks) in enumerate(shapes):
+        p = planted(seed * 7919 + t, dims, ranks, "gauss", noise_rel, dtype=np.float32)
+        res.append((p.A, dims, ranks))
+    return res
