@@ -1,0 +1,321 @@
+"""Benchmark: st-HOSVD-ALS time-to-tolerance on the 512^3 FP32 workload.
+
+Workload: 512 x 512 x 512 FP32 tensor (512 MiB) of multilinear rank (32,32,32)
+with a 1/k core spectrum, Haar factors and 1e-2 relative Gaussian noise;
+st-HOSVD-ALS to eta = 1e-6 (at most 50 sweeps per mode). One step = one full
+decomposition (all modes: initial guess, ALS sweeps until the stop rule, the
+truncations) -- one graph launch through the C ABI. The input (512 MiB) is
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (see the keys below). Under torchrun each rank runs an
+independent replica on its own GPU (weak scaling, no collective on the data
+path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at equal error"
+DIMS = (512, 512, 512)
+RANKS = (32, 32, 32)
+ETA = 1e-6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_oracle_run(a64, ranks, eta):
+    from oracle import tucker_oracle as O
+    t0 = time.perf_counter()
+    res = O.st_hosvd_als(a64, ranks, eta=eta, seed=1)
+    return time.perf_counter() - t0, res
+
+
+def _cpu_sample(budget_s: float = 20.0):
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    recipe at 512 x 512 x S with S chosen so one run takes about budget_s."""
+    import numpy as np
+    import workloads as W
+    cores = len(os.sched_getaffinity(0))
+    # probe on a small slab, then scale the slab to the budget (time ~ linear in S)
+    s = 32
+    p = W.planted(W.SEED_BASE + 1, (512, 512, s), RANKS, "inv_k", 1e-2, dtype=np.float32)
+    dt, _ = _cpu_oracle_run(p.A.astype(np.float64), RANKS, ETA)
+    s2 = int(max(32, min(512, s * budget_s / max(dt, 1e-3))))
+    s2 = max(32, (s2 // 32) * 32)
+    p = W.planted(W.SEED_BASE + 1, (512, 512, s2), RANKS, "inv_k", 1e-2, dtype=np.float32)
+    dt2, res = _cpu_oracle_run(p.A.astype(np.float64), RANKS, ETA)
+    frac = s2 / 512.0
+    # decompositions of the full workload per second, scaled by the sample's share
+    value = frac / dt2
+    return {"value": value, "unit": "st-HOSVD/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 NumPy oracle st-HOSVD-ALS on a 512x512x{s2} slab of the same recipe "
+                      f"({dt2:.1f} s), scaled by {s2}/512 to the full tensor",
+            "seconds": dt2}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: bounded samples on the host cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads as W
+    cores = len(os.sched_getaffinity(0))
+    s = 64
+    p = W.planted(W.SEED_BASE + 1, (512, 512, s), RANKS, "inv_k", 1e-2, dtype=np.float32)
+    a64 = p.A.astype(np.float64)
+    for _ in range(args.warmup):
+        _cpu_oracle_run(a64, RANKS, ETA)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = _cpu_oracle_run(a64, RANKS, ETA)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = (s / 512.0) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "st-HOSVD/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3 * 512.0 / s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
+                                   "1e-2 noise eta 1e-6", "sample": f"512x512x{s} slab"},
+            "cpu_baseline": {"value": value, "unit": "st-HOSVD/s", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle on a 512x512x{s} slab per step, scaled "
+                                       f"by {s}/512"},
+            "e2e": {"value": value, "unit": "st-HOSVD/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tals", choices=["tals", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="native", choices=["native", "mixed_bf16"])
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--dims", default=None, help="override tensor sizes (profiling), e.g. 512,512,256")
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="only launch the mode-1 sweep pass twice (for an ncu capture)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    global DIMS
+    if args.dims:
+        DIMS = tuple(int(x) for x in args.dims.split(","))
+
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+
+    cfg = W.CONFIGS["c512_f32"]
+    p = W.planted(cfg.seed, DIMS, RANKS, cfg.core, cfg.noise_rel, dtype=np.float32)
+    A = torch.from_numpy(p.A).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=args.precision)
+    if args.profile_pass:
+        ms_, by_, fl_ = ctx.time_pass(mode=0, iters=1)
+        print(json.dumps({"profile_pass_ms": ms_, "bytes": by_, "flops": fl_}))
+        ctx.close()
+        return
+    G = torch.empty(RANKS, device="cuda")
+    Us = [torch.empty((d, r), device="cuda") for d, r in zip(DIMS, RANKS)]
+
+    for _ in range(max(3, args.warmup)):
+        _, _, st = ctx.st_hosvd(G, Us)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweeps_total = 0
+    for _ in range(args.steps):
+        _, _, st = ctx.st_hosvd(G, Us)
+        sweeps_total += sum(st["sweeps"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else {}
+
+    # dominant kernel: the mode-1 sweep pass over the full tensor, timed with CUDA
+    # events on the stream it is launched on, same configuration as inside the step
+    pass_ms, pass_bytes, pass_flops = ctx.time_pass(mode=st["order"][0], iters=10)
+
+    # end to end through the C ABI with host buffers (H2D of A, D2H of G and U)
+    e_ms, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        hctx = tals.HostContext(DIMS, RANKS, "f32", eta=ETA, seed=1, precision=args.precision)
+        A_h = torch.from_numpy(p.A).pin_memory()
+        G_h = torch.empty(RANKS).pin_memory()
+        U_h = [torch.empty((d, r)).pin_memory() for d, r in zip(DIMS, RANKS)]
+        for _ in range(2):
+            hctx.st_hosvd(A_h, G_h, U_h)
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        e_steps = max(3, args.steps // 2)
+        for _ in range(e_steps):
+            hctx.st_hosvd(A_h, G_h, U_h)
+        e_ms = (time.perf_counter() - e0) * 1e3 / e_steps
+        h2d = A_h.numel() * 4
+        d2h = G_h.numel() * 4 + sum(u.numel() * 4 for u in U_h)
+        hctx.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    # the pass runs on CUDA cores: 152 SMs x 128 FP32 FMA x 2 flops x SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak_tflops = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
+    achieved_tflops = pass_flops / (pass_ms * 1e-3) / 1e12
+    bound_alu = achieved_tflops / alu_peak_tflops > achieved_gbs / hbm
+    roofline = {
+        "bound": "alu" if bound_alu else "hbm",
+        "achieved": round(achieved_tflops if bound_alu else achieved_gbs, 2),
+        "peak": round(alu_peak_tflops if bound_alu else hbm, 2),
+        "unit": "TFLOP/s" if bound_alu else "GB/s",
+        "frac": round((achieved_tflops / alu_peak_tflops) if bound_alu else (achieved_gbs / hbm), 4),
+        "traffic": None,
+        "kernel": "tals::pass_kernel<float,32,4,16> (sweep, mode-1 view 1 x 512 x 262144)",
+        "hbm_gbs_achieved": round(achieved_gbs, 1),
+        "hbm_frac": round(achieved_gbs / hbm, 4),
+        "pass_ms": round(pass_ms, 4),
+        "peak_source": f"{peak_kind} (HBM {hbm} GB/s; FP32 FMA peak from SM count x clock)",
+    }
+    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep
+    launches = sum(10 + 9 * s for s in st["sweeps"])
+    value = world * 1e3 / ms
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "st-HOSVD/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "native" else "bf16+f32", "data": "synthetic",
+        "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
+                               "1e-2 noise eta 1e-6", "precision": args.precision,
+                   "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
+                   "rel_err": st["rel_err"], "l2": "inputs (512 MiB) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "e2e": None if e_ms is None else
+               {"value": round(world * 1e3 / e_ms, 3), "unit": "st-HOSVD/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 3)},
+        "gpu_launches": launches * args.steps,
+        "launches_per_step": launches,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                   "reasons": clk.get("reasons", [])},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = _cpu_sample()
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

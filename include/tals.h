@@ -1,0 +1,212 @@
+/*
+ * tals.h -- C ABI of the GB300 (sm_103a) library for ALS-based truncated HOSVD.
+ *
+ * Method: Xiao, Yang, Li, "Efficient Alternating Least Squares Algorithms for
+ * Low Multilinear Rank Approximation of Tensors" (arXiv 2004.02583).
+ *   - Alg. 3  matrix ALS  R_k = (A^T L_k)(L_k^T L_k)^-1,  L_{k+1} = (A R_k)(R_k^T R_k)^-1
+ *   - Alg. 4  t-HOSVD-ALS (ALS per mode on A_(n), QR of L, core projection)
+ *   - Alg. 5  st-HOSVD-ALS (ALS on B_(n), QR, B_(n) <- R^ R^T, G <- last B)
+ *   - Sec. 4  initial guess  L_0 = Q of QR(A_(n) S), S uniform on [0,1)
+ *   - Eq. 5.01 stop rule  | e_k - e_{k+1} | <= eta ||A||_F,  at most 50 sweeps (Sec. 6)
+ *   - Sec. 2  mode-n unfolding, mode-n product, Tucker model
+ *
+ * Conventions shared by every entry point
+ *   Tensors are dense, contiguous, row-major (C order): element (i_1..i_N) of a
+ *   tensor with sizes (I_1..I_N) sits at offset ((i_1*I_2 + i_2)*I_3 + ...) + i_N.
+ *   The mode-n unfolding column index j is the row-major linear index over the
+ *   remaining modes in logical order (the paper writes the Fortran order; the
+ *   two differ only by a column permutation, which no result depends on except
+ *   the seeded random initial sketch S).
+ *   Factor matrices U^(n) are I_n x R_n row-major: U[i*R_n + r].
+ *   dtype: TALS_F64 (double) or TALS_F32 (float); one dtype per call for the
+ *   tensor, the core and the factors.
+ *   All data pointers are DEVICE pointers unless an entry point says "host".
+ *   The library never writes the input tensor and never keeps a pointer to a
+ *   caller buffer beyond the call (tucker_als_init keeps A until tals_destroy:
+ *   the caller keeps A alive and unmodified until then).
+ *   `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream. All device work of a call is enqueued on that stream. Calls that
+ *   return statistics synchronise the stream once at their end.
+ *   Errors: every call returns a tals_status; TALS_EINVAL for bad arguments
+ *   (checked on the host before any launch), TALS_ECUDA for a CUDA runtime
+ *   error, TALS_ESINGULAR when an R x R Gram matrix is not numerically positive
+ *   definite (the truncation exceeds the numerical rank, Remark 3), TALS_ENOTSUP
+ *   for shapes outside the kernels' limits. tals_last_error() returns a
+ *   thread-local message for the last failure. Not converging within
+ *   max_sweeps is TALS_OK with converged[n] = 0.
+ */
+#ifndef TALS_H
+#define TALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TALS_MAX_NDIM 8
+
+typedef enum {
+  TALS_OK = 0,
+  TALS_EINVAL = 1,
+  TALS_ENOMEM = 2,
+  TALS_ECUDA = 3,
+  TALS_ESINGULAR = 4,
+  TALS_ETIMEOUT = 5,
+  TALS_ENOTSUP = 6
+} tals_status;
+
+typedef enum { TALS_F64 = 0, TALS_F32 = 1 } tals_dtype;
+
+/* Arithmetic of the unfolding products.
+ *   TALS_PREC_NATIVE      products in the tensor dtype on CUDA cores (FP32 or FP64).
+ *   TALS_PREC_MIXED_BF16  F32 tensors only: bulk sweeps read a BF16 shadow copy of
+ *                         the tensor and run on tcgen05 tensor cores (BF16 operands,
+ *                         FP32 accumulation); finishing sweeps run in FP32 on the
+ *                         original tensor until the stop rule fires.
+ * In every mode the Grams, Cholesky factorisations, QR and norms are FP64. */
+typedef enum { TALS_PREC_NATIVE = 0, TALS_PREC_MIXED_BF16 = 1 } tals_precision;
+
+typedef struct {
+  double eta;            /* Eq. 5.01 tolerance; default 1e-4 (Sec. 6). eta < 0: never stop early */
+  int max_sweeps;        /* ALS iterations (R-updates) per mode; default 50 (Sec. 6) */
+  uint64_t seed;         /* seed of the initial sketch S (Sec. 4) */
+  int has_order;         /* 1: use order[] for st-HOSVD; 0: ascending R_n, ties by n (Prop. 1) */
+  int order[TALS_MAX_NDIM];
+  int precision;         /* tals_precision */
+  int bulk_sweeps;       /* mixed precision: most BF16 sweeps per mode (default 8) */
+  int use_graph;         /* 1 (default): run each mode's sweep loop as one CUDA graph whose
+                            device-side while-node evaluates the stop rule; 0: host loop */
+} tals_opts;
+
+typedef struct {
+  double rel_err;                       /* ||A - G x U||_F / ||A||_F (see st_hosvd/t_hosvd) */
+  double norm_a;                        /* ||A||_F */
+  double err_per_mode[TALS_MAX_NDIM];   /* e_n = ||B_(n) - L R^T||_F at the returned pair */
+  int sweeps[TALS_MAX_NDIM];            /* R-updates performed on mode n (all precisions) */
+  int bulk_sweeps[TALS_MAX_NDIM];       /* of which BF16 bulk sweeps */
+  int converged[TALS_MAX_NDIM];         /* 1 if Eq. 5.01 fired before max_sweeps */
+  int order[TALS_MAX_NDIM];             /* processing order used */
+  int status;                           /* worst per-mode status */
+} tals_stats;
+
+typedef struct tals_ctx tals_ctx;
+
+/* Fills *o with the defaults above. */
+void tals_default_opts(tals_opts* o);
+
+/* Create a context for tensor A (device, dtype, ndim <= 8, dims[ndim] >= 1) with
+ * truncation ranks[ndim]. Validates on the host: 1 <= R_n <= I_n and
+ * R_n <= prod_{m != n} R_m (so every sequential truncation is feasible).
+ * Allocates all workspace on `stream` (stream-ordered) and builds nothing else;
+ * the context owns its workspace and frees it in tals_destroy. A must stay
+ * alive and unmodified for the lifetime of the context. */
+tals_status tucker_als_init(tals_ctx** ctx, const void* A, int dtype, int ndim,
+                            const int64_t* dims, const int* ranks, const tals_opts* opts,
+                            void* stream);
+
+/* The user-drivable unit of Alg. 3: run up to max_iters ALS sweeps on the mode-n
+ * unfolding of the context's current tensor (A for t-HOSVD, the partially
+ * truncated B for st-HOSVD). The first call on a mode draws S and forms the
+ * initial guess (Sec. 4); later calls continue from the stored iterate. Each
+ * sweep reads the tensor once: with Q_k the orthonormal basis of L_k it forms
+ * W = B_(n)^T Q_k and Y = B_(n) W in one pass (Eq. 2.2), e_k from
+ * ||B_(n)||^2 - ||W||^2, and L_{k+1} = Y (Q_k^T Y)^-1 re-orthonormalised by
+ * CholeskyQR, which leaves the iterates of Alg. 3 unchanged up to an R x R
+ * triangular factor. Returns the current e_k in *err_out and whether the stop
+ * rule (Eq. 5.01) has fired in *converged_out (either may be NULL). Synchronises
+ * the stream. */
+tals_status als_mode_sweep(tals_ctx* ctx, int mode, int max_iters, double* err_out,
+                           int* converged_out);
+
+/* Finish a mode driven by als_mode_sweep: write U^(n) (I_n x R_n, device) and, if
+ * truncate != 0, replace the context's current tensor by B x_n U^(n)T taken from
+ * the last sweep's W (Alg. 5, B_(n) <- R^ R^T; no extra pass over B). */
+tals_status als_mode_finish(tals_ctx* ctx, int mode, void* U_out, int truncate);
+
+/* st-HOSVD-ALS (Alg. 5) of the context's tensor. G_out: device buffer of
+ * prod R_n elements (row-major R_1 x ... x R_N). U_out[n]: device buffers of
+ * I_n x R_n. st (host, may be NULL) receives the statistics; rel_err is
+ * sqrt(sum_n e_n^2) / ||A|| (the st-HOSVD error is the sum of the mode-wise
+ * truncation errors, Lemma 2). May be called repeatedly on one context. */
+tals_status st_hosvd(tals_ctx* ctx, void* G_out, void* const* U_out, tals_stats* st);
+
+/* t-HOSVD-ALS (Alg. 4): every mode on A, then G = A x_1 U1^T ... x_N UN^T. The first
+ * projection is the last mode's W (no extra pass), the rest run on shrinking
+ * tensors. rel_err = sqrt(||A||^2 - ||G||^2) / ||A||. */
+tals_status t_hosvd(tals_ctx* ctx, void* G_out, void* const* U_out, tals_stats* st);
+
+/* Same as st_hosvd, with HOST buffers: copies A (host, dtype, dims as in the
+ * context) to the device, runs st-HOSVD-ALS and copies G and U^(n) back to the
+ * host buffers. The context's own device copy of A is used as the tensor; the
+ * context must have been created with A == NULL (see tucker_als_init_owned). */
+tals_status st_hosvd_host(tals_ctx* ctx, const void* A_host, void* G_host,
+                          void* const* U_host, tals_stats* st);
+
+/* Like tucker_als_init but the context allocates and owns a device buffer for A
+ * (to be filled by st_hosvd_host or by copying into tals_ctx_tensor()). */
+tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int64_t* dims,
+                                  const int* ranks, const tals_opts* opts, void* stream);
+
+/* Device pointer of the tensor the context reads (A, or its owned buffer). */
+void* tals_ctx_tensor(tals_ctx* ctx);
+
+/* Tucker reconstruction (Sec. 2): B = G x_1 U1 x_2 U2 ... x_N UN.
+ * G: device, prod R_n elements; U[n]: device I_n x R_n; B_out: device prod I_n.
+ * Intermediate mode products are formed in stream-ordered scratch. */
+tals_status reconstruct(const void* G, void* const* U, int dtype, int ndim,
+                        const int64_t* dims, const int* ranks, void* B_out, void* stream);
+
+/* Core projection G = A x_1 U1^T ... x_N UN^T (Alg. 1/4 core step). */
+tals_status project(const void* A, void* const* U, int dtype, int ndim, const int64_t* dims,
+                    const int* ranks, void* G_out, void* stream);
+
+/* Adjoint of reconstruct: given B_bar (device, prod I_n), write
+ * G_bar = B_bar x_1 U1^T ... x_N UN^T and U_bar[n] = (B_bar x_{m!=n} Um^T)_(n) G_(n)^T.
+ * The partial contractions are recomputed per mode, never stored for all n.
+ * Any U_bar[n] may be NULL (skipped). */
+tals_status reconstruct_backward(const void* G, void* const* U, const void* B_bar, int dtype,
+                                 int ndim, const int64_t* dims, const int* ranks,
+                                 void* G_bar, void* const* U_bar, void* stream);
+
+/* Adjoint of project: given G_bar, write A_bar = G_bar x_1 U1 ... x_N UN (may be
+ * NULL) and U_bar[n] = (A x_{m!=n} Um^T)_(n) G_bar_(n)^T (any may be NULL). */
+tals_status project_backward(const void* A, void* const* U, const void* G_bar, int dtype,
+                             int ndim, const int64_t* dims, const int* ranks, void* A_bar,
+                             void* const* U_bar, void* stream);
+
+/* Batched st-HOSVD-ALS over `count` independent third-order FP32 tensors of
+ * uneven sizes. A_ptrs/G_ptrs/U_ptrs are HOST arrays of DEVICE pointers
+ * (U_ptrs has 3*count entries: tensor t's factors at 3t, 3t+1, 3t+2); dims and
+ * ranks are host arrays of 3*count entries. One persistent kernel (captured in
+ * a CUDA graph on first use) processes all tensors; each CTA takes whole
+ * tensors from an atomic queue, so no CTA ever waits on another. stats (host,
+ * may be NULL) receives count entries. Limits: I_n <= 128, R_n <= 16. */
+tals_status tals_batched_st_hosvd(int count, void* const* A_ptrs, const int64_t* dims,
+                                  const int* ranks, const tals_opts* opts, void* const* G_ptrs,
+                                  void* const* U_ptrs, tals_stats* stats, void* stream);
+
+/* Measurement hook (no counterpart in the paper): launch the sweep pass of `mode`
+ * (one read of the context's tensor A viewed as its mode-`mode` unfolding, with
+ * the context's current factor buffer and W written) `iters` times on the
+ * context's stream between two CUDA events recorded on that stream. Returns the
+ * mean duration in *ms, and the pass's algorithmic bytes (tensor read + W write)
+ * and flops (4 R_n prod(I)) per launch. Synchronises the stream. */
+tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, double* bytes,
+                           double* flops);
+
+/* Free a context (its workspace, graphs and owned buffers). NULL is allowed. */
+void tals_destroy(tals_ctx* ctx);
+
+/* Thread-local message describing the last non-OK status. */
+const char* tals_last_error(void);
+
+/* Library version string. */
+const char* tals_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TALS_H */

@@ -1,0 +1,444 @@
+"""Python binding of libtals: ALS-based truncated HOSVD (t-/st-HOSVD-ALS) on GB300.
+
+This module only marshals arguments to the C ABI declared in ``include/tals.h``
+(same names): every step of the computation runs in the library's CUDA kernels.
+There is no CPU fallback -- importing works anywhere, but every call raises if
+``libtals.so`` has not been built or no CUDA device is present.
+
+Tensors are torch CUDA tensors, contiguous, row-major, float32 or float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtals.so")
+MAX_NDIM = 8
+
+TALS_OK, TALS_EINVAL, TALS_ENOMEM, TALS_ECUDA, TALS_ESINGULAR, TALS_ETIMEOUT, TALS_ENOTSUP = range(7)
+TALS_F64, TALS_F32 = 0, 1
+PREC_NATIVE, PREC_MIXED_BF16 = 0, 1
+_STATUS_NAMES = {0: "TALS_OK", 1: "TALS_EINVAL", 2: "TALS_ENOMEM", 3: "TALS_ECUDA",
+                 4: "TALS_ESINGULAR", 5: "TALS_ETIMEOUT", 6: "TALS_ENOTSUP"}
+
+
+class TalsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tals_opts(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("max_sweeps", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("has_order", ctypes.c_int),
+                ("order", ctypes.c_int * MAX_NDIM), ("precision", ctypes.c_int),
+                ("bulk_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class tals_stats(ctypes.Structure):
+    _fields_ = [("rel_err", ctypes.c_double), ("norm_a", ctypes.c_double),
+                ("err_per_mode", ctypes.c_double * MAX_NDIM),
+                ("sweeps", ctypes.c_int * MAX_NDIM), ("bulk_sweeps", ctypes.c_int * MAX_NDIM),
+                ("converged", ctypes.c_int * MAX_NDIM), ("order", ctypes.c_int * MAX_NDIM),
+                ("status", ctypes.c_int)]
+
+    def to_dict(self, ndim: int) -> dict:
+        return {"rel_err": self.rel_err, "norm_a": self.norm_a,
+                "err_per_mode": list(self.err_per_mode[:ndim]),
+                "sweeps": list(self.sweeps[:ndim]),
+                "bulk_sweeps": list(self.bulk_sweeps[:ndim]),
+                "converged": [bool(x) for x in self.converged[:ndim]],
+                "order": list(self.order[:ndim]), "status": self.status}
+
+
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_IP = ctypes.POINTER(ctypes.c_int)
+_VPP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); mirrors include/tals.h
+SIGNATURES = {
+    "tals_default_opts": (None, [ctypes.POINTER(tals_opts)]),
+    "tucker_als_init": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, ctypes.c_int, ctypes.c_int,
+                                       _I64P, _IP, ctypes.POINTER(tals_opts), _VP]),
+    "tucker_als_init_owned": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
+                                             _I64P, _IP, ctypes.POINTER(tals_opts), _VP]),
+    "tals_ctx_tensor": (_VP, [_VP]),
+    "als_mode_sweep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), _IP]),
+    "als_mode_finish": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "st_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
+    "t_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
+    "st_hosvd_host": (ctypes.c_int, [_VP, _VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
+    "reconstruct": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
+    "project": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
+    "reconstruct_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P,
+                                            _IP, _VP, _VPP, _VP]),
+    "project_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P, _IP,
+                                        _VP, _VPP, _VP]),
+    "tals_batched_st_hosvd": (ctypes.c_int, [ctypes.c_int, _VPP, _I64P, _IP,
+                                             ctypes.POINTER(tals_opts), _VPP, _VPP,
+                                             ctypes.POINTER(tals_stats), _VP]),
+    "tals_time_pass": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "tals_destroy": (None, [_VP]),
+    "tals_last_error": (ctypes.c_char_p, []),
+    "tals_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libtals.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                f"g.build()\"`. There is no CPU fallback.")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int):
+    if status != TALS_OK:
+        msg = lib().tals_last_error()
+        raise TalsError(status, msg.decode() if msg else "")
+
+
+def default_opts(**kw) -> tals_opts:
+    o = tals_opts()
+    lib().tals_default_opts(ctypes.byref(o))
+    order = kw.pop("order", None)
+    if order is not None:
+        o.has_order = 1
+        for i, n in enumerate(order):
+            o.order[i] = int(n)
+    prec = kw.pop("precision", None)
+    if prec is not None:
+        o.precision = {"native": PREC_NATIVE, "mixed_bf16": PREC_MIXED_BF16}.get(prec, prec)
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return TALS_F32
+    if t.dtype == torch.float64:
+        return TALS_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors (no CPU fallback)")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptrs(ts) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Context:
+    """A tals context over a CUDA tensor A (kept alive by this object)."""
+
+    def __init__(self, A, ranks: Sequence[int], eta: float = 1e-4, max_sweeps: int = 50,
+                 seed: int = 0, order: Optional[Sequence[int]] = None,
+                 precision="native", bulk_sweeps: Optional[int] = None,
+                 use_graph: bool = True, stream=None):
+        _require_cuda(A)
+        self.A = A
+        self.ndim = A.dim()
+        self.dims = [int(d) for d in A.shape]
+        self.ranks = [int(r) for r in ranks]
+        self.dtype = A.dtype
+        self._code = _dtype_code(A)
+        self._stream = stream
+        o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed),
+                         order=order, precision=precision, bulk_sweeps=bulk_sweeps,
+                         use_graph=int(bool(use_graph)))
+        self._opts = o
+        dims = (ctypes.c_int64 * self.ndim)(*self.dims)
+        rk = (ctypes.c_int * self.ndim)(*self.ranks)
+        h = ctypes.c_void_p()
+        _check(lib().tucker_als_init(ctypes.byref(h), A.data_ptr(), self._code, self.ndim, dims,
+                                     rk, ctypes.byref(o), _stream_ptr(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outputs(self, G=None, Us=None):
+        torch = _torch()
+        if G is None:
+            G = torch.empty(self.ranks, dtype=self.dtype, device=self.A.device)
+        if Us is None:
+            Us = [torch.empty((d, r), dtype=self.dtype, device=self.A.device)
+                  for d, r in zip(self.dims, self.ranks)]
+        _require_cuda(G, *Us)
+        return G, Us
+
+    def st_hosvd(self, G=None, Us=None):
+        """st-HOSVD-ALS (Alg. 5). Returns (G, [U_n], stats)."""
+        G, Us = self._outputs(G, Us)
+        st = tals_stats()
+        _check(lib().st_hosvd(self._h, G.data_ptr(), _ptrs(Us), ctypes.byref(st)))
+        return G, Us, st.to_dict(self.ndim)
+
+    def t_hosvd(self, G=None, Us=None):
+        """t-HOSVD-ALS (Alg. 4). Returns (G, [U_n], stats)."""
+        G, Us = self._outputs(G, Us)
+        st = tals_stats()
+        _check(lib().t_hosvd(self._h, G.data_ptr(), _ptrs(Us), ctypes.byref(st)))
+        return G, Us, st.to_dict(self.ndim)
+
+    def mode_sweep(self, mode: int, max_iters: int):
+        err = ctypes.c_double()
+        conv = ctypes.c_int()
+        _check(lib().als_mode_sweep(self._h, int(mode), int(max_iters), ctypes.byref(err),
+                                    ctypes.byref(conv)))
+        return err.value, bool(conv.value)
+
+    def mode_finish(self, mode: int, truncate: bool = True, U=None):
+        torch = _torch()
+        if U is None:
+            U = torch.empty((self.dims[mode], self.ranks[mode]), dtype=self.dtype,
+                            device=self.A.device)
+        _check(lib().als_mode_finish(self._h, int(mode), U.data_ptr(), int(bool(truncate))))
+        return U
+
+
+    def time_pass(self, mode: int = 0, iters: int = 10):
+        """Mean duration (ms), algorithmic bytes and flops of one sweep pass."""
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().tals_time_pass(self._h, int(mode), int(iters), ctypes.byref(ms),
+                                    ctypes.byref(by), ctypes.byref(fl)))
+        return ms.value, by.value, fl.value
+
+
+def st_hosvd(A, ranks, **kw):
+    ctx = Context(A, ranks, **kw)
+    try:
+        return ctx.st_hosvd()
+    finally:
+        ctx.close()
+
+
+def t_hosvd(A, ranks, **kw):
+    ctx = Context(A, ranks, **kw)
+    try:
+        return ctx.t_hosvd()
+    finally:
+        ctx.close()
+
+
+class HostContext:
+    """Context owning its device tensor; st_hosvd() takes and returns host arrays
+    (the end-to-end path: host->device copy, decomposition, device->host copies)."""
+
+    def __init__(self, dims, ranks, dtype="f32", eta=1e-4, max_sweeps=50, seed=0,
+                 precision="native", use_graph=True, stream=None):
+        self.ndim = len(dims)
+        self.dims = [int(d) for d in dims]
+        self.ranks = [int(r) for r in ranks]
+        self._code = TALS_F32 if dtype in ("f32", "float32") else TALS_F64
+        o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed),
+                         precision=precision, use_graph=int(bool(use_graph)))
+        d = (ctypes.c_int64 * self.ndim)(*self.dims)
+        rk = (ctypes.c_int * self.ndim)(*self.ranks)
+        h = ctypes.c_void_p()
+        _check(lib().tucker_als_init_owned(ctypes.byref(h), self._code, self.ndim, d, rk,
+                                           ctypes.byref(o), _stream_ptr(stream)))
+        self._h = h
+
+    def st_hosvd(self, A_host, G_host, U_host):
+        """A_host, G_host, U_host: pinned (or pageable) host torch tensors."""
+        st = tals_stats()
+        _check(lib().st_hosvd_host(self._h, A_host.data_ptr(), G_host.data_ptr(),
+                                   _ptrs(U_host), ctypes.byref(st)))
+        return st.to_dict(self.ndim)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _op_args(X, Us):
+    _require_cuda(X, *Us)
+    ndim = len(Us)
+    dims = (ctypes.c_int64 * ndim)(*[int(u.shape[0]) for u in Us])
+    ranks = (ctypes.c_int * ndim)(*[int(u.shape[1]) for u in Us])
+    return ndim, dims, ranks
+
+
+def project(A, Us, out=None, stream=None):
+    """G = A x_1 U1^T ... x_N UN^T (the core projection of Alg. 1/4)."""
+    torch = _torch()
+    ndim, dims, ranks = _op_args(A, Us)
+    G = out if out is not None else torch.empty([int(u.shape[1]) for u in Us], dtype=A.dtype,
+                                                 device=A.device)
+    _check(lib().project(A.data_ptr(), _ptrs(Us), _dtype_code(A), ndim, dims, ranks,
+                         G.data_ptr(), _stream_ptr(stream)))
+    return G
+
+
+def reconstruct(G, Us, out=None, stream=None):
+    """B = G x_1 U1 ... x_N UN (Tucker model)."""
+    torch = _torch()
+    ndim, dims, ranks = _op_args(G, Us)
+    B = out if out is not None else torch.empty([int(u.shape[0]) for u in Us], dtype=G.dtype,
+                                                 device=G.device)
+    _check(lib().reconstruct(G.data_ptr(), _ptrs(Us), _dtype_code(G), ndim, dims, ranks,
+                             B.data_ptr(), _stream_ptr(stream)))
+    return B
+
+
+def reconstruct_backward(G, Us, B_bar, need_g=True, need_u=True, stream=None):
+    """(G_bar, [U_bar_n]) of B = reconstruct(G, Us) for the output gradient B_bar."""
+    torch = _torch()
+    ndim, dims, ranks = _op_args(B_bar, Us)
+    _require_cuda(G)
+    G_bar = torch.empty_like(G) if need_g else None
+    U_bar = [torch.empty_like(u) for u in Us] if need_u else [None] * ndim
+    _check(lib().reconstruct_backward(G.data_ptr(), _ptrs(Us), B_bar.data_ptr(), _dtype_code(G),
+                                      ndim, dims, ranks, G_bar.data_ptr() if need_g else None,
+                                      _ptrs(U_bar), _stream_ptr(stream)))
+    return G_bar, U_bar
+
+
+def project_backward(A, Us, G_bar, need_a=True, need_u=True, stream=None):
+    """(A_bar, [U_bar_n]) of G = project(A, Us) for the output gradient G_bar."""
+    torch = _torch()
+    ndim, dims, ranks = _op_args(A, Us)
+    _require_cuda(G_bar)
+    A_bar = torch.empty_like(A) if need_a else None
+    U_bar = [torch.empty_like(u) for u in Us] if need_u else [None] * ndim
+    _check(lib().project_backward(A.data_ptr(), _ptrs(Us), G_bar.data_ptr(), _dtype_code(A),
+                                  ndim, dims, ranks, A_bar.data_ptr() if need_a else None,
+                                  _ptrs(U_bar), _stream_ptr(stream)))
+    return A_bar, U_bar
+
+
+def _autograd():
+    torch = _torch()
+
+    class TalsProject(torch.autograd.Function):
+        """G = A x_1 U1^T ... x_N UN^T with hand-written backward kernels."""
+
+        @staticmethod
+        def forward(ctx, A, *Us):
+            Us = [u.contiguous() for u in Us]
+            ctx.save_for_backward(A, *Us)
+            return project(A.contiguous(), Us)
+
+        @staticmethod
+        def backward(ctx, G_bar):
+            A, *Us = ctx.saved_tensors
+            need_a = ctx.needs_input_grad[0]
+            need_u = any(ctx.needs_input_grad[1:])
+            A_bar, U_bar = project_backward(A, Us, G_bar.contiguous(), need_a, need_u)
+            return (A_bar, *U_bar)
+
+    class TalsReconstruct(torch.autograd.Function):
+        """B = G x_1 U1 ... x_N UN with hand-written backward kernels."""
+
+        @staticmethod
+        def forward(ctx, G, *Us):
+            Us = [u.contiguous() for u in Us]
+            ctx.save_for_backward(G, *Us)
+            return reconstruct(G.contiguous(), Us)
+
+        @staticmethod
+        def backward(ctx, B_bar):
+            G, *Us = ctx.saved_tensors
+            need_g = ctx.needs_input_grad[0]
+            need_u = any(ctx.needs_input_grad[1:])
+            G_bar, U_bar = reconstruct_backward(G, Us, B_bar.contiguous(), need_g, need_u)
+            return (G_bar, *U_bar)
+
+    return TalsProject, TalsReconstruct
+
+
+def tucker_project(A, Us):
+    """Differentiable core projection (autograd.Function over the C ABI)."""
+    return _autograd()[0].apply(A, *Us)
+
+
+def tucker_reconstruct(G, Us):
+    """Differentiable Tucker reconstruction (autograd.Function over the C ABI)."""
+    return _autograd()[1].apply(G, *Us)
+
+
+def batched_st_hosvd(As, ranks, eta=1e-4, max_sweeps=50, seed=0, stream=None):
+    """st-HOSVD-ALS of many small third-order FP32 CUDA tensors in one persistent,
+    graph-captured launch. ranks: list of 3-tuples. Returns (Gs, Us, stats)."""
+    torch = _torch()
+    count = len(As)
+    if len(ranks) != count:
+        raise ValueError("one rank triple per tensor")
+    for a in As:
+        _require_cuda(a)
+        if a.dtype != torch.float32 or a.dim() != 3:
+            raise ValueError("batched tensors are third-order float32")
+    Gs = [torch.empty(tuple(r), dtype=torch.float32, device=a.device) for a, r in zip(As, ranks)]
+    Us = [torch.empty((int(a.shape[n]), int(r[n])), dtype=torch.float32, device=a.device)
+          for a, r in zip(As, ranks) for n in range(3)]
+    dims = (ctypes.c_int64 * (3 * count))(*[int(d) for a in As for d in a.shape])
+    rk = (ctypes.c_int * (3 * count))(*[int(x) for r in ranks for x in r])
+    o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed))
+    stats = (tals_stats * max(count, 1))()
+    _check(lib().tals_batched_st_hosvd(count, _ptrs(As), dims, rk, ctypes.byref(o), _ptrs(Gs),
+                                       _ptrs(Us), stats, _stream_ptr(stream)))
+    return Gs, [Us[3 * t:3 * t + 3] for t in range(count)], [stats[t].to_dict(3) for t in range(count)]
+
+
+def version() -> str:
+    return lib().tals_version().decode()

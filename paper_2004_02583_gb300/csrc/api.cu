@@ -1,0 +1,678 @@
+// C ABI of the tals library: contexts, validation, the per-mode ALS driver
+// (Alg. 3 with the Sec. 4 initial guess and the Eq. 5.01 stop rule), and the
+// st-HOSVD-ALS (Alg. 5) and t-HOSVD-ALS (Alg. 4) drivers.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tals.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "internal.h"
+
+using namespace tals;
+
+namespace {
+thread_local std::string g_err;
+}
+
+namespace tals {
+
+tals_status fail(tals_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+tals_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(TALS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+ModeView view_of(const long long* dims, int N, int n) {
+  ModeView v;
+  v.P = 1;
+  v.Q = 1;
+  for (int m = 0; m < n; ++m) v.P *= dims[m];
+  for (int m = n + 1; m < N; ++m) v.Q *= dims[m];
+  v.I = dims[n];
+  return v;
+}
+
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+}  // namespace tals
+
+// ---------------------------------------------------------------------------
+// Workspace planning
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Need {
+  size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0;
+  void add_mode(int dtype, const ModeView& v, int R, int sms, bool sweep) {
+    PassConfig pc = pass_config(dtype, v, R, sms);
+    if (!pc.ok) return;
+    if (sweep) ypart = std::max(ypart, (size_t)pc.grid_x * (size_t)v.I * (size_t)R);
+    spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
+    RowPlan rp = row_plan(v.I, R, sms);
+    gpart = std::max(gpart, (size_t)rp.blocks * (size_t)R * (size_t)R);
+    ir = std::max(ir, (size_t)v.I * (size_t)R);
+  }
+};
+
+std::vector<int> default_order(const int* ranks, int N) {
+  std::vector<int> o(N);
+  for (int i = 0; i < N; ++i) o[i] = i;
+  std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return ranks[a] < ranks[b]; });
+  return o;
+}
+
+}  // namespace
+
+namespace tals {
+
+tals_status ctx_plan_and_alloc(tals_ctx* c) {
+  const int N = c->N;
+  Need need;
+  // st-HOSVD shapes (in the context's order)
+  {
+    long long d[TALS_MAX_NDIM];
+    for (int m = 0; m < N; ++m) d[m] = c->dims[m];
+    for (int idx = 0; idx < N; ++idx) {
+      const int n = c->order[idx];
+      ModeView v = view_of(d, N, n);
+      PassConfig pc = pass_config(c->dtype, v, c->ranks[n], c->sms);
+      if (!pc.ok)
+        return fail(TALS_ENOTSUP, "mode %d: size %lld with rank %d exceeds the pass kernel limits",
+                    n, v.I, c->ranks[n]);
+      need.add_mode(c->dtype, v, c->ranks[n], c->sms, true);
+      if (idx < N - 1) need.tbuf = std::max(need.tbuf, (size_t)(v.J() * c->ranks[n]));
+      d[n] = c->ranks[n];
+    }
+  }
+  // t-HOSVD shapes: every mode on A, then projections on shrinking tensors
+  {
+    long long d[TALS_MAX_NDIM];
+    for (int m = 0; m < N; ++m) d[m] = c->dims[m];
+    for (int n = 0; n < N; ++n) {
+      ModeView v = view_of(d, N, n);
+      PassConfig pc = pass_config(c->dtype, v, c->ranks[n], c->sms);
+      if (!pc.ok)
+        return fail(TALS_ENOTSUP, "mode %d: size %lld with rank %d exceeds the pass kernel limits",
+                    n, v.I, c->ranks[n]);
+      need.add_mode(c->dtype, v, c->ranks[n], c->sms, true);
+    }
+    ModeView v = view_of(d, N, N - 1);
+    need.tbuf = std::max(need.tbuf, (size_t)(v.J() * c->ranks[N - 1]));
+    d[N - 1] = c->ranks[N - 1];
+    for (int m = 0; m < N - 1; ++m) {
+      ModeView w = view_of(d, N, m);
+      PassConfig pc = pass_config(c->dtype, w, c->ranks[m], c->sms);
+      if (!pc.ok) return fail(TALS_ENOTSUP, "projection of mode %d exceeds the kernel limits", m);
+      need.add_mode(c->dtype, w, c->ranks[m], c->sms, false);
+      need.tbuf = std::max(need.tbuf, (size_t)(w.J() * c->ranks[m]));
+      d[m] = c->ranks[m];
+    }
+  }
+  const size_t esz = c->esz;
+  cudaStream_t s = c->stream;
+  auto al = [&](void** p, size_t bytes) -> cudaError_t {
+    return cudaMallocAsync(p, std::max<size_t>(bytes, 256), s);
+  };
+  cudaError_t e;
+#define TALS_AL(ptr, bytes)                                                        \
+  if ((e = al((void**)&(ptr), (bytes))) != cudaSuccess) {                          \
+    return cuda_fail(e, "workspace allocation");                                   \
+  }
+  TALS_AL(c->tbuf[0], need.tbuf * esz);
+  TALS_AL(c->tbuf[1], need.tbuf * esz);
+  TALS_AL(c->Ypart, need.ypart * esz);
+  TALS_AL(c->spart, need.spart * sizeof(double));
+  TALS_AL(c->Gpart, need.gpart * sizeof(double));
+  TALS_AL(c->GpartL, need.gpart * sizeof(double));
+  int rmax = 1;
+  for (int m = 0; m < N; ++m) rmax = std::max(rmax, c->ranks[m]);
+  TALS_AL(c->Gfin, (size_t)rmax * rmax * sizeof(double));
+  TALS_AL(c->F, (size_t)rmax * rmax * sizeof(double));
+  TALS_AL(c->GfinL, (size_t)rmax * rmax * sizeof(double));
+  TALS_AL(c->Y64, need.ir * sizeof(double));
+  TALS_AL(c->L64, need.ir * sizeof(double));
+  TALS_AL(c->Z64, need.ir * sizeof(double));
+  TALS_AL(c->Lt, need.ir * esz);
+  if ((e = cudaMemsetAsync(c->Lt, 0, need.ir * esz, s)) != cudaSuccess)
+    return cuda_fail(e, "workspace clear");
+  TALS_AL(c->st, (size_t)TALS_MAX_NDIM * sizeof(ModeState));
+  TALS_AL(c->norm_a2, 8 * sizeof(double));
+#undef TALS_AL
+  if ((e = cudaMallocHost((void**)&c->st_host, TALS_MAX_NDIM * sizeof(ModeState))) != cudaSuccess)
+    return cuda_fail(e, "pinned state buffer");
+  if ((e = cudaMallocHost((void**)&c->host_d, (need.spart + 16) * sizeof(double))) != cudaSuccess)
+    return cuda_fail(e, "pinned scratch");
+  c->host_d_n = need.spart + 16;
+  c->need_ir = need.ir;
+  return TALS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-mode ALS (Alg. 3) on a given tensor view
+// ---------------------------------------------------------------------------
+
+tals_status mode_setup(tals_ctx* c, ModeJob& j) {
+  j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
+  if (!j.pc.ok) return fail(TALS_ENOTSUP, "pass kernel limits exceeded (I=%lld R=%d)", j.v.I, j.R);
+  j.rp = row_plan(j.v.I, j.R, c->sms);
+  j.st = c->st + j.n;
+  // FP32: on tensors up to a quarter of the input (and at least 16M elements) the
+  // sweeps measure e_k from the residual ||B - Q W^T||^2 directly; ||B||^2 - ||W||^2
+  // cancels too many FP32 digits there (small e on small tensors). Costs one more
+  // rank-R product per element on those small tensors only.
+  long long tot = 1;
+  for (int m = 0; m < c->N; ++m) tot *= c->dims[m];
+  const long long mine = j.v.P * j.v.I * j.v.Q;
+  j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 &&
+            mine <= std::max(tot / 4, 16LL << 20);
+  return TALS_OK;
+}
+
+uint64_t sketch_state(uint64_t seed, int mode) {
+  return seed ^ ((uint64_t)mode << 56);
+}
+
+tals_status mode_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
+  cudaStream_t s = c->stream;
+  const int R = j.R;
+  const long long I = j.v.I;
+  cudaError_t e;
+#define TALS_CK(x)                                   \
+  if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
+  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s));
+  // Sec. 4: Y0 = B_(n) S and ||B_(n)||^2 in one pass
+  TALS_CK(launch_pass(c->dtype, j.pc, PASS_INIT, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr,
+                      sketch_state(c->opts.seed, j.n), j.st, 1 << 30, s));
+  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, j.pc.grid_x, I, R, c->Y64, 1, nullptr, c->Gpart,
+                             j.rp, c->spart, j.pc.grid_x * j.pc.grid_y, 0, j.st,
+                             set_norm_a ? c->norm_a2 : nullptr, s));
+  // L0 = Q of QR(Y0) by CholeskyQR2 (two rounds; Y0 can be ill-conditioned)
+  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
+  TALS_CK(launch_small(c->Gfin, 1, R, 0, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s));
+  TALS_CK(launch_row_solve(c->dtype, c->Y64, I, R, c->F, 0, c->Z64, nullptr, c->Gpart, j.rp, j.st, s));
+  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
+  TALS_CK(launch_small(c->Gfin, 1, R, 0, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s));
+  TALS_CK(launch_row_solve(c->dtype, c->Z64, I, R, c->F, 0, c->L64, c->Lt, c->GpartL, j.rp, j.st, s,
+                           1));
+  TALS_CK(launch_gram_sum(c->GpartL, j.rp.blocks, R, c->GfinL, j.st, s));
+  return TALS_OK;
+}
+
+tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
+  cudaStream_t s = c->stream;
+  const int R = j.R;
+  const long long I = j.v.I;
+  cudaError_t e;
+  // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
+  TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
+                      j.Wdest, 0, j.st, 1, s, nullptr, j.resid));
+  // Y (FP64), X = Q_k^T Y partials, ||W||^2
+  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, j.pc.grid_x, I, R, c->Y64, 2, c->L64, c->Gpart,
+                             j.rp, c->spart, j.pc.grid_x * j.pc.grid_y, 1, j.st, nullptr, s));
+  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
+  // e_k, Eq. 5.01, and chol(X) if the sweep continues
+  TALS_CK(launch_small(c->Gfin, 1, R, 1, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s, c->GfinL));
+  // L_{k+1} = Y X^{-1} (Alg. 3 L-update in the Q_k basis), then its Q factor
+  TALS_CK(launch_row_solve(c->dtype, c->Y64, I, R, c->F, 1, c->Z64, nullptr, c->Gpart, j.rp, j.st, s));
+  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
+  TALS_CK(launch_small(c->Gfin, 1, R, 0, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s));
+  TALS_CK(launch_row_solve(c->dtype, c->Z64, I, R, c->F, 0, c->L64, c->Lt, c->GpartL, j.rp, j.st, s,
+                           1));
+  TALS_CK(launch_gram_sum(c->GpartL, j.rp.blocks, R, c->GfinL, j.st, s));
+#undef TALS_CK
+  return TALS_OK;
+}
+
+tals_status read_states(tals_ctx* c) {
+  cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, TALS_MAX_NDIM * sizeof(ModeState),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "state readback");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return TALS_OK;
+}
+
+// Run the sweep loop of a mode until its state says done (host-driven).
+tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters) {
+  int launched = 0;
+  tals_status st;
+  // the stop rule can fire first after the second sweep: launch two before checking
+  const int first = std::min(2, max_iters);
+  for (; launched < first; ++launched)
+    if ((st = mode_sweep_launch(c, j)) != TALS_OK) return st;
+  while (true) {
+    if ((st = read_states(c)) != TALS_OK) return st;
+    const ModeState& ms = c->st_host[j.n];
+    if (ms.done || launched >= max_iters) break;
+    if ((st = mode_sweep_launch(c, j)) != TALS_OK) return st;
+    ++launched;
+  }
+  return TALS_OK;
+}
+
+tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a) {
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
+  return mode_loop_host(c, j, c->opts.max_sweeps);
+}
+
+tals_status mode_status(tals_ctx* c, int n) {
+  const ModeState& ms = c->st_host[n];
+  if (ms.status != 0)
+    return fail((tals_status)ms.status,
+                "mode %d: Gram matrix not positive definite at %s (truncation above the "
+                "numerical rank, Remark 3)",
+                n, ms.fail_stage == 1 ? "the R-update" : "the QR step");
+  return TALS_OK;
+}
+
+}  // namespace tals
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void tals_default_opts(tals_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eta = 1e-4;
+  o->max_sweeps = 50;
+  o->seed = 0;
+  o->has_order = 0;
+  o->precision = TALS_PREC_NATIVE;
+  o->bulk_sweeps = 8;
+  o->use_graph = 1;
+}
+
+const char* tals_last_error(void) { return g_err.c_str(); }
+
+const char* tals_version(void) { return "tals 0.1 (sm_103a)"; }
+
+static tals_status validate(int dtype, int ndim, const int64_t* dims, const int* ranks) {
+  if (dtype != TALS_F32 && dtype != TALS_F64) return fail(TALS_EINVAL, "unsupported dtype %d", dtype);
+  if (ndim < 2 || ndim > TALS_MAX_NDIM) return fail(TALS_EINVAL, "ndim %d outside [2, 8]", ndim);
+  if (!dims || !ranks) return fail(TALS_EINVAL, "dims/ranks must not be NULL");
+  for (int n = 0; n < ndim; ++n) {
+    if (dims[n] < 1) return fail(TALS_EINVAL, "dims[%d] = %lld < 1", n, (long long)dims[n]);
+    if (ranks[n] < 1 || ranks[n] > dims[n])
+      return fail(TALS_EINVAL, "ranks[%d] = %d outside [1, I_n = %lld]", n, ranks[n],
+                  (long long)dims[n]);
+    long long other = 1;
+    for (int m = 0; m < ndim; ++m)
+      if (m != n) other *= ranks[m];
+    if (ranks[n] > other)
+      return fail(TALS_EINVAL, "ranks[%d] = %d exceeds the product of the other ranks (%lld)", n,
+                  ranks[n], other);
+  }
+  return TALS_OK;
+}
+
+static tals_status ctx_create(tals_ctx** out, const void* A, bool owned, int dtype, int ndim,
+                              const int64_t* dims, const int* ranks, const tals_opts* opts,
+                              void* stream) {
+  if (!out) return fail(TALS_EINVAL, "ctx must not be NULL");
+  *out = nullptr;
+  tals_status st = validate(dtype, ndim, dims, ranks);
+  if (st != TALS_OK) return st;
+  if (!owned && !A) return fail(TALS_EINVAL, "A must not be NULL");
+  tals_ctx* c = new tals_ctx();
+  c->dtype = dtype;
+  c->esz = dtype == TALS_F32 ? 4 : 8;
+  c->N = ndim;
+  for (int n = 0; n < ndim; ++n) {
+    c->dims[n] = dims[n];
+    c->ranks[n] = ranks[n];
+  }
+  if (opts) c->opts = *opts; else tals_default_opts(&c->opts);
+  if (c->opts.max_sweeps < 1) {
+    delete c;
+    return fail(TALS_EINVAL, "max_sweeps must be >= 1");
+  }
+  if (c->opts.precision == TALS_PREC_MIXED_BF16 && dtype != TALS_F32) {
+    delete c;
+    return fail(TALS_EINVAL, "mixed BF16 precision needs an FP32 tensor");
+  }
+  std::vector<int> ord;
+  if (c->opts.has_order) {
+    std::vector<int> seen(ndim, 0);
+    for (int i = 0; i < ndim; ++i) {
+      const int n = c->opts.order[i];
+      if (n < 0 || n >= ndim || seen[n]) {
+        delete c;
+        return fail(TALS_EINVAL, "order is not a permutation of 0..%d", ndim - 1);
+      }
+      seen[n] = 1;
+      ord.push_back(n);
+    }
+  } else {
+    ord = default_order(ranks, ndim);
+  }
+  for (int i = 0; i < ndim; ++i) c->order[i] = ord[i];
+  c->stream = (cudaStream_t)stream;
+  c->sms = device_sms();
+  if (c->sms <= 0) {
+    delete c;
+    return fail(TALS_ECUDA, "no CUDA device available");
+  }
+  st = ctx_plan_and_alloc(c);
+  if (st == TALS_OK && owned) {
+    size_t n = 1;
+    for (int m = 0; m < ndim; ++m) n *= (size_t)dims[m];
+    cudaError_t e = cudaMallocAsync(&c->A_owned, n * c->esz, c->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "tensor allocation");
+    c->A = c->A_owned;
+  } else {
+    c->A = A;
+  }
+  if (st == TALS_OK && c->opts.precision == TALS_PREC_MIXED_BF16) st = mixed_alloc(c);
+  if (st != TALS_OK) {
+    tals_destroy(c);
+    return st;
+  }
+  *out = c;
+  return TALS_OK;
+}
+
+tals_status tucker_als_init(tals_ctx** ctx, const void* A, int dtype, int ndim,
+                            const int64_t* dims, const int* ranks, const tals_opts* opts,
+                            void* stream) {
+  return ctx_create(ctx, A, false, dtype, ndim, dims, ranks, opts, stream);
+}
+
+tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int64_t* dims,
+                                  const int* ranks, const tals_opts* opts, void* stream) {
+  return ctx_create(ctx, nullptr, true, dtype, ndim, dims, ranks, opts, stream);
+}
+
+void* tals_ctx_tensor(tals_ctx* ctx) { return ctx ? const_cast<void*>(ctx->A) : nullptr; }
+
+void tals_destroy(tals_ctx* c) {
+  if (!c) return;
+  cudaStream_t s = c->stream;
+  graphs_destroy(c);
+  mixed_free(c);
+  void* bufs[] = {c->GpartL, c->GfinL, c->tbuf[0], c->tbuf[1], c->Ypart, c->spart, c->Gpart, c->Gfin, c->F,
+                  c->Y64,     c->L64,     c->Z64,   c->Lt,    c->st,    c->norm_a2, c->A_owned};
+  for (void* p : bufs)
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->host_d) cudaFreeHost(c->host_d);
+  delete c;
+}
+
+// Copy the current orthonormal factor Q (dtype) of a finished mode to U_out.
+static tals_status emit_factor(tals_ctx* c, const ModeJob& j, void* U_out) {
+  if (!U_out) return TALS_OK;
+  cudaError_t e = cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "factor copy");
+}
+
+static void fill_mode_stats(tals_ctx* c, int n, tals_stats* st) {
+  if (!st) return;
+  const ModeState& ms = c->st_host[n];
+  st->err_per_mode[n] = ms.e_cur;
+  st->sweeps[n] = ms.k;
+  st->bulk_sweeps[n] = ms.bulk;
+  st->converged[n] = ms.converged;
+  if (ms.status && !st->status) st->status = ms.status;
+}
+
+tals_status st_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* stats) {
+  if (!c || !G_out) return fail(TALS_EINVAL, "ctx and G_out must not be NULL");
+  if (c->opts.use_graph && c->opts.precision == TALS_PREC_NATIVE)
+    return st_hosvd_graph(c, G_out, U_out, stats);
+  const int N = c->N;
+  long long d[TALS_MAX_NDIM];
+  for (int m = 0; m < N; ++m) d[m] = c->dims[m];
+  const void* cur = c->A;
+  tals_stats local;
+  std::memset(&local, 0, sizeof(local));
+  tals_status st;
+  for (int idx = 0; idx < N; ++idx) {
+    const int n = c->order[idx];
+    ModeJob j;
+    j.n = n;
+    j.v = view_of(d, N, n);
+    j.R = c->ranks[n];
+    j.X = cur;
+    j.Wdest = (idx == N - 1) ? G_out : c->tbuf[idx & 1];
+    if (c->opts.precision == TALS_PREC_MIXED_BF16)
+      st = run_mode_mixed(c, j, idx == 0);
+    else
+      st = run_mode(c, j, idx == 0);
+    if (st != TALS_OK) return st;
+    if ((st = read_states(c)) != TALS_OK) return st;
+    if ((st = mode_status(c, n)) != TALS_OK) return st;
+    if (U_out && (st = emit_factor(c, j, U_out[n])) != TALS_OK) return st;
+    fill_mode_stats(c, n, &local);
+    cur = j.Wdest;
+    d[n] = c->ranks[n];
+  }
+  double na2 = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&c->host_d[0], c->norm_a2, sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "readback");
+  na2 = c->host_d[0];
+  double err2 = 0.0;
+  for (int n = 0; n < N; ++n) err2 += local.err_per_mode[n] * local.err_per_mode[n];
+  local.norm_a = std::sqrt(na2);
+  local.rel_err = na2 > 0 ? std::sqrt(err2 / na2) : 0.0;
+  for (int i = 0; i < N; ++i) local.order[i] = c->order[i];
+  if (stats) *stats = local;
+  return TALS_OK;
+}
+
+tals_status t_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* stats) {
+  if (!c || !G_out) return fail(TALS_EINVAL, "ctx and G_out must not be NULL");
+  if (!U_out) return fail(TALS_EINVAL, "t_hosvd needs U_out (the projections read the factors)");
+  for (int n = 0; n < c->N; ++n)
+    if (!U_out[n]) return fail(TALS_EINVAL, "U_out[%d] is NULL", n);
+  if (c->opts.use_graph && c->opts.precision == TALS_PREC_NATIVE)
+    return t_hosvd_graph(c, G_out, U_out, stats);
+  const int N = c->N;
+  tals_stats local;
+  std::memset(&local, 0, sizeof(local));
+  tals_status st;
+  long long d[TALS_MAX_NDIM];
+  for (int m = 0; m < N; ++m) d[m] = c->dims[m];
+  for (int n = 0; n < N; ++n) {
+    ModeJob j;
+    j.n = n;
+    j.v = view_of(d, N, n);
+    j.R = c->ranks[n];
+    j.X = c->A;
+    j.Wdest = (n == N - 1) ? c->tbuf[0] : nullptr;   // A x_n U^T of the last mode
+    if (c->opts.precision == TALS_PREC_MIXED_BF16)
+      st = run_mode_mixed(c, j, n == 0);
+    else
+      st = run_mode(c, j, n == 0);
+    if (st != TALS_OK) return st;
+    if ((st = read_states(c)) != TALS_OK) return st;
+    if ((st = mode_status(c, n)) != TALS_OK) return st;
+    if ((st = emit_factor(c, j, U_out[n])) != TALS_OK) return st;
+    fill_mode_stats(c, n, &local);
+  }
+  // core: G = (A x_N U_N^T) x_1 U_1^T ... x_{N-1} U_{N-1}^T on shrinking tensors
+  d[N - 1] = c->ranks[N - 1];
+  const void* cur = c->tbuf[0];
+  int nsp = 0;
+  for (int m = 0; m < N - 1; ++m) {
+    ModeView v = view_of(d, N, m);
+    PassConfig pc = pass_config(c->dtype, v, c->ranks[m], c->sms);
+    void* dest = (m == N - 2) ? G_out : c->tbuf[(m + 1) & 1];
+    cudaError_t e = launch_pass(c->dtype, pc, PASS_PROJECT, cur, v, c->ranks[m], U_out[m],
+                                nullptr, c->spart, dest, 0, nullptr, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "projection pass");
+    nsp = pc.grid_x * pc.grid_y;
+    cur = dest;
+    d[m] = c->ranks[m];
+  }
+  cudaError_t e = cudaMemcpyAsync(c->host_d, c->spart, nsp * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->host_d + nsp, c->norm_a2, sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "readback");
+  double g2 = 0.0;
+  for (int i = 0; i < nsp; ++i) g2 += c->host_d[i];
+  for (int n = 0; n < N; ++n) g2 -= c->st_host[n].corr;   // rounded-basis terms of every mode
+  const double na2 = c->host_d[nsp];
+  local.norm_a = std::sqrt(na2);
+  local.rel_err = na2 > 0 ? std::sqrt(std::max(na2 - g2, 0.0) / na2) : 0.0;
+  for (int i = 0; i < N; ++i) local.order[i] = i;
+  if (stats) *stats = local;
+  return TALS_OK;
+}
+
+tals_status st_hosvd_host(tals_ctx* c, const void* A_host, void* G_host, void* const* U_host,
+                          tals_stats* stats) {
+  if (!c || !A_host || !G_host) return fail(TALS_EINVAL, "NULL argument");
+  if (!c->A_owned) return fail(TALS_EINVAL, "st_hosvd_host needs a context from tucker_als_init_owned");
+  size_t nA = 1, nG = 1;
+  for (int m = 0; m < c->N; ++m) {
+    nA *= (size_t)c->dims[m];
+    nG *= (size_t)c->ranks[m];
+  }
+  cudaError_t e = cudaMemcpyAsync(c->A_owned, A_host, nA * c->esz, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor upload");
+  if (!c->hostio_G) {
+    if ((e = cudaMallocAsync(&c->hostio_G, nG * c->esz, c->stream)) != cudaSuccess)
+      return cuda_fail(e, "core buffer");
+    for (int m = 0; m < c->N; ++m)
+      if ((e = cudaMallocAsync(&c->hostio_U[m], (size_t)c->dims[m] * c->ranks[m] * c->esz,
+                               c->stream)) != cudaSuccess)
+        return cuda_fail(e, "factor buffer");
+  }
+  tals_status st = st_hosvd(c, c->hostio_G, c->hostio_U, stats);
+  if (st != TALS_OK) return st;
+  e = cudaMemcpyAsync(G_host, c->hostio_G, nG * c->esz, cudaMemcpyDeviceToHost, c->stream);
+  for (int m = 0; m < c->N && e == cudaSuccess; ++m)
+    if (U_host && U_host[m])
+      e = cudaMemcpyAsync(U_host[m], c->hostio_U[m], (size_t)c->dims[m] * c->ranks[m] * c->esz,
+                          cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "result download");
+}
+
+tals_status als_mode_sweep(tals_ctx* c, int mode, int max_iters, double* err_out,
+                           int* converged_out) {
+  if (!c || mode < 0 || mode >= c->N) return fail(TALS_EINVAL, "bad context or mode");
+  if (max_iters < 0) return fail(TALS_EINVAL, "max_iters < 0");
+  DriveState& ds = c->drive[mode];
+  tals_status st;
+  if (ds.finished) return fail(TALS_EINVAL, "mode %d already finished", mode);
+  if (!ds.inited) {
+    if (!c->cur) {
+      c->cur = c->A;
+      for (int m = 0; m < c->N; ++m) c->cur_dims[m] = c->dims[m];
+    }
+    ds.job.n = mode;
+    ds.job.v = view_of(c->cur_dims, c->N, mode);
+    ds.job.R = c->ranks[mode];
+    ds.job.X = c->cur;
+    ds.job.Wdest = c->tbuf[c->cur_buf];
+    if ((st = mode_setup(c, ds.job)) != TALS_OK) return st;
+    if ((st = mode_init_launch(c, ds.job, !c->norm_set)) != TALS_OK) return st;
+    c->norm_set = true;
+    ds.inited = true;
+  }
+  for (int k = 0; k < max_iters; ++k) {
+    if ((st = read_states(c)) != TALS_OK) return st;
+    if (c->st_host[mode].done) break;
+    // before the stop rule fires no further sweep may overwrite W while it is
+    // still needed, so W is written on every sweep once k >= 1
+    if ((st = mode_sweep_launch(c, ds.job)) != TALS_OK) return st;
+  }
+  if ((st = read_states(c)) != TALS_OK) return st;
+  if ((st = mode_status(c, mode)) != TALS_OK) return st;
+  if (err_out) *err_out = c->st_host[mode].e_cur;
+  if (converged_out) *converged_out = c->st_host[mode].converged;
+  return TALS_OK;
+}
+
+tals_status als_mode_finish(tals_ctx* c, int mode, void* U_out, int truncate) {
+  if (!c || mode < 0 || mode >= c->N) return fail(TALS_EINVAL, "bad context or mode");
+  DriveState& ds = c->drive[mode];
+  if (!ds.inited) return fail(TALS_EINVAL, "mode %d has not been swept", mode);
+  if (c->st_host[mode].k < 1) return fail(TALS_EINVAL, "mode %d needs at least one sweep", mode);
+  tals_status st = emit_factor(c, ds.job, U_out);
+  if (st != TALS_OK) return st;
+  // the last sweep wrote W = B^T Q into tbuf[cur_buf] only if k >= 1 at its start
+  // or it was the budgeted last; re-project when W is stale
+  const ModeState& ms = c->st_host[mode];
+  if (truncate) {
+    // W of the last sweep is B x_n Q^T only when that sweep ended the mode; a
+    // mode interrupted by the caller is truncated with its latest iterate
+    if (!ms.done) {
+      cudaError_t e = launch_pass(c->dtype, ds.job.pc, PASS_PROJECT, ds.job.X, ds.job.v, ds.job.R,
+                                  c->Lt, nullptr, c->spart, ds.job.Wdest, 0, nullptr, 0, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "projection pass");
+    }
+    c->cur = ds.job.Wdest;
+    c->cur_dims[mode] = c->ranks[mode];
+    c->cur_buf ^= 1;
+  }
+  ds.finished = true;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "synchronize");
+}
+
+tals_status tals_time_pass(tals_ctx* c, int mode, int iters, double* ms, double* bytes,
+                           double* flops) {
+  if (!c || mode < 0 || mode >= c->N || iters < 1) return fail(TALS_EINVAL, "bad arguments");
+  ModeJob j;
+  j.n = mode;
+  j.v = view_of(c->dims, c->N, mode);
+  j.R = c->ranks[mode];
+  j.X = c->A;
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, j.R, c->Lt, c->Ypart, c->spart,
+                              c->tbuf[0], 0, nullptr, 0, c->stream);   // warm-up
+  cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < iters && e == cudaSuccess; ++i)
+    e = launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, j.R, c->Lt, c->Ypart, c->spart,
+                    c->tbuf[0], 0, nullptr, 0, c->stream);
+  cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "timed pass");
+  const double T = (double)j.v.P * j.v.I * j.v.Q;
+  if (ms) *ms = t / iters;
+  if (bytes) *bytes = T * c->esz + (double)j.v.J() * j.R * c->esz;
+  if (flops) *flops = 4.0 * j.R * T;
+  return TALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Shared device-side definitions of the tals library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tals {
+
+constexpr int kThreads = 256;       // threads per CTA of the pass and row kernels
+constexpr int kTileCols = 16;       // unfolding columns per tile of the pass kernel
+
+// Per-mode ALS state, resident in device memory. Written only by the single-CTA
+// small kernels, read by every kernel of the sweep to skip work once the stop
+// rule has fired.
+struct ModeState {
+  double normM2;      // ||B_(n)||^2, from the initial pass
+  double normA;       // ||A||_F of the original input (reading of Eq. 5.01's norm)
+  double eta;         // stop tolerance (negative: never stop early)
+  double e_prev;      // e_{k-1}
+  double e_cur;       // e_k
+  double sW;          // ||W||^2 = ||Q_k^T B_(n)||^2 of the last sweep
+  int k;              // completed R-updates
+  int max_sweeps;
+  int done;           // stop rule fired or sweep budget exhausted
+  int converged;      // stop rule fired
+  int status;         // 0 ok, else a tals_status code
+  int fail_stage;     // where a factorisation failed (diagnostics)
+  int bulk;           // sweeps run on the bulk (BF16) path
+  int resid;          // sW holds ||B - Q W^T||^2 (the error itself) instead of ||W||^2
+  double corr;        // tr((Q'^T Q' - I) X): first-order term for the rounded basis Q'
+};
+
+// splitmix64 output number c of the stream seeded with `state`:
+// mix(state + (c + 1) * 0x9E3779B97F4A7C15) (Steele, Lea, Flood 2014; Vigna).
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t state, uint64_t c) {
+  uint64_t z = state + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Entry (j, r) of the initial sketch S: top 24 bits of output j*R + r, scaled
+// to [0, 1) (exactly representable in FP32 and FP64).
+__device__ __forceinline__ float sketch_entry(uint64_t state, uint64_t j, int R, int r) {
+  uint64_t z = splitmix64_at(state, j * (uint64_t)R + (uint64_t)r);
+  return (float)(uint32_t)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red /* >= 32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = lane < nw ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+}  // namespace tals

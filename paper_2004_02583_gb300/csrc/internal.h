@@ -1,0 +1,99 @@
+// Library-internal declarations shared by the host-side translation units.
+#pragma once
+
+#include <cstdarg>
+#include <cstddef>
+
+#include "../../include/tals.h"
+#include "kernels.h"
+
+namespace tals {
+
+struct ModeJob {
+  int n = 0;
+  ModeView v{};
+  int R = 0;
+  const void* X = nullptr;       // tensor the mode reads
+  void* Wdest = nullptr;         // where the final sweep writes B x_n Q^T (P x R x Q), or null
+  PassConfig pc;
+  RowPlan rp{};
+  ModeState* st = nullptr;
+  unsigned long long cond = 0;   // CUDA graph conditional handle of the sweep loop
+  int has_cond = 0;
+  int resid = 0;                 // sweeps measure the error from the explicit residual
+};
+
+struct DriveState {
+  bool inited = false;
+  bool finished = false;
+  ModeJob job;
+};
+
+struct GraphCache;
+struct MixedState;
+
+tals_status fail(tals_status code, const char* fmt, ...);
+tals_status cuda_fail(cudaError_t e, const char* what);
+ModeView view_of(const long long* dims, int N, int n);
+tals_status mode_setup(tals_ctx* c, ModeJob& j);
+tals_status mode_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
+tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j);
+tals_status read_states(tals_ctx* c);
+tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a);
+
+// graph.cu: whole decompositions as one CUDA graph per context and output set
+tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
+tals_status t_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
+void graphs_destroy(tals_ctx* c);
+
+// mixed.cu: BF16 shadow + tcgen05 bulk sweeps
+tals_status mixed_alloc(tals_ctx* c);
+void mixed_free(tals_ctx* c);
+tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a);
+
+}  // namespace tals
+
+struct tals_ctx {
+  int dtype = 0;
+  size_t esz = 4;
+  int N = 0;
+  long long dims[TALS_MAX_NDIM] = {};
+  int ranks[TALS_MAX_NDIM] = {};
+  int order[TALS_MAX_NDIM] = {};
+  tals_opts opts{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap[2] = {nullptr, nullptr};   // private streams used only for graph capture
+  int sms = 0;
+  const void* A = nullptr;
+  void* A_owned = nullptr;
+  // workspace
+  void* tbuf[2] = {nullptr, nullptr};
+  void* Ypart = nullptr;
+  double* spart = nullptr;
+  double* Gpart = nullptr;
+  double* Gfin = nullptr;
+  double* GpartL = nullptr;   // Gram partials of the stored (rounded) basis
+  double* GfinL = nullptr;
+  double* F = nullptr;
+  double* Y64 = nullptr;
+  double* L64 = nullptr;
+  double* Z64 = nullptr;
+  void* Lt = nullptr;
+  tals::ModeState* st = nullptr;
+  double* norm_a2 = nullptr;
+  tals::ModeState* st_host = nullptr;   // pinned
+  double* host_d = nullptr;             // pinned scratch
+  size_t host_d_n = 0;
+  size_t need_ir = 0;
+  // als_mode_sweep / als_mode_finish drive state
+  tals::DriveState drive[TALS_MAX_NDIM];
+  const void* cur = nullptr;
+  long long cur_dims[TALS_MAX_NDIM] = {};
+  int cur_buf = 0;
+  bool norm_set = false;
+  // st_hosvd_host device buffers
+  void* hostio_G = nullptr;
+  void* hostio_U[TALS_MAX_NDIM] = {};
+  tals::GraphCache* graphs = nullptr;
+  tals::MixedState* mixed = nullptr;
+};

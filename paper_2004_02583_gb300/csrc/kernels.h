@@ -1,0 +1,90 @@
+// Host-side launchers of the tals kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tals {
+
+enum PassMode { PASS_INIT = 0, PASS_SWEEP = 1, PASS_PROJECT = 2, PASS_GIVEN = 3 };
+
+// View of a row-major tensor for mode n: P (product of earlier sizes) x I_n x Q
+// (product of later sizes). Column j = p*Q + q of the unfolding B_(n).
+struct ModeView {
+  long long P, I, Q;
+  __host__ __device__ long long J() const { return P * Q; }
+};
+
+struct PassConfig {
+  int rc = 0;        // r-chunk width of the instantiation
+  int rpt = 0;       // rows per thread of the Y accumulation
+  int rw = 0;        // r-columns per thread of the Y accumulation
+  int grid_x = 0;    // CTAs along the tiles
+  int grid_y = 0;    // r-chunks
+  size_t smem = 0;   // dynamic shared memory
+  int nbuf = 2;      // tile buffers (2: cp.async double buffering)
+  int nt = 256;      // threads per CTA
+  bool ok = false;
+};
+
+// Pick the instantiation and launch shape for a pass over `v` with rank R.
+PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms);
+
+// One read of the tensor:
+//   INIT:    Y += B_(n) S (S the seeded sketch), ||B||^2 partials
+//   SWEEP:   W = B_(n)^T Lq, Y += B_(n) W, ||W||^2 partials, optional W output
+//   PROJECT: W = B_(n)^T Lq, ||W||^2 partials, W output
+//   GIVEN:   Y += B_(n) W with W read from Win (P x R x Q layout)
+// Ypart: [grid_x][I][R] (dtype), spart: [grid_y*grid_x] doubles.
+// W output layout: P x R x Q (the tensor B x_n Lq^T). Written when Wout != 0
+// and (st == 0 or st->k >= w_from_k or st->k + 1 >= st->max_sweeps).
+cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* X,
+                        const ModeView& v, int R, const void* Lq, void* Ypart,
+                        double* spart, void* Wout, uint64_t sketch_state,
+                        const ModeState* st, int w_from_k, cudaStream_t s,
+                        const void* Win = nullptr, int resid = 0);
+
+// Y64[i][r] = sum_b Ypart[b][i][r] (FP64, fixed order); Gram partials per row
+// block: gram_mode 1 = Y64^T Y64, 2 = L64^T Y64; scalar: sum of spart[0..nsp)
+// stored into st->normM2 (which = 0, also into *norm_a2 if non-null) or st->sW (which = 1).
+struct RowPlan { int rows_per_block; int blocks; };
+RowPlan row_plan(long long I, int R, int num_sms);
+cudaError_t launch_reduce_rows(int dtype, const void* Ypart, int gx, long long I, int R,
+                               double* Y64, int gram_mode, const double* L64, double* Gpart,
+                               const RowPlan& rp, const double* spart, int nsp, int which,
+                               ModeState* st, double* norm_a2, cudaStream_t s,
+                               void* YT = nullptr);
+
+// Out[c][r] = In[r][c] for a rows x cols row-major matrix (dtype).
+cudaError_t launch_transpose(int dtype, const void* In, long long rows, long long cols, void* Out,
+                             cudaStream_t s);
+
+// Gfin[o] = sum_b Gpart[b][o] over nb partials of R x R (deterministic order).
+cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
+                            const ModeState* st, cudaStream_t s);
+
+// Single-CTA FP64 kernel: sums nb Gram partials, then
+//   op 0 (QR):   lower Cholesky factor F of the Gram (fails -> ESINGULAR)
+//   op 1 (TEST): e_k = sqrt(normM2 - sW), Eq. 5.01 stop rule, k++, and if the
+//                sweep continues, F = chol(Gram).
+// When has_cond, thread 0 sets the CUDA graph conditional `cond` to 0 once the
+// mode is done (stop rule, sweep budget or failure), ending the device-side loop.
+cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F,
+                         ModeState* st, const double* norm_a2, unsigned long long cond,
+                         int has_cond, cudaStream_t s, const double* GL = nullptr);
+
+// Row-wise solves against the R x R lower factor F (FP64):
+//   op 0 (LT):  Out = In F^-T          (Q factor of CholeskyQR)
+//   op 1 (SPD): Out = In (F F^T)^-1
+// optional: OutT (dtype copy of Out), Gpart (per-block Out^T Out partials).
+cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, const double* F,
+                             int op, double* Out, void* OutT, double* Gpart, const RowPlan& rp,
+                             const ModeState* st, cudaStream_t s, int gram_rounded = 0);
+
+// Initialise a ModeState (k = 0, flags cleared) on the device. resid: the
+// sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
+cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s);
+
+}  // namespace tals

@@ -1,0 +1,140 @@
+// Grid-level launch of the fused ALS pass (see pass_impl.cuh for the device code).
+#include <algorithm>
+
+#include "pass_impl.cuh"
+
+namespace tals {
+
+template <typename T, int RC, int RPT, int RW, int NT>
+__global__ void __launch_bounds__(NT, 1) pass_kernel(PassArgs<T> a) {
+  if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* yp = a.Ypart != nullptr ? a.Ypart + (size_t)blockIdx.x * a.I * a.R : nullptr;
+  const double tot =
+      pass_cta<T, RC, RPT, RW, NT>(a, blockIdx.x, gridDim.x, blockIdx.y, smem_raw, yp);
+  if (threadIdx.x == 0) a.spart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Host side: instantiation table and launch
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Inst {
+  int rc, rpt, rw, nt;
+};
+
+// Candidate instantiations per dtype. 512-thread shapes keep <= 128 registers
+// per thread (16 warps per SM for latency hiding); 256-thread shapes serve
+// larger per-thread tiles.
+const Inst kInstF32[] = {{32, 1, 16, 512}, {32, 2, 16, 512}, {32, 4, 16, 256},
+                         {16, 1, 16, 512}, {16, 2, 16, 512}, {16, 4, 16, 256},
+                         {8, 1, 8, 512},   {8, 2, 8, 512},   {8, 4, 8, 512},  {8, 8, 8, 256}};
+const Inst kInstF64[] = {{16, 1, 8, 256}, {16, 2, 8, 256}, {16, 4, 8, 256},
+                         {8, 1, 8, 256},  {8, 2, 8, 256},  {8, 4, 8, 256}};
+
+template <typename T, int RC, int RPT, int RW, int NT>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&pass_kernel<T, RC, RPT, RW, NT>);
+}
+
+template <typename T>
+void* lookup(const Inst& in) {
+#define TALS_CASE(RC, RPT, RW, NT)                                            \
+  if (in.rc == RC && in.rpt == RPT && in.rw == RW && in.nt == NT)             \
+    return kernel_ptr<T, RC, RPT, RW, NT>();
+  if constexpr (sizeof(T) == 4) {
+    TALS_CASE(32, 1, 16, 512) TALS_CASE(32, 2, 16, 512) TALS_CASE(32, 4, 16, 256)
+    TALS_CASE(16, 1, 16, 512) TALS_CASE(16, 2, 16, 512) TALS_CASE(16, 4, 16, 256)
+    TALS_CASE(8, 1, 8, 512) TALS_CASE(8, 2, 8, 512) TALS_CASE(8, 4, 8, 512)
+    TALS_CASE(8, 8, 8, 256)
+  } else {
+    TALS_CASE(16, 1, 8, 256) TALS_CASE(16, 2, 8, 256) TALS_CASE(16, 4, 8, 256)
+    TALS_CASE(8, 1, 8, 256) TALS_CASE(8, 2, 8, 256) TALS_CASE(8, 4, 8, 256)
+  }
+#undef TALS_CASE
+  return nullptr;
+}
+
+}  // namespace
+
+PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
+  PassConfig cfg;
+  const bool f32 = dtype == 1;
+  const Inst* tab = f32 ? kInstF32 : kInstF64;
+  const int ntab = f32 ? (int)(sizeof(kInstF32) / sizeof(Inst)) : (int)(sizeof(kInstF64) / sizeof(Inst));
+  const size_t smem_max = 227 * 1024;
+  // Score every fitting (instantiation, buffering): rank chunks re-read the
+  // tensor (mostly from L2) and a single buffer exposes load latency; prefer
+  // the smallest RPT (fewest idle rows) among equals.
+  double best = 1e30;
+  for (int nbuf = 2; nbuf >= 1; --nbuf) {
+    for (int k = 0; k < ntab; ++k) {
+      const Inst& in = tab[k];
+      const int nrg = in.rc / in.rw;
+      const int rowt = in.nt / nrg;
+      if ((long long)rowt * in.rpt < v.I) continue;
+      size_t sm = f32 ? pass_smem_bytes<float>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt)
+                      : pass_smem_bytes<double>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt);
+      if (sm > smem_max) continue;
+      const int chunks = (R + in.rc - 1) / in.rc;
+      const double waste = (double)(in.rc * chunks - R) / (double)(in.rc * chunks);
+      // prefer more resident warps, then fewer idle rows
+      const double score = chunks * (nbuf == 1 ? 1.35 : 1.0) * (1.0 + waste) +
+                           (in.nt == 512 ? 0.0 : 2e-3) + 1e-3 * in.rpt;
+      if (score < best) {
+        best = score;
+        cfg.rc = in.rc;
+        cfg.rpt = in.rpt;
+        cfg.rw = in.rw;
+        cfg.nt = in.nt;
+        cfg.smem = sm;
+        cfg.nbuf = nbuf;
+        cfg.ok = true;
+      }
+    }
+  }
+  if (!cfg.ok) return cfg;
+  cfg.grid_y = (R + cfg.rc - 1) / cfg.rc;
+  const long long ntiles = (v.J() + kJT - 1) / kJT;
+  int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (cfg.smem + 1024));
+  per_sm = std::min(per_sm, 2);
+  long long gx = std::max<long long>(1, (long long)num_sms * per_sm / cfg.grid_y);
+  gx = std::min(gx, ntiles);
+  cfg.grid_x = (int)gx;
+  return cfg;
+}
+
+cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* X,
+                        const ModeView& v, int R, const void* Lq, void* Ypart, double* spart,
+                        void* Wout, uint64_t sketch_state, const ModeState* st, int w_from_k,
+                        cudaStream_t s, const void* Win, int resid) {
+  if (!cfg.ok) return cudaErrorInvalidConfiguration;
+  if (resid && cfg.grid_y != 1) return cudaErrorInvalidValue;
+  const Inst in{cfg.rc, cfg.rpt, cfg.rw, cfg.nt};
+  void* fn = dtype == 1 ? lookup<float>(in) : lookup<double>(in);
+  if (fn == nullptr) return cudaErrorInvalidDeviceFunction;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cfg.smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(cfg.grid_x, cfg.grid_y);
+  const long long ntiles = (v.J() + kJT - 1) / kJT;
+  const size_t esz = dtype == 1 ? 4 : 8;
+  const int vec_ok = ((uintptr_t)X % 16 == 0) && ((v.Q * esz) % 16 == 0);
+  if (dtype == 1) {
+    PassArgs<float> a{(const float*)X, v.P, v.I, v.Q, v.J(), R, mode, (const float*)Lq,
+                      (const float*)Win, (float*)Ypart, spart, (float*)Wout, sketch_state, st,
+                      w_from_k, ntiles, cfg.nbuf, vec_ok, resid};
+    void* args[] = {&a};
+    return cudaLaunchKernel(fn, grid, dim3(cfg.nt), args, cfg.smem, s);
+  } else {
+    PassArgs<double> a{(const double*)X, v.P, v.I, v.Q, v.J(), R, mode, (const double*)Lq,
+                       (const double*)Win, (double*)Ypart, spart, (double*)Wout, sketch_state, st,
+                       w_from_k, ntiles, cfg.nbuf, vec_ok, resid};
+    void* args[] = {&a};
+    return cudaLaunchKernel(fn, grid, dim3(cfg.nt), args, cfg.smem, s);
+  }
+}
+
+}  // namespace tals

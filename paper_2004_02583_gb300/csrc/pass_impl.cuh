@@ -1,0 +1,401 @@
+// The fused ALS pass over the mode-n unfolding (CUDA cores, FP32 or FP64).
+//
+// One CTA walks tiles of kTileCols consecutive unfolding columns j = p*Q + q,
+// reading B[p, 0:I, q] in place (never forming a permuted unfolding, Sec. 3
+// "row-wise update"). Per tile, with Qb the orthonormal basis of L_k in shared
+// memory:
+//   step 1  W_t = B_t^T Qb                (kTileCols x RC, K = I)     Alg. 3 R-update
+//   step 2  Y  += B_t W_t                 (I x RC, K = kTileCols)     Alg. 3 L-update
+// so one read of the tensor gives Y = B B^T Qb (Eq. 2.2). Y stays in registers
+// across the CTA's tiles and is written once as a per-CTA partial; the FP64
+// reduction over CTAs runs in a second kernel (deterministic order). ||W||^2 is
+// accumulated per tile in the compute type and per CTA in FP64, giving
+// e_k^2 = ||B||^2 - ||W||^2 for the Eq. 5.01 stop rule. W itself is written in
+// the P x R x Q layout, i.e. as the tensor B x_n Qb^T -- the st-HOSVD
+// truncation of Alg. 5 without another pass.
+//
+// Tiles are staged into shared memory with cp.async, two buffers deep, so the
+// next tile streams in while the current one is multiplied. The tile is kept
+// as Ts[i][c] with 16-byte aligned rows: step 1 reads four columns of a row as
+// one vector, step 2 reads four columns of the thread's rows the same way.
+//
+// Rank is split into chunks of RC columns along gridDim.y: a chunk's W and Y
+// columns depend only on the same columns of Qb, so chunks are independent.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tals {
+
+constexpr int kJT = kTileCols;   // columns per tile
+constexpr int kJTP = kJT + 4;    // padded row stride (elements), keeps rows 16-byte aligned
+
+template <typename T>
+struct PassArgs {
+  const T* X;
+  long long P, I, Q, J;
+  int R;
+  int mode;
+  const T* L;
+  const T* Win;      // PASS_GIVEN: W read from a tensor in the P x R x Q layout
+  T* Ypart;
+  double* spart;
+  T* Wout;
+  uint64_t sketch_state;
+  const ModeState* st;
+  int w_from_k;
+  long long ntiles;
+  int nbuf;          // tile buffers (2: cp.async double buffering)
+  int vec_ok;        // X is 16-byte aligned and Q keeps rows aligned
+  int resid;         // SWEEP: accumulate ||B - Qb W^T||^2 instead of ||W||^2 (one chunk only)
+};
+
+template <typename T, int RC, int RPT, int RW, int NT>
+struct PassShape {
+  static constexpr int NRG = RC / RW;              // r-groups of the Y accumulation
+  static constexpr int ROWT = NT / NRG;            // row-threads per r-group
+  static constexpr int RL = RC / 8;                // r-columns per lane in step 1 (8 r-groups)
+  static constexpr int NW = NT / 32;               // warps (step 1 splits I over them)
+  static constexpr int WSP = RC + 4;               // padded row stride of W tiles
+  static_assert(RC % RW == 0 && RC % 8 == 0 && RW % 4 == 0, "bad chunk");
+  static_assert(NT % NRG == 0 && (ROWT % 32) == 0, "r-groups must be warp-uniform");
+};
+
+// Rows of slack after the tile buffers: step 2 reads (and discards) rows up to
+// rowspan - 1 of the last buffer.
+__host__ __device__ inline long long slack_rows(long long I, int rowspan) {
+  return rowspan > I ? rowspan - I : 0;
+}
+
+template <typename T>
+__host__ __device__ inline size_t pass_smem_bytes(long long I, int RC, int rowspan, int nbuf,
+                                                  int nt = kThreads) {
+  size_t ts = (size_t)nbuf * ((size_t)I * kJTP) + (size_t)slack_rows(I, rowspan) * kJTP;
+  size_t ls = (size_t)I * RC;
+  size_t wr = (size_t)(nt / 32) * kJT * (RC + 4);
+  size_t ws = (size_t)kJT * (RC + 4);
+  return (ts + ls + wr + ws) * sizeof(T) + 32 * sizeof(double);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes));
+}
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int src_bytes) {
+  if constexpr (B == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Issue the copies of tile t into Tb (I x kJTP). Columns beyond J are zero-filled.
+template <typename T>
+__device__ __forceinline__ void issue_tile(const PassArgs<T>& a, long long t, T* Tb) {
+  const long long I = a.I, Q = a.Q;
+  const long long j0 = t * kJT;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long p0 = j0 / Q, q0 = j0 - p0 * Q;
+  constexpr int EPV = 16 / sizeof(T);   // elements per 16-byte chunk
+  if (a.vec_ok && q0 + kJT <= Q && j0 + kJT <= a.J) {
+    // whole tile inside one p: every row is kJT contiguous elements
+    const T* base = a.X + p0 * I * Q + q0;
+    constexpr int CPR = kJT / EPV;      // chunks per row
+    for (long long e = tid; e < I * CPR; e += nt) {
+      const long long i = e / CPR;
+      const int k = (int)(e - i * CPR);
+      cp_async16(Tb + i * kJTP + k * EPV, base + i * Q + k * EPV, 16);
+    }
+  } else if (Q >= kJT) {
+    // column-fastest element copies (rows may straddle two p)
+    for (long long e = tid; e < I * kJT; e += nt) {
+      const long long i = e / kJT;
+      const int c = (int)(e - i * kJT);
+      const long long j = j0 + c;
+      const bool ok = j < a.J;
+      const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
+      cp_async_elem<sizeof(T)>(Tb + i * kJTP + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+    }
+  } else {
+    // row-fastest element copies: consecutive threads read consecutive i
+    for (long long e = tid; e < I * kJT; e += nt) {
+      const int c = (int)(e / I);
+      const long long i = e - (long long)c * I;
+      const long long j = j0 + c;
+      const bool ok = j < a.J;
+      const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
+      cp_async_elem<sizeof(T)>(Tb + i * kJTP + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+    }
+  }
+}
+
+// load 4 consecutive T from 16-byte aligned shared memory
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+
+// One CTA's share of a pass: tiles t_begin, t_begin + t_step, ... of rank chunk
+// `rchunk`. Y (this chunk's columns) is written to Yout (I x R, row stride R);
+// returns the CTA's FP64 sum (||B||^2, ||W||^2 or ||B - Qb W^T||^2) in thread 0.
+template <typename T, int RC, int RPT, int RW, int NT>
+__device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_begin, long long t_step,
+                                           int rchunk, unsigned char* smem_raw, T* Yout) {
+  using S = PassShape<T, RC, RPT, RW, NT>;
+  constexpr int WSP = S::WSP;
+  const long long I = a.I;
+  T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][I][kJTP]
+  T* Ls = Tbuf + (size_t)a.nbuf * I * kJTP + (size_t)slack_rows(I, S::ROWT * RPT) * kJTP;  // [I][RC]
+  T* Wred = Ls + (size_t)I * RC;                                           // [NW][kJT][WSP]
+  T* Ws = Wred + (size_t)S::NW * kJT * WSP;                                // [kJT][WSP]
+  double* red = reinterpret_cast<double*>(Ws + (size_t)kJT * WSP);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = rchunk * RC;
+  const bool do_w = a.mode == PASS_SWEEP || a.mode == PASS_PROJECT;
+  const bool do_y = a.mode != PASS_PROJECT;
+  const bool resid = a.resid && a.mode == PASS_SWEEP;
+  const bool cfast = a.Q >= kJT;   // W output mapping: q-contiguous or r-contiguous
+  bool write_w = a.Wout != nullptr;
+  if (write_w && a.st != nullptr)
+    write_w = (a.st->k >= a.w_from_k) || (a.st->k + 1 >= a.st->max_sweeps);
+
+  // first tile in flight before anything else
+  long long t = t_begin;
+  if (t < a.ntiles) issue_tile(a, t, Tbuf);
+  cp_async_commit();
+
+  // Qb columns r0 .. r0+RC-1 (zero beyond R) into shared memory.
+  if (do_w) {
+    for (long long e = tid; e < I * RC; e += NT) {
+      const long long i = e / RC;
+      const int rl = (int)(e - i * RC);
+      const int r = r0 + rl;
+      Ls[e] = (r < a.R) ? a.L[i * a.R + r] : T(0);
+    }
+  }
+
+  T yacc[RPT][RW];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k)
+#pragma unroll
+    for (int v = 0; v < RW; ++v) yacc[k][v] = T(0);
+  double sacc = 0.0;   // this thread's share of the pass's FP64 sum
+
+  const int rgrp = tid / S::ROWT;            // step-2 r-group (warp-uniform)
+  const int ti = tid - rgrp * S::ROWT;       // step-2 row-thread index
+  const long long IW = (I + S::NW - 1) / S::NW;
+  const long long ilo = min(I, warp * IW), ihi = min(I, ilo + IW);
+  const int cg = lane & 3, rg = lane >> 2;   // step-1 lane layout: 4 col groups x 8 r groups
+
+  int buf = 0;
+  for (; t < a.ntiles; t += t_step) {
+    const long long tn = t + t_step;
+    T* Tb = Tbuf + (size_t)buf * I * kJTP;
+    if (a.nbuf > 1) {
+      // stream the next tile into the other buffer while this one is used
+      if (tn < a.ntiles) issue_tile(a, tn, Tbuf + (size_t)(buf ^ 1) * I * kJTP);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const long long j0 = t * kJT;
+    const int ncol = (int)min((long long)kJT, a.J - j0);
+
+    if (a.mode == PASS_INIT && rchunk == 0) {
+      T nacc = T(0);
+      for (long long e = tid; e < I * kJT; e += NT) {
+        const long long i = e / kJT;
+        const int c = (int)(e - i * kJT);
+        const T x = Tb[i * kJTP + c];
+        nacc += (c < ncol) ? x * x : T(0);
+      }
+      sacc += (double)nacc;
+    }
+
+    if (do_w) {
+      // ---- step 1: W_t = B_t^T Qb, split over the warps along i ----
+      T acc[4][S::RL];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < S::RL; ++v) acc[u][v] = T(0);
+      const T* trow = Tb + cg * 4;
+      const T* lrow = Ls + rg * S::RL;
+      if (ilo < ihi) {
+        T tv[4], lv[S::RL];
+        ld4(trow + ilo * kJTP, tv);
+#pragma unroll
+        for (int v = 0; v < S::RL; ++v) lv[v] = lrow[ilo * RC + v];
+#pragma unroll 4
+        for (long long i = ilo; i < ihi; ++i) {
+          // operands of row i+1 are loaded before row i is multiplied
+          const long long inx = (i + 1 < ihi) ? i + 1 : i;
+          T tn4[4], ln[S::RL];
+          ld4(trow + inx * kJTP, tn4);
+          if constexpr (S::RL % 4 == 0) {
+#pragma unroll
+            for (int v = 0; v < S::RL; v += 4) {
+              T q4[4];
+              ld4(lrow + inx * RC + v, q4);
+#pragma unroll
+              for (int w = 0; w < 4; ++w) ln[v + w] = q4[w];
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < S::RL; ++v) ln[v] = lrow[inx * RC + v];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < S::RL; ++v) acc[u][v] = fma(tv[u], lv[v], acc[u][v]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) tv[u] = tn4[u];
+#pragma unroll
+          for (int v = 0; v < S::RL; ++v) lv[v] = ln[v];
+        }
+      }
+      T* wr = Wred + (size_t)warp * kJT * WSP;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < S::RL; ++v) wr[(cg * 4 + u) * WSP + rg * S::RL + v] = acc[u][v];
+      __syncthreads();
+      // final W: consecutive threads -> consecutive q (cfast) or consecutive r
+      T wsq = T(0);
+      for (int o = tid; o < kJT * RC; o += NT) {
+        const int c = cfast ? (o % kJT) : (o / RC);
+        const int rl = cfast ? (o / kJT) : (o % RC);
+        T w = T(0);
+#pragma unroll
+        for (int g = 0; g < S::NW; ++g) w += Wred[((size_t)g * kJT + c) * WSP + rl];
+        const int r = r0 + rl;
+        const bool valid = (c < ncol) && (r < a.R);
+        w = valid ? w : T(0);
+        Ws[c * WSP + rl] = w;
+        wsq += w * w;
+        if (write_w && valid) {
+          const long long j = j0 + c, p = j / a.Q, q = j - p * a.Q;
+          a.Wout[(p * a.R + r) * a.Q + q] = w;
+        }
+      }
+      if (!resid) sacc += (double)wsq;
+      if (resid) {
+        // ||B_t - Qb W_t^T||^2 from the tile: no cancellation against ||B||^2
+        __syncthreads();
+        T racc = T(0);
+        for (long long e = tid; e < I * kJT; e += NT) {
+          const long long i = e / kJT;
+          const int c = (int)(e - i * kJT);
+          T dot = T(0);
+#pragma unroll
+          for (int v = 0; v < RC; v += 4) {
+            T l4[4], w4[4];
+            ld4(Ls + i * RC + v, l4);
+            ld4(Ws + c * WSP + v, w4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dot = fma(l4[q], w4[q], dot);
+          }
+          const T rsd = Tb[i * kJTP + c] - dot;
+          racc += (c < ncol) ? rsd * rsd : T(0);
+        }
+        sacc += (double)racc;
+      }
+    } else if (a.mode == PASS_GIVEN) {
+      // W_t read from the given tensor (P x R x Q layout)
+      for (int o = tid; o < kJT * RC; o += NT) {
+        const int c = cfast ? (o % kJT) : (o / RC);
+        const int rl = cfast ? (o / kJT) : (o % RC);
+        const int r = r0 + rl;
+        T w = T(0);
+        if (c < ncol && r < a.R) {
+          const long long j = j0 + c, p = j / a.Q, q = j - p * a.Q;
+          w = a.Win[(p * a.R + r) * a.Q + q];
+        }
+        Ws[c * WSP + rl] = w;
+      }
+    } else {
+      // INIT: W_t is the seeded sketch S restricted to the tile's columns
+      for (int o = tid; o < kJT * RC; o += NT) {
+        const int c = o % kJT, rl = o / kJT;
+        const int r = r0 + rl;
+        T w = T(0);
+        if (c < ncol && r < a.R) w = (T)sketch_entry(a.sketch_state, (uint64_t)(j0 + c), a.R, r);
+        Ws[c * WSP + rl] = w;
+      }
+    }
+
+    if (do_y) {
+      __syncthreads();
+      // ---- step 2: Y[i, r] += sum_c B_t[i, c] W_t[c, r] ----
+      const T* wrow = Ws + rgrp * RW;
+      const T* tbase = Tb + (size_t)ti * kJTP;
+#pragma unroll
+      for (int c4 = 0; c4 < kJT; c4 += 4) {
+        T tv[RPT][4];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) ld4(tbase + (size_t)k * S::ROWT * kJTP + c4, tv[k]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          T wv[RW];
+#pragma unroll
+          for (int v = 0; v < RW; v += 4) {
+            T q4[4];
+            ld4(wrow + (c4 + u) * WSP + v, q4);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) wv[v + w] = q4[w];
+          }
+#pragma unroll
+          for (int k = 0; k < RPT; ++k)
+#pragma unroll
+            for (int v = 0; v < RW; ++v) yacc[k][v] = fma(tv[k][u], wv[v], yacc[k][v]);
+        }
+      }
+    }
+    __syncthreads();   // buffer `buf` and Ws fully consumed before they are refilled
+    if (a.nbuf > 1) {
+      buf ^= 1;
+    } else if (tn < a.ntiles) {
+      issue_tile(a, tn, Tbuf);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait<0>();
+
+  if (do_y) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const long long i = ti + (long long)k * S::ROWT;
+      if (i < I) {
+#pragma unroll
+        for (int v = 0; v < RW; ++v) {
+          const int r = r0 + rgrp * RW + v;
+          if (r < a.R) Yout[i * a.R + r] = yacc[k][v];
+        }
+      }
+    }
+  }
+  return block_sum(sacc, red);
+}
+
+}  // namespace tals

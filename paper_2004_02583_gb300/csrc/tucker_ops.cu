@@ -1,0 +1,336 @@
+// Tucker-model operators and their adjoints (Sec. 2 mode products and Tucker
+// model; the core step of Alg. 1/4):
+//   project      G = A x_1 U1^T ... x_N UN^T
+//   reconstruct  B = G x_1 U1 ... x_N UN
+//   project_backward / reconstruct_backward: the vector-Jacobian products.
+// Every mode product is one pass of the same tiled kernel that the ALS sweep
+// uses (PROJECT mode: X x_n L^T with L = U_n, or L = U_n^T to expand a mode).
+// The factor adjoints U_bar_n = (X x_{m!=n} Um^T)_(n) V_(n)^T need, for every n,
+// X projected on all other modes. Those partial contractions are recomputed
+// with a leave-one-out tree: split the modes in halves, project X on one half
+// and recurse into the other, so the full-size X is read twice for any N and no
+// partial is stored for all n at once.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace tals {
+
+namespace {
+
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  void* get(size_t bytes, cudaError_t* e) {
+    void* p = nullptr;
+    *e = cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s);
+    if (*e == cudaSuccess) ptrs.push_back(p);
+    return p;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(q, s);
+        q = nullptr;
+      }
+  }
+  ~Scratch() {
+    for (void* p : ptrs)
+      if (p) cudaFreeAsync(p, s);
+  }
+};
+
+struct OpCtx {
+  int dtype;
+  size_t esz;
+  int N;
+  long long dims[TALS_MAX_NDIM];
+  int ranks[TALS_MAX_NDIM];
+  void* const* U;
+  cudaStream_t s;
+  int sms;
+  Scratch* sc;
+};
+
+size_t numel(const long long* d, int N) {
+  size_t n = 1;
+  for (int m = 0; m < N; ++m) n *= (size_t)d[m];
+  return n;
+}
+
+// out = X x_n L^T, where X has sizes d and L is d[n] x R_out (row-major).
+tals_status apply_mode(OpCtx& o, const void* X, const long long* d, int n, const void* L,
+                       int R_out, void* out) {
+  ModeView v = view_of(d, o.N, n);
+  PassConfig pc = pass_config(o.dtype, v, R_out, o.sms);
+  if (!pc.ok) return fail(TALS_ENOTSUP, "mode product of mode %d (size %lld -> %d) exceeds the "
+                          "kernel limits", n, v.I, R_out);
+  cudaError_t e;
+  double* sp = (double*)o.sc->get((size_t)pc.grid_x * pc.grid_y * sizeof(double), &e);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch");
+  e = launch_pass(o.dtype, pc, PASS_PROJECT, X, v, R_out, L, nullptr, sp, out, 0, nullptr, 0, o.s);
+  if (e != cudaSuccess) return cuda_fail(e, "mode product");
+  return TALS_OK;
+}
+
+// X x_m Um^T for every m in `modes` (in that order); returns the new tensor
+// (scratch) and updates d. Never frees X.
+tals_status project_modes(OpCtx& o, const void* X, long long* d, const std::vector<int>& modes,
+                          const void** out) {
+  const void* cur = X;
+  void* prev_owned = nullptr;
+  for (int m : modes) {
+    long long nd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, nd);
+    nd[m] = o.ranks[m];
+    cudaError_t e;
+    void* dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    tals_status st = apply_mode(o, cur, d, m, o.U[m], o.ranks[m], dst);
+    if (st != TALS_OK) return st;
+    if (prev_owned) o.sc->release(prev_owned);
+    prev_owned = dst;
+    cur = dst;
+    d[m] = o.ranks[m];
+  }
+  *out = cur;
+  return TALS_OK;
+}
+
+// U_bar_n = (P)_(n) V_(n)^T where P has sizes d (mode n full, others at rank).
+tals_status factor_adjoint(OpCtx& o, const void* P, const long long* d, int n, const void* V,
+                           void* Ubar) {
+  ModeView v = view_of(d, o.N, n);
+  const int R = o.ranks[n];
+  PassConfig pc = pass_config(o.dtype, v, R, o.sms);
+  if (!pc.ok) return fail(TALS_ENOTSUP, "factor adjoint of mode %d exceeds the kernel limits", n);
+  RowPlan rp = row_plan(v.I, R, o.sms);
+  cudaError_t e;
+  void* yp = o.sc->get((size_t)pc.grid_x * v.I * R * o.esz, &e);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch");
+  double* sp = (double*)o.sc->get((size_t)pc.grid_x * pc.grid_y * sizeof(double), &e);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch");
+  e = launch_pass(o.dtype, pc, PASS_GIVEN, P, v, R, nullptr, yp, sp, nullptr, 0, nullptr, 0, o.s, V);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint pass");
+  e = launch_reduce_rows(o.dtype, yp, pc.grid_x, v.I, R, nullptr, 0, nullptr, nullptr, rp, nullptr,
+                         0, 0, nullptr, nullptr, o.s, Ubar);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint reduction");
+  o.sc->release(yp);
+  return TALS_OK;
+}
+
+// Leave-one-out tree over `targets` (all still full in X, as are the modes in `full`).
+tals_status loo(OpCtx& o, const void* X, const long long* d, std::vector<int> full,
+                std::vector<int> targets, const void* V, void* const* Ubar, void* Gproj,
+                bool* gproj_done) {
+  if (targets.size() == 1) {
+    const int n = targets[0];
+    std::vector<int> others;
+    for (int m : full)
+      if (m != n) others.push_back(m);
+    long long dd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, dd);
+    const void* P = nullptr;
+    tals_status st = project_modes(o, X, dd, others, &P);
+    if (st != TALS_OK) return st;
+    if (Ubar && Ubar[n] && (st = factor_adjoint(o, P, dd, n, V, Ubar[n])) != TALS_OK) return st;
+    if (Gproj && !*gproj_done) {
+      if ((st = apply_mode(o, P, dd, n, o.U[n], o.ranks[n], Gproj)) != TALS_OK) return st;
+      *gproj_done = true;
+    }
+    if (P != X) o.sc->release(const_cast<void*>(P));
+    return TALS_OK;
+  }
+  const size_t h = targets.size() / 2;
+  std::vector<int> t1(targets.begin(), targets.begin() + h), t2(targets.begin() + h, targets.end());
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<int>& keep = pass == 0 ? t1 : t2;
+    const std::vector<int>& drop = pass == 0 ? t2 : t1;
+    long long dd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, dd);
+    const void* Xp = nullptr;
+    tals_status st = project_modes(o, X, dd, drop, &Xp);
+    if (st != TALS_OK) return st;
+    std::vector<int> rest;
+    for (int m : full)
+      if (std::find(drop.begin(), drop.end(), m) == drop.end()) rest.push_back(m);
+    st = loo(o, Xp, dd, rest, keep, V, Ubar, Gproj, gproj_done);
+    if (Xp != X) o.sc->release(const_cast<void*>(Xp));
+    if (st != TALS_OK) return st;
+  }
+  return TALS_OK;
+}
+
+tals_status validate_ops(int dtype, int ndim, const int64_t* dims, const int* ranks,
+                         void* const* U) {
+  if (dtype != TALS_F32 && dtype != TALS_F64) return fail(TALS_EINVAL, "unsupported dtype %d", dtype);
+  if (ndim < 1 || ndim > TALS_MAX_NDIM) return fail(TALS_EINVAL, "ndim %d outside [1, 8]", ndim);
+  if (!dims || !ranks || !U) return fail(TALS_EINVAL, "dims, ranks and U must not be NULL");
+  for (int n = 0; n < ndim; ++n) {
+    if (dims[n] < 1 || ranks[n] < 1 || ranks[n] > dims[n])
+      return fail(TALS_EINVAL, "mode %d: need 1 <= R_n <= I_n", n);
+    if (!U[n]) return fail(TALS_EINVAL, "U[%d] is NULL", n);
+  }
+  return TALS_OK;
+}
+
+OpCtx make_ctx(int dtype, int ndim, const int64_t* dims, const int* ranks, void* const* U,
+               void* stream, Scratch* sc) {
+  OpCtx o;
+  o.dtype = dtype;
+  o.esz = dtype == TALS_F32 ? 4 : 8;
+  o.N = ndim;
+  for (int n = 0; n < ndim; ++n) {
+    o.dims[n] = dims[n];
+    o.ranks[n] = ranks[n];
+  }
+  o.U = U;
+  o.s = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+  o.sc = sc;
+  return o;
+}
+
+// Order in which a chain of mode products keeps intermediates smallest.
+std::vector<int> shrink_order(const OpCtx& o, bool expand) {
+  std::vector<int> ord(o.N);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    const double ra = (double)o.ranks[a] / o.dims[a], rb = (double)o.ranks[b] / o.dims[b];
+    return expand ? ra > rb : ra < rb;
+  });
+  return ord;
+}
+
+tals_status do_project(OpCtx& o, const void* A, void* G_out) {
+  std::vector<int> ord = shrink_order(o, false);
+  long long d[TALS_MAX_NDIM];
+  std::copy(o.dims, o.dims + o.N, d);
+  const void* cur = A;
+  void* owned = nullptr;
+  for (size_t k = 0; k < ord.size(); ++k) {
+    const int m = ord[k];
+    long long nd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, nd);
+    nd[m] = o.ranks[m];
+    void* dst = G_out;
+    cudaError_t e = cudaSuccess;
+    if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    tals_status st = apply_mode(o, cur, d, m, o.U[m], o.ranks[m], dst);
+    if (st != TALS_OK) return st;
+    if (owned) o.sc->release(owned);
+    owned = (dst == G_out) ? nullptr : dst;
+    cur = dst;
+    d[m] = o.ranks[m];
+  }
+  return TALS_OK;
+}
+
+tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
+  std::vector<int> ord = shrink_order(o, true);
+  long long d[TALS_MAX_NDIM];
+  for (int m = 0; m < o.N; ++m) d[m] = o.ranks[m];
+  const void* cur = G;
+  void* owned = nullptr;
+  cudaError_t e;
+  for (size_t k = 0; k < ord.size(); ++k) {
+    const int m = ord[k];
+    // expand mode m: X x_m U_m = X x_m (U_m^T)^T with L = U_m^T (R_m x I_m)
+    void* Lt = o.sc->get((size_t)o.dims[m] * o.ranks[m] * o.esz, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    e = launch_transpose(o.dtype, o.U[m], o.dims[m], o.ranks[m], Lt, o.s);
+    if (e != cudaSuccess) return cuda_fail(e, "transpose");
+    long long nd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, nd);
+    nd[m] = o.dims[m];
+    void* dst = B_out;
+    if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    tals_status st = apply_mode(o, cur, d, m, Lt, (int)o.dims[m], dst);
+    if (st != TALS_OK) return st;
+    o.sc->release(Lt);
+    if (owned) o.sc->release(owned);
+    owned = (dst == B_out) ? nullptr : dst;
+    cur = dst;
+    d[m] = o.dims[m];
+  }
+  return TALS_OK;
+}
+
+tals_status finish(cudaStream_t s) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "tucker op");
+}
+
+}  // namespace
+
+}  // namespace tals
+
+using namespace tals;
+
+extern "C" {
+
+tals_status project(const void* A, void* const* U, int dtype, int ndim, const int64_t* dims,
+                    const int* ranks, void* G_out, void* stream) {
+  tals_status st = validate_ops(dtype, ndim, dims, ranks, U);
+  if (st != TALS_OK) return st;
+  if (!A || !G_out) return fail(TALS_EINVAL, "A and G_out must not be NULL");
+  Scratch sc((cudaStream_t)stream);
+  OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
+  if ((st = do_project(o, A, G_out)) != TALS_OK) return st;
+  return finish(o.s);
+}
+
+tals_status reconstruct(const void* G, void* const* U, int dtype, int ndim, const int64_t* dims,
+                        const int* ranks, void* B_out, void* stream) {
+  tals_status st = validate_ops(dtype, ndim, dims, ranks, U);
+  if (st != TALS_OK) return st;
+  if (!G || !B_out) return fail(TALS_EINVAL, "G and B_out must not be NULL");
+  Scratch sc((cudaStream_t)stream);
+  OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
+  if ((st = do_reconstruct(o, G, B_out)) != TALS_OK) return st;
+  return finish(o.s);
+}
+
+tals_status reconstruct_backward(const void* G, void* const* U, const void* B_bar, int dtype,
+                                 int ndim, const int64_t* dims, const int* ranks, void* G_bar,
+                                 void* const* U_bar, void* stream) {
+  tals_status st = validate_ops(dtype, ndim, dims, ranks, U);
+  if (st != TALS_OK) return st;
+  if (!G || !B_bar) return fail(TALS_EINVAL, "G and B_bar must not be NULL");
+  Scratch sc((cudaStream_t)stream);
+  OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
+  std::vector<int> all(ndim);
+  std::iota(all.begin(), all.end(), 0);
+  bool gdone = false;
+  // G_bar = B_bar x U^T; U_bar_n = (B_bar x_{m!=n} Um^T)_(n) G_(n)^T
+  if ((st = loo(o, B_bar, o.dims, all, all, G, U_bar, G_bar, &gdone)) != TALS_OK) return st;
+  return finish(o.s);
+}
+
+tals_status project_backward(const void* A, void* const* U, const void* G_bar, int dtype,
+                             int ndim, const int64_t* dims, const int* ranks, void* A_bar,
+                             void* const* U_bar, void* stream) {
+  tals_status st = validate_ops(dtype, ndim, dims, ranks, U);
+  if (st != TALS_OK) return st;
+  if (!A || !G_bar) return fail(TALS_EINVAL, "A and G_bar must not be NULL");
+  Scratch sc((cudaStream_t)stream);
+  OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
+  // A_bar = G_bar x_1 U1 ... x_N UN
+  if (A_bar && (st = do_reconstruct(o, G_bar, A_bar)) != TALS_OK) return st;
+  if (U_bar) {
+    std::vector<int> all(ndim);
+    std::iota(all.begin(), all.end(), 0);
+    bool gdone = true;
+    if ((st = loo(o, A, o.dims, all, all, G_bar, U_bar, nullptr, &gdone)) != TALS_OK) return st;
+  }
+  return finish(o.s);
+}
+
+}  // extern "C"

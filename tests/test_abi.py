@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI library: it builds, loads and exports every symbol
+that include/tals.h declares (no compute calls: no GPU here)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b([A-Za-z_]\w*)\s*\(", txt, flags=re.M):
+            name = m.group(1)
+            if name in ("if", "while", "for", "sizeof") or name.isupper():
+                continue
+            names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_02583_gb300 import build
+    build.build()
+    import paper_2004_02583_gb300 as pkg
+    return pkg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["tucker_als_init", "als_mode_sweep", "st_hosvd", "t_hosvd", "reconstruct"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    import paper_2004_02583_gb300 as pkg
+    assert set(_declared()) <= set(pkg.SIGNATURES)
+
+
+def test_host_only_calls(lib):
+    import paper_2004_02583_gb300 as pkg
+    o = pkg.default_opts()
+    assert o.eta == 1e-4 and o.max_sweeps == 50 and o.use_graph == 1
+    assert b"sm_103a" in lib.tals_version()
+
+
+def test_product_path_does_not_touch_oracle():
+    pkg_dir = os.path.join(ROOT, "paper_2004_02583_gb300")
+    for dp, _, files in os.walk(pkg_dir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "oracle" not in txt.replace("the oracle", ""), f
