@@ -175,6 +175,9 @@ def main():
     ap.add_argument("--precision", default="native", choices=["native", "mixed_bf16"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--dims", default=None, help="override tensor sizes (profiling), e.g. 512,512,256")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven sweep loop instead of the CUDA graph (same kernels; ncu "
+                         "cannot profile kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
     args = ap.parse_args()
@@ -201,7 +204,8 @@ def main():
     p = W.planted(cfg.seed, DIMS, RANKS, cfg.core, cfg.noise_rel, dtype=np.float32)
     A = torch.from_numpy(p.A).cuda()
     stream = torch.cuda.current_stream()
-    ctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=args.precision)
+    ctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=args.precision,
+                       use_graph=not args.no_graph)
     if args.profile_pass:
         ms_, by_, fl_ = ctx.time_pass(mode=0, iters=1)
         print(json.dumps({"profile_pass_ms": ms_, "bytes": by_, "flops": fl_}))
@@ -299,6 +303,7 @@ def main():
                                "1e-2 noise eta 1e-6", "precision": args.precision,
                    "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
                    "rel_err": st["rel_err"], "l2": "inputs (512 MiB) larger than L2",
+                   "driver": "host loop" if args.no_graph else "CUDA graph with device-side while",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "e2e": None if e_ms is None else
