@@ -196,6 +196,16 @@ tals_status tals_batched_st_hosvd(int count, void* const* A_ptrs, const int64_t*
 tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, double* bytes,
                            double* flops);
 
+/* Diagnostics (one fused sweep, Eq. 2.2): for the FP32 tensor A (device, dims[ndim])
+ * viewed as its mode-`mode` unfolding B and the FP32 basis Q (device, I_mode x R,
+ * row-major), write Y = B B^T Q (device, FP64, I_mode x R) and *wnorm2 = ||B^T Q||^2.
+ * engine 0: CUDA-core FP32 pass. engine 1: tensor-core pass (tcgen05, BF16 operands,
+ * FP32 accumulation) on a BF16 copy of A; needs I_mode % 128 == 0, I_mode <= 512,
+ * prod of the later sizes % 128 == 0 and R <= 64 (else TALS_ENOTSUP). Uses
+ * stream-ordered scratch and synchronises the stream. */
+tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mode, const void* Q,
+                            int R, int engine, double* Y_out, double* wnorm2, void* stream);
+
 /* Free a context (its workspace, graphs and owned buffers). NULL is allowed. */
 void tals_destroy(tals_ctx* ctx);
 

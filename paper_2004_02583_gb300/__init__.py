@@ -85,6 +85,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "tals_sweep_pass": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP, ctypes.c_int,
+                                       ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     "tals_destroy": (None, [_VP]),
     "tals_last_error": (ctypes.c_char_p, []),
     "tals_version": (ctypes.c_char_p, []),
@@ -438,6 +440,23 @@ def batched_st_hosvd(As, ranks, eta=1e-4, max_sweeps=50, seed=0, stream=None):
     _check(lib().tals_batched_st_hosvd(count, _ptrs(As), dims, rk, ctypes.byref(o), _ptrs(Gs),
                                        _ptrs(Us), stats, _stream_ptr(stream)))
     return Gs, [Us[3 * t:3 * t + 3] for t in range(count)], [stats[t].to_dict(3) for t in range(count)]
+
+
+def sweep_pass(A, mode, Q, engine="cuda", stream=None):
+    """One fused sweep pass (diagnostics): returns (Y = B B^T Q in FP64, ||B^T Q||^2)
+    for the mode-`mode` unfolding B of the FP32 tensor A. engine: "cuda" (FP32 CUDA
+    cores) or "tc" (tcgen05 BF16 tensor cores)."""
+    torch = _torch()
+    _require_cuda(A, Q)
+    ndim = A.dim()
+    dims = (ctypes.c_int64 * ndim)(*[int(d) for d in A.shape])
+    R = int(Q.shape[1])
+    Y = torch.empty((int(A.shape[mode]), R), dtype=torch.float64, device=A.device)
+    w2 = ctypes.c_double()
+    _check(lib().tals_sweep_pass(A.data_ptr(), ndim, dims, int(mode), Q.data_ptr(), R,
+                                 {"cuda": 0, "tc": 1}[engine], Y.data_ptr(), ctypes.byref(w2),
+                                 _stream_ptr(stream)))
+    return Y, w2.value
 
 
 def version() -> str:

@@ -163,6 +163,8 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     return cuda_fail(e, "pinned scratch");
   c->host_d_n = need.spart + 16;
   c->need_ir = need.ir;
+  c->ypart_elems = need.ypart;
+  c->spart_n = need.spart;
   return TALS_OK;
 }
 
@@ -192,13 +194,17 @@ uint64_t sketch_state(uint64_t seed, int mode) {
 }
 
 tals_status mode_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
+  return mode_init_launch_bulk(c, j, set_norm_a, 0);
+}
+
+tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a, int bulk_max) {
   cudaStream_t s = c->stream;
   const int R = j.R;
   const long long I = j.v.I;
   cudaError_t e;
 #define TALS_CK(x)                                   \
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
-  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s));
+  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s, bulk_max));
   // Sec. 4: Y0 = B_(n) S and ||B_(n)||^2 in one pass
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_INIT, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr,
                       sketch_state(c->opts.seed, j.n), j.st, 1 << 30, s));
@@ -225,12 +231,21 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
                       j.Wdest, 0, j.st, 1, s, nullptr, j.resid));
+  return mode_sweep_tail(c, j, j.pc.grid_x, j.pc.grid_x * j.pc.grid_y, 1);
+}
+
+tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int test_op) {
+  cudaStream_t s = c->stream;
+  const int R = j.R;
+  const long long I = j.v.I;
+  cudaError_t e;
   // Y (FP64), X = Q_k^T Y partials, ||W||^2
-  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, j.pc.grid_x, I, R, c->Y64, 2, c->L64, c->Gpart,
-                             j.rp, c->spart, j.pc.grid_x * j.pc.grid_y, 1, j.st, nullptr, s));
+  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, gx, I, R, c->Y64, 2, c->L64, c->Gpart,
+                             j.rp, c->spart, nsp, 1, j.st, nullptr, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
   // e_k, Eq. 5.01, and chol(X) if the sweep continues
-  TALS_CK(launch_small(c->Gfin, 1, R, 1, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s, c->GfinL));
+  TALS_CK(launch_small(c->Gfin, 1, R, test_op, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s,
+                       c->GfinL));
   // L_{k+1} = Y X^{-1} (Alg. 3 L-update in the Q_k basis), then its Q factor
   TALS_CK(launch_row_solve(c->dtype, c->Y64, I, R, c->F, 1, c->Z64, nullptr, c->Gpart, j.rp, j.st, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));

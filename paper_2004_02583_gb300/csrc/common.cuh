@@ -28,6 +28,10 @@ struct ModeState {
   int bulk;           // sweeps run on the bulk (BF16) path
   int resid;          // sW holds ||B - Q W^T||^2 (the error itself) instead of ||W||^2
   double corr;        // tr((Q'^T Q' - I) X): first-order term for the rounded basis Q'
+  int bulk_mode;      // 1 while the mixed-precision bulk (BF16) sweeps run
+  int kf;             // sweeps of the current (final-precision) phase
+  int bulk_max;       // at most this many bulk sweeps
+  int pad2;
 };
 
 // splitmix64 output number c of the stream seeded with `state`:

@@ -38,8 +38,12 @@ ModeView view_of(const long long* dims, int N, int n);
 tals_status mode_setup(tals_ctx* c, ModeJob& j);
 tals_status mode_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
 tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j);
+// The sweep chain after the pass: reduce, TEST (op), CholeskyQR update.
+tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int test_op);
+tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a, int bulk_max);
 tals_status read_states(tals_ctx* c);
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a);
+tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters);
 
 // graph.cu: whole decompositions as one CUDA graph per context and output set
 tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
@@ -85,6 +89,8 @@ struct tals_ctx {
   double* host_d = nullptr;             // pinned scratch
   size_t host_d_n = 0;
   size_t need_ir = 0;
+  size_t ypart_elems = 0;     // capacity of Ypart (elements)
+  size_t spart_n = 0;         // capacity of spart
   // als_mode_sweep / als_mode_finish drive state
   tals::DriveState drive[TALS_MAX_NDIM];
   const void* cur = nullptr;

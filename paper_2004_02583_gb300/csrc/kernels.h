@@ -85,6 +85,13 @@ cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, co
 
 // Initialise a ModeState (k = 0, flags cleared) on the device. resid: the
 // sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
-cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s);
+cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
+                              int bulk_max = 0);
+
+// Tensor-core (tcgen05, BF16) sweep pass; see tc_pass.cu.
+bool tc_supported(const ModeView& v, int R);
+cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
+                           double* spart, int* err, int grid, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s);
 
 }  // namespace tals

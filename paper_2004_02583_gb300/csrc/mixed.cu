@@ -1,19 +1,158 @@
-// Mixed-precision form: BF16 shadow copy of the tensor, tcgen05 bulk sweeps,
-// FP32 finishing sweeps. (Filled in by the tensor-core path.)
+// Mixed-precision form of the per-mode ALS: bulk sweeps on the tensor cores
+// over a BF16 copy of the tensor, then finishing sweeps in FP32 on the original
+// tensor until the Eq. 5.01 stop rule fires.
+//
+// The bulk sweeps drive the subspace to within BF16 resolution at half the
+// bytes per sweep and tensor-core speed; the iterate stays the literal Alg. 3
+// iterate of the (rounded) data, so the FP32 sweeps that follow start from it
+// and contract the remaining error by sigma_{R+1}^2 / sigma_R^2 per sweep
+// (Thm. 2). The stop rule is only evaluated on FP32 sweeps (at least two, so
+// both compared errors are FP32), and the truncation W of Alg. 5 always comes
+// from an FP32 sweep. Grams, Cholesky, QR and norms stay FP64 throughout.
+// Modes whose shape the tensor-core pass does not cover (and the small later
+// modes of st-HOSVD) run the plain FP32 path.
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 
 namespace tals {
 
+struct MixedState {
+  void* shadow = nullptr;       // BF16 copy of A
+  size_t shadow_elems = 0;
+  int* err = nullptr;           // tensor-core pass error flag
+  const void* converted = nullptr;
+};
+
 tals_status mixed_alloc(tals_ctx* c) {
-  (void)c;
-  return fail(TALS_ENOTSUP, "mixed BF16 precision is not available in this build");
+  if (c->mixed) return TALS_OK;
+  c->mixed = new MixedState();
+  size_t n = 1;
+  for (int m = 0; m < c->N; ++m) n *= (size_t)c->dims[m];
+  cudaError_t e = cudaMallocAsync(&c->mixed->shadow, n * 2, c->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&c->mixed->err, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->mixed->err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "BF16 shadow allocation");
+  c->mixed->shadow_elems = n;
+  return TALS_OK;
 }
 
-void mixed_free(tals_ctx* c) { (void)c; }
+void mixed_free(tals_ctx* c) {
+  if (!c->mixed) return;
+  if (c->mixed->shadow) cudaFreeAsync(c->mixed->shadow, c->stream);
+  if (c->mixed->err) cudaFreeAsync(c->mixed->err, c->stream);
+  delete c->mixed;
+  c->mixed = nullptr;
+}
 
 tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
-  (void)c; (void)j; (void)set_norm_a;
-  return fail(TALS_ENOTSUP, "mixed BF16 precision is not available in this build");
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  const bool tc = c->mixed && j.X == c->A && c->dtype == TALS_F32 && tc_supported(j.v, j.R) &&
+                  c->opts.bulk_sweeps > 0;
+  if (!tc) {
+    if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
+    return mode_loop_host(c, j, c->opts.max_sweeps);
+  }
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  // BF16 copy of the tensor (once per decomposition call)
+  e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
+  if ((st = mode_init_launch_bulk(c, j, set_norm_a, c->opts.bulk_sweeps)) != TALS_OK) return st;
+  // one CTA per SM, within the capacity of the per-CTA partial buffers
+  int grid = std::min<int>(c->sms, (int)((j.v.J() + 127) / 128));
+  grid = (int)std::min<size_t>((size_t)grid, c->ypart_elems / ((size_t)j.v.I * j.R));
+  grid = (int)std::min<size_t>((size_t)grid, c->spart_n);
+  if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
+  for (int k = 0; k < c->opts.max_sweeps; ++k) {
+    if ((st = read_states(c)) != TALS_OK) return st;
+    const ModeState& ms = c->st_host[j.n];
+    if (ms.done) break;
+    if (ms.bulk_mode) {
+      e = launch_tc_pass(c->mixed->shadow, j.v, j.R, (const float*)c->Lt, (float*)c->Ypart,
+                         c->spart, c->mixed->err, grid, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
+      if ((st = mode_sweep_tail(c, j, grid, grid, 2)) != TALS_OK) return st;
+    } else {
+      if ((st = mode_sweep_launch(c, j)) != TALS_OK) return st;
+    }
+  }
+  int err = 0;
+  e = cudaMemcpyAsync(&err, c->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
+  if (err) return fail(TALS_ETIMEOUT, "tensor-core pass gave up waiting (code %d)", err);
+  return read_states(c);
 }
 
 }  // namespace tals
+
+using namespace tals;
+
+extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mode,
+                                       const void* Q, int R, int engine, double* Y_out,
+                                       double* wnorm2, void* stream) {
+  if (!A || !dims || !Q || !Y_out || ndim < 1 || ndim > TALS_MAX_NDIM || mode < 0 || mode >= ndim ||
+      R < 1 || (engine != 0 && engine != 1))
+    return fail(TALS_EINVAL, "bad arguments");
+  long long d[TALS_MAX_NDIM];
+  size_t n = 1;
+  for (int m = 0; m < ndim; ++m) {
+    d[m] = dims[m];
+    n *= (size_t)dims[m];
+  }
+  ModeView v = view_of(d, ndim, mode);
+  if (R > v.I) return fail(TALS_EINVAL, "R exceeds I");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  void* ypart = nullptr;
+  double* spart = nullptr;
+  void* shadow = nullptr;
+  int* err = nullptr;
+  int gx = 0, nsp = 0;
+  RowPlan rp = row_plan(v.I, R, sms);
+  if (engine == 0) {
+    PassConfig pc = pass_config(TALS_F32, v, R, sms);
+    if (!pc.ok) return fail(TALS_ENOTSUP, "shape outside the pass kernel limits");
+    gx = pc.grid_x;
+    nsp = pc.grid_x * pc.grid_y;
+    e = cudaMallocAsync(&ypart, (size_t)gx * v.I * R * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, nsp * sizeof(double), s);
+    if (e == cudaSuccess)
+      e = launch_pass(TALS_F32, pc, PASS_SWEEP, A, v, R, Q, ypart, spart, nullptr, 0, nullptr, 0, s);
+  } else {
+    if (!tc_supported(v, R)) return fail(TALS_ENOTSUP, "shape outside the tensor-core pass limits");
+    gx = std::min<int>(sms, (int)((v.J() + 127) / 128));
+    nsp = gx;
+    e = cudaMallocAsync(&ypart, (size_t)gx * v.I * R * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, nsp * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&shadow, n * 2, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_to_bf16((const float*)A, shadow, n, sms, s);
+    if (e == cudaSuccess) e = launch_tc_pass(shadow, v, R, (const float*)Q, (float*)ypart, spart, err, gx, s);
+  }
+  if (e == cudaSuccess)
+    e = launch_reduce_rows(TALS_F32, ypart, gx, v.I, R, Y_out, 0, nullptr, nullptr, rp, nullptr, 0,
+                           0, nullptr, nullptr, s);
+  std::vector<double> sp(nsp);
+  int herr = 0;
+  if (e == cudaSuccess && nsp > 0)
+    e = cudaMemcpyAsync(sp.data(), spart, nsp * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && err) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (void* p : {(void*)ypart, (void*)spart, shadow, (void*)err})
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep pass");
+  if (herr) return fail(TALS_ETIMEOUT, "tensor-core pass gave up waiting");
+  double t = 0.0;
+  for (double x : sp) t += x;
+  if (wnorm2) *wnorm2 = t;
+  return TALS_OK;
+}

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
   __shared__ int fail;
   const int tid = threadIdx.x;
 
-  if (op == 1) {
+  if (op == 1 || op == 2) {
     // Eq. 5.01 on e_k^2 = ||B_(n)||^2 - ||W||^2 (W = B^T Q_k is the LS optimum for Q_k),
     // plus tr((Q'^T Q' - I) X), the first-order term of the projector onto the
     // rounded basis Q' actually used, X = Q^T B B^T Q' (the cross Gram below)
@@ -128,15 +128,28 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       }
     const double corr = block_sum(c, red);
     if (tid == 0) {
-      st->corr = st->resid ? 0.0 : corr;
-      const double e2 = st->resid ? st->sW : st->normM2 - st->sW + corr;
+      const bool rs = st->resid && op == 1;
+      st->corr = rs ? 0.0 : corr;
+      const double e2 = rs ? st->sW : st->normM2 - st->sW + corr;
       const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
       const int k = st->k;
       const double norm_a = sqrt(*norm_a2);
       int s = 0;
-      if (k >= 1 && fabs(st->e_prev - e) <= st->eta * norm_a) {
-        s = 1;
-        st->converged = 1;
+      if (op == 2) {
+        // mixed-precision bulk phase: leave it once the BF16 error estimate stops
+        // moving at BF16 resolution (or after bulk_max sweeps); never ends the mode
+        const bool flat = k >= 1 && fabs(st->e_prev - e) <= fmax(st->eta * norm_a, 0.0039 * e);
+        if (flat || st->bulk + 1 >= st->bulk_max) {
+          st->bulk_mode = 0;
+          st->kf = 0;
+        }
+        st->bulk += 1;
+      } else {
+        if (st->kf >= 1 && fabs(st->e_prev - e) <= st->eta * norm_a) {
+          s = 1;
+          st->converged = 1;
+        }
+        st->kf += 1;
       }
       if (k + 1 >= st->max_sweeps) s = 1;
       st->e_prev = e;
@@ -327,16 +340,20 @@ cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
   return cudaGetLastError();
 }
 
-__global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int resid) {
+__global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int resid,
+                                  int bulk_max) {
   ModeState z = {};
   z.eta = eta;
   z.max_sweeps = max_sweeps;
   z.resid = resid;
+  z.bulk_mode = bulk_max > 0 ? 1 : 0;
+  z.bulk_max = bulk_max;
   *st = z;
 }
 
-cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s) {
-  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid);
+cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
+                              int bulk_max) {
+  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max);
   return cudaGetLastError();
 }
 
