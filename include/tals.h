@@ -206,6 +206,26 @@ tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, doubl
 tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mode, const void* Q,
                             int R, int engine, double* Y_out, double* wnorm2, void* stream);
 
+/* The paper has no counterpart to this entry point; it serves callers that cannot
+ * allocate device memory at call time -- for example code running while a memory
+ * pool or a framework's caching allocator owns the device memory, or a
+ * latency-critical loop that cannot pay for an allocation. It computes exactly
+ * what tals_sweep_pass with engine 0 computes (FP32 tensor A, FP32 basis Q,
+ * Y_out = B B^T Q as FP64 I_mode x R, device), except that the sum ||B^T Q||^2 is
+ * written to *wnorm2_out, a DEVICE double, and nothing is synchronised.
+ * It allocates nothing: its scratch (the per-CTA partial sums) is one fixed array
+ * of 4 MiB + 8 KiB in device global memory, defined in the library and held by
+ * every GPU that loads the library until the process exits. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on each device before any stream capture. Limit: I_mode x R <= 2^20
+ * (larger shapes return TALS_EINVAL); the pass uses fewer CTAs when their partials
+ * would not fit. All calls share the one array: calls whose work overlaps on the
+ * GPU (two streams, or two host threads) race and must be serialised by the
+ * caller. Nothing in the array carries over from one call to the next. */
+tals_status tals_sweep_pass_noalloc(const void* A, int ndim, const int64_t* dims, int mode,
+                                    const void* Q, int R, double* Y_out, double* wnorm2_out,
+                                    void* stream);
+
 /* Free a context (its workspace, graphs and owned buffers). NULL is allowed. */
 void tals_destroy(tals_ctx* ctx);
 

@@ -87,6 +87,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "tals_sweep_pass": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP, ctypes.c_int,
                                        ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+    "tals_sweep_pass_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP,
+                                               ctypes.c_int, _VP, _VP, _VP]),
     "tals_destroy": (None, [_VP]),
     "tals_last_error": (ctypes.c_char_p, []),
     "tals_version": (ctypes.c_char_p, []),
