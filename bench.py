@@ -272,24 +272,35 @@ def main():
     peaks, peak_kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-    # the pass runs on CUDA cores: 152 SMs x 128 FP32 FMA x 2 flops x SM clock
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak_tflops = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
     achieved_tflops = pass_flops / (pass_ms * 1e-3) / 1e12
-    bound_alu = achieved_tflops / alu_peak_tflops > achieved_gbs / hbm
+    if args.precision == "native":
+        # CUDA-core pass: 152 SMs x 128 FP32 FMA x 2 flops x SM clock
+        comp_kind, comp_peak = "alu", sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+        comp_src = "FP32 FMA peak from SM count x median SM clock"
+    else:
+        # tensor-core pass (BF16): the measured dense BF16 burst peak
+        comp_kind, comp_peak = "tensor", float(peaks.get("bf16_tflops", 1900.0))
+        comp_src = "dense BF16 burst peak"
+    comp_frac = achieved_tflops / comp_peak
+    hbm_frac = achieved_gbs / hbm
+    bound_comp = comp_frac > hbm_frac
     roofline = {
-        "bound": "alu" if bound_alu else "hbm",
-        "achieved": round(achieved_tflops if bound_alu else achieved_gbs, 2),
-        "peak": round(alu_peak_tflops if bound_alu else hbm, 2),
-        "unit": "TFLOP/s" if bound_alu else "GB/s",
-        "frac": round((achieved_tflops / alu_peak_tflops) if bound_alu else (achieved_gbs / hbm), 4),
+        "bound": comp_kind if bound_comp else "hbm",
+        "achieved": round(achieved_tflops if bound_comp else achieved_gbs, 2),
+        "peak": round(comp_peak if bound_comp else hbm, 2),
+        "unit": "TFLOP/s" if bound_comp else "GB/s",
+        "frac": round(comp_frac if bound_comp else hbm_frac, 4),
         "traffic": None,
-        "kernel": "tals::pass_kernel<float,32,4,16> (sweep, mode-1 view 1 x 512 x 262144)",
+        "kernel": ("tals::pass_kernel<float,32,2,16,512> (CUDA-core FP32 sweep" if args.precision == "native"
+                   else "tals::tc_pass_kernel<32> (tcgen05 BF16 sweep") + ", mode-1 view 1 x 512 x 262144)",
         "hbm_gbs_achieved": round(achieved_gbs, 1),
-        "hbm_frac": round(achieved_gbs / hbm, 4),
+        "hbm_frac": round(hbm_frac, 4),
+        "compute_tflops_achieved": round(achieved_tflops, 2),
+        "compute_frac": round(comp_frac, 4),
         "pass_ms": round(pass_ms, 4),
-        "peak_source": f"{peak_kind} (HBM {hbm} GB/s; FP32 FMA peak from SM count x clock)",
+        "peak_source": f"{peak_kind} HBM {hbm} GB/s (of measured); {comp_src}",
     }
     # kernels per step: per mode 10 (initial guess chain) + 9 per sweep
     launches = sum(10 + 9 * s for s in st["sweeps"])

@@ -667,6 +667,8 @@ tals_status tals_time_pass(tals_ctx* c, int mode, int iters, double* ms, double*
   j.X = c->A;
   tals_status st = mode_setup(c, j);
   if (st != TALS_OK) return st;
+  if (c->mixed && c->dtype == TALS_F32 && tc_supported(j.v, j.R))
+    return time_tc_pass(c, j, iters, ms, bytes, flops);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

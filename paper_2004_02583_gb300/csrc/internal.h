@@ -54,6 +54,8 @@ void graphs_destroy(tals_ctx* c);
 tals_status mixed_alloc(tals_ctx* c);
 void mixed_free(tals_ctx* c);
 tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a);
+tals_status time_tc_pass(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes,
+                         double* flops);
 
 }  // namespace tals
 

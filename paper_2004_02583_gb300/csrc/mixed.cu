@@ -87,6 +87,38 @@ tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   return read_states(c);
 }
 
+tals_status time_tc_pass(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes,
+                         double* flops) {
+  cudaStream_t s = c->stream;
+  int grid = std::min<int>(c->sms, (int)((j.v.J() + 127) / 128));
+  grid = (int)std::min<size_t>((size_t)grid, c->ypart_elems / ((size_t)j.v.I * j.R));
+  grid = (int)std::min<size_t>((size_t)grid, c->spart_n);
+  cudaError_t e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems,
+                                 c->sms, s);
+  if (e == cudaSuccess)
+    e = launch_tc_pass(c->mixed->shadow, j.v, j.R, (const float*)c->Lt, (float*)c->Ypart, c->spart,
+                       c->mixed->err, grid, s);   // warm-up
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  for (int i = 0; i < iters && e == cudaSuccess; ++i)
+    e = launch_tc_pass(c->mixed->shadow, j.v, j.R, (const float*)c->Lt, (float*)c->Ypart, c->spart,
+                       c->mixed->err, grid, s);
+  cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "timed tensor-core pass");
+  const double T = (double)j.v.P * j.v.I * j.v.Q;
+  if (ms) *ms = t / iters;
+  if (bytes) *bytes = T * 2.0;   // one read of the BF16 copy
+  if (flops) *flops = 4.0 * j.R * T;
+  return TALS_OK;
+}
+
 }  // namespace tals
 
 using namespace tals;
