@@ -32,6 +32,7 @@ struct ModeState {
   int kf;             // sweeps of the current (final-precision) phase
   int bulk_max;       // at most this many bulk sweeps
   int pad2;
+  double sw_prev;     // ||W||^2 of the previous bulk sweep
 };
 
 // splitmix64 output number c of the stream seeded with `state`:

@@ -136,9 +136,12 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       const double norm_a = sqrt(*norm_a2);
       int s = 0;
       if (op == 2) {
-        // mixed-precision bulk phase: leave it once the BF16 error estimate stops
-        // moving at BF16 resolution (or after bulk_max sweeps); never ends the mode
-        const bool flat = k >= 1 && fabs(st->e_prev - e) <= fmax(st->eta * norm_a, 0.0039 * e);
+        // mixed-precision bulk phase: e from ||B||^2 - ||W||^2 is below BF16
+        // resolution, so leave the phase once ||W||^2 = tr(Q^T B B^T Q) stops moving
+        // at BF16 resolution (2^-9 relative), or after bulk_max sweeps; the stop
+        // rule itself is only taken on the FP32 sweeps that follow
+        const bool flat = st->bulk >= 1 && fabs(st->sW - st->sw_prev) <= 0.001953125 * st->sW;
+        st->sw_prev = st->sW;
         if (flat || st->bulk + 1 >= st->bulk_max) {
           st->bulk_mode = 0;
           st->kf = 0;
@@ -197,8 +200,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       }
     }
     __syncthreads();
-    const double dk = G[k * R + k];
-    for (int i = k + 1 + tid; i < R; i += kSmallThreads) G[i * R + k] /= dk;
+    const double rk = 1.0 / G[k * R + k];
+    for (int i = k + 1 + tid; i < R; i += kSmallThreads) G[i * R + k] *= rk;
     __syncthreads();
     const int m = R - k - 1;
     for (int o = tid; o < m * m; o += kSmallThreads) {
@@ -234,7 +237,10 @@ cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F, 
 }
 
 // ---------------------------------------------------------------------------
-// Row-wise triangular solves: one thread per row, F in shared memory.
+// Row-wise triangular solves: one warp per row, lane j owns columns j and j+32
+// (R <= 64). Each solved entry is broadcast with a shuffle and every lane
+// updates its own running sums, so the dependent chain per row is R short steps
+// (no per-thread R^2 chain). Pivot reciprocals are taken once per block.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int R,
@@ -244,36 +250,70 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
   if (st != nullptr && st->done) return;
   extern __shared__ double sh[];
   double* Fs = sh;                                   // [R][R]
-  double* Os = sh + (size_t)R * R;                   // [rows_per_block][R]
+  double* dinv = sh + (size_t)R * R;                 // [R]
+  double* Os = dinv + R;                             // [rows_per_block][R]
   for (int o = threadIdx.x; o < R * R; o += blockDim.x) Fs[o] = F[o];
+  for (int r = threadIdx.x; r < R; r += blockDim.x) dinv[r] = 1.0 / F[r * R + r];
   __syncthreads();
   const long long row0 = (long long)blockIdx.x * rows_per_block;
   const int nrows = (int)min((long long)rows_per_block, I - row0);
-  for (int lr = threadIdx.x; lr < nrows; lr += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int j0 = lane, j1 = lane + 32;
+  for (int lr = warp; lr < nrows; lr += nwarp) {
     const long long i = row0 + lr;
-    double* x = Os + (size_t)lr * R;
-    for (int r = 0; r < R; ++r) x[r] = In[i * R + r];
-    // forward: x F^T = b  <=>  F x^T = b^T
+    double b0 = j0 < R ? In[i * R + j0] : 0.0, b1 = j1 < R ? In[i * R + j1] : 0.0;
+    double a0 = 0.0, a1 = 0.0;   // running sums of the solve
+    double x0 = 0.0, x1 = 0.0;   // solved entries owned by this lane
+    // forward: F x^T = b^T, x_r = (b_r - sum_{c<r} F[r][c] x_c) / F[r][r]
     for (int r = 0; r < R; ++r) {
-      double s = x[r];
-      for (int c = 0; c < r; ++c) s = fma(-Fs[r * R + c], x[c], s);
-      x[r] = s / Fs[r * R + r];
+      const int owner = r & 31;
+      double v = 0.0;
+      if (lane == owner) v = ((r < 32 ? b0 : b1) - (r < 32 ? a0 : a1)) * dinv[r];
+      v = __shfl_sync(0xffffffffu, v, owner);
+      if (lane == owner) {
+        if (r < 32) x0 = v; else x1 = v;
+      }
+      if (j0 > r && j0 < R) a0 = fma(Fs[j0 * R + r], v, a0);
+      if (j1 > r && j1 < R) a1 = fma(Fs[j1 * R + r], v, a1);
     }
     if (op == 1) {
-      // backward: z F = a  <=>  F^T z^T = a^T
+      // backward: F^T z^T = x^T, z_r = (x_r - sum_{c>r} F[c][r] z_c) / F[r][r]
+      b0 = x0;
+      b1 = x1;
+      a0 = 0.0;
+      a1 = 0.0;
       for (int r = R - 1; r >= 0; --r) {
-        double s = x[r];
-        for (int c = r + 1; c < R; ++c) s = fma(-Fs[c * R + r], x[c], s);
-        x[r] = s / Fs[r * R + r];
+        const int owner = r & 31;
+        double v = 0.0;
+        if (lane == owner) v = ((r < 32 ? b0 : b1) - (r < 32 ? a0 : a1)) * dinv[r];
+        v = __shfl_sync(0xffffffffu, v, owner);
+        if (lane == owner) {
+          if (r < 32) x0 = v; else x1 = v;
+        }
+        if (j0 < r) a0 = fma(Fs[r * R + j0], v, a0);
+        if (j1 < r && j1 < R) a1 = fma(Fs[r * R + j1], v, a1);
       }
     }
-    for (int r = 0; r < R; ++r) {
-      Out[i * R + r] = x[r];
+    double* xs = Os + (size_t)lr * R;
+    if (j0 < R) {
+      Out[i * R + j0] = x0;
+      double g = x0;
       if (OutT != nullptr) {
-        const T v = (T)x[r];
-        OutT[i * R + r] = v;
-        if (gram_rounded) x[r] = (double)v;   // the Gram below is of the stored basis
+        const T q = (T)x0;
+        OutT[i * R + j0] = q;
+        if (gram_rounded) g = (double)q;   // the Gram below is of the stored basis
       }
+      xs[j0] = g;
+    }
+    if (j1 < R) {
+      Out[i * R + j1] = x1;
+      double g = x1;
+      if (OutT != nullptr) {
+        const T q = (T)x1;
+        OutT[i * R + j1] = q;
+        if (gram_rounded) g = (double)q;
+      }
+      xs[j1] = g;
     }
   }
   if (Gpart != nullptr) {
@@ -281,9 +321,14 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
     double* gp = Gpart + (size_t)blockIdx.x * R * R;
     for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
       const int r = o / R, c = o % R;
-      double g = 0.0;
-      for (int k = 0; k < nrows; ++k) g = fma(Os[k * R + r], Os[k * R + c], g);
-      gp[o] = g;
+      double g0 = 0.0, g1 = 0.0;
+      int k = 0;
+      for (; k + 1 < nrows; k += 2) {
+        g0 = fma(Os[k * R + r], Os[k * R + c], g0);
+        g1 = fma(Os[(k + 1) * R + r], Os[(k + 1) * R + c], g1);
+      }
+      if (k < nrows) g0 = fma(Os[k * R + r], Os[k * R + c], g0);
+      gp[o] = g0 + g1;
     }
   }
 }
@@ -291,8 +336,9 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
 cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, const double* F,
                              int op, double* Out, void* OutT, double* Gpart, const RowPlan& rp,
                              const ModeState* st, cudaStream_t s, int gram_rounded) {
-  const size_t sm = ((size_t)R * R + (size_t)rp.rows_per_block * R) * sizeof(double);
-  const int threads = rp.rows_per_block <= 32 ? 32 : (rp.rows_per_block <= 64 ? 64 : 128);
+  if (R > 64) return cudaErrorInvalidValue;
+  const size_t sm = ((size_t)R * R + R + (size_t)rp.rows_per_block * R) * sizeof(double);
+  const int threads = 32 * std::max(1, std::min(8, rp.rows_per_block));
   if (dtype == 1) {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(row_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

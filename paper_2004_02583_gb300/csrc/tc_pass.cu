@@ -150,37 +150,73 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int kcol) {
 
 }  // namespace
 
+// Clock-bounded wait (about two seconds); gives up early when another role of
+// the CTA has already failed.
+__device__ __forceinline__ bool mbar_wait_b(uint32_t mbar, uint32_t parity, volatile int* fail) {
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(mbar, parity)) return true;
+    if (*fail) return false;
+    if (clock64() - t0 > (4ll << 30)) {
+      *fail = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Warp-specialised, pipelined pass. Warps 0-3 drain TMEM (W conversion, final Y),
+// warp 4 lane 0 issues TMA, warp 5 lane 0 issues MMAs. The chunk stream is
+// A(0), A(1), B(0), A(2), B(1), ..., B(last): A(t) feeds GEMM1 of tile t, B(t)
+// (the same chunks again, now from L2) feeds GEMM2 of tile t, so GEMM1 of the
+// next tile runs while the epilogue converts the current W.
+constexpr int kTcThreads2 = 192;
+constexpr int kMaxSlots = 8;
+
 template <int RP>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads2, 1)
+    tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a, int nslots) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-up: [4 chunks][Q operand][W operand][barriers]
   unsigned char* base = smem_raw;
-  const uint32_t b0 = su32(base);
-  const uint32_t pad = (1024u - (b0 & 1023u)) & 1023u;
-  base += pad;
+  base += (1024u - (su32(base) & 1023u)) & 1023u;
   const int nchunk = a.I / kTcRows;
-  unsigned char* chunks = base;                                    // nchunk x 32 KiB
-  unsigned char* qop = chunks + (size_t)nchunk * kChunkBytes;     // (I/64) x RP x 128 B
-  unsigned char* wop = qop + (size_t)(a.I / 64) * RP * 128;        // 2 x RP x 128 B
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wop + 2 * RP * 128);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4);
+  unsigned char* ring = base;                                           // nslots x 32 KiB
+  unsigned char* qop = ring + (size_t)nslots * kChunkBytes;            // (I/64) x RP x 128 B
+  unsigned char* wop = qop + (size_t)(a.I / 64) * RP * 128;             // 2 buffers x (2 x RP x 128 B)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wop + 4 * RP * 128);
+  uint64_t* full = bars;                     // [kMaxSlots]
+  uint64_t* empty = bars + kMaxSlots;        // [kMaxSlots]
+  uint64_t* wfull = bars + 2 * kMaxSlots;    // [2] GEMM1 done -> W in TMEM buffer
+  uint64_t* wfree = wfull + 2;               // [2] epilogue read the TMEM W buffer
+  uint64_t* opfull = wfree + 2;              // [2] bf16 W operand written
+  uint64_t* opfree = opfull + 2;             // [2] GEMM2 done reading the operand
+  uint64_t* ydone = opfree + 2;              // [1] all MMAs done
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(ydone + 1);
   __shared__ double red[32];
   __shared__ int s_fail;
-  __shared__ uint32_t s_pend_bar, s_pend_par;   // barrier phase outstanding after a timeout
+  volatile int* vfail = &s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_tma = su32(&bars[0]), bar_g1 = su32(&bars[1]), bar_g2 = su32(&bars[2]);
+  const long long nt = a.ntiles > blockIdx.x ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   if (tid == 0) {
-    mbar_init(bar_tma, 1);
-    mbar_init(bar_g1, 1);
-    mbar_init(bar_g2, 1);
+    for (int k = 0; k < nslots; ++k) {
+      mbar_init(su32(&full[k]), 1);
+      mbar_init(su32(&empty[k]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(su32(&wfull[b]), 1);
+      mbar_init(su32(&wfree[b]), 128);
+      mbar_init(su32(&opfull[b]), 128);
+      mbar_init(su32(&opfree[b]), 1);
+    }
+    mbar_init(su32(ydone), 1);
     s_fail = 0;
-    s_pend_bar = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // tensor memory: W (RP columns) + Y (nchunk x RP columns), power of two >= 32
-  const uint32_t need = (uint32_t)(RP + nchunk * RP);
+  const uint32_t need = (uint32_t)(2 * RP + nchunk * RP);
   uint32_t ncols = 32;
   while (ncols < need) ncols <<= 1;
   if (warp == 0) {
@@ -189,146 +225,184 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // Q operand (B of GEMM1: n = r, k = i), K-major, 128B swizzle, bf16
-  for (int e = tid; e < a.I * RP; e += kTcThreads) {
+  for (int e = tid; e < a.I * RP; e += kTcThreads2) {
     const int i = e / RP, r = e % RP;
     const float v = r < a.R ? a.L[(size_t)i * a.R + r] : 0.f;
-    const int katom = i >> 6;
-    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(qop + (size_t)katom * RP * 128 +
-                                                          sw128_off(r, i & 63));
-    *dst = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(qop + (size_t)(i >> 6) * RP * 128 + sw128_off(r, i & 63)) =
+        __float2bfloat16_rn(v);
   }
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_holder;
-  const uint32_t t_w = tmem;                 // W: columns [0, RP)
-  const uint32_t t_y = tmem + RP;            // Y chunk c: columns [RP + c*RP, ...)
-  constexpr uint32_t kIdesc = idesc_bf16(128, RP, 0, 0);
-  constexpr uint32_t kIdescMN = idesc_bf16(128, RP, 1, 0);
+  const uint32_t t_w0 = tmem, t_y = tmem + 2 * RP;   // W buffers at 0 and RP; Y chunks after
   double wsq = 0.0;
-  uint32_t ph_tma = 0, ph_g1 = 0, ph_g2 = 0;
-  int first = 1;
 
-  for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const long long j0 = t * kTcCols;
-    const long long p = j0 / a.Q, q0 = j0 - p * a.Q;
-    // ---- TMA: the tile's nchunk chunks, two 64-column boxes each ----
-    if (tid == 0 && !s_fail) {
-      mbar_expect_tx(bar_tma, (uint32_t)(nchunk * kChunkBytes));
-      for (int c = 0; c < nchunk; ++c)
-        for (int h = 0; h < 2; ++h)
-          tma_load_3d(su32(chunks + (size_t)c * kChunkBytes + h * kHalfBytes), &tmap, bar_tma,
-                      (int)(q0 + h * 64), c * kTcRows, (int)p);
-    }
-    if (!mbar_wait(bar_tma, ph_tma) && tid == 0) {
-      s_fail = 1;
-      s_pend_bar = bar_tma;
-      s_pend_par = ph_tma;
-    }
-    ph_tma ^= 1;
-    // ---- GEMM1: W = B_t^T Q (M = 128 columns, K = I) ----
-    if (tid == 0 && !s_fail) {
-      fence_after();
-      for (int c = 0; c < nchunk; ++c)
-        for (int ks = 0; ks < kTcRows / 16; ++ks) {
-          const uint32_t a_addr = su32(chunks + (size_t)c * kChunkBytes) + ks * 16 * 128;
-          const uint64_t ad = desc_sw128(a_addr, kHalfBytes, 1024);   // MN-major: LBO = next 64 columns
-          const int k = c * kTcRows + ks * 16;                          // global i
-          const uint32_t b_addr = su32(qop) + (uint32_t)((k >> 6) * RP * 128 + ((k & 63) >> 4) * 32);
-          const uint64_t bd = desc_sw128(b_addr, 16, 1024);
-          mma_bf16(t_w, ad, bd, kIdescMN, (c | ks) ? 1u : 0u);
-        }
-      mma_commit(bar_g1);
-    }
-    __syncthreads();
-    if (!mbar_wait(bar_g1, ph_g1) && tid == 0) {
-      s_fail = 1;
-      s_pend_bar = bar_g1;
-      s_pend_par = ph_g1;
-    }
-    ph_g1 ^= 1;
-    fence_after();
-    // ---- W: TMEM -> registers -> bf16 K-major operand (n = r, k = column) ----
-    {
-      const int col = warp * 32 + lane;   // this thread's tile column (TMEM lane)
-      const bool valid = j0 + col < a.J;
-#pragma unroll
-      for (int rb = 0; rb < RP; rb += 32) {
-        float v[32];
-        tmem_ld32(t_w + ((uint32_t)(warp * 32) << 16) + rb, v);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int r = rb + k;
-          if (r >= RP) break;
-          const float w = (valid && r < a.R) ? v[k] : 0.f;
-          wsq += (double)w * w;
-          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(
-              wop + (size_t)(col >> 6) * RP * 128 + sw128_off(r, col & 63));
-          *dst = __float2bfloat16_rn(w);
+  if (warp == 4) {
+    // ---------------- producer (whole warp waits, lane 0 issues) ----------------
+    int slot = 0;
+    uint32_t ph = 0;
+    for (long long step = 0; step <= nt && !*vfail; ++step) {
+      for (int kind = 0; kind < 2 && !*vfail; ++kind) {   // kind 0: A(step), 1: B(step-1)
+        const long long lt = kind == 0 ? step : step - 1;
+        if (lt < 0 || lt >= nt) continue;
+        const long long j0 = (blockIdx.x + lt * gridDim.x) * kTcCols;
+        const long long p = j0 / a.Q, q0 = j0 - p * a.Q;
+        for (int c = 0; c < nchunk; ++c) {
+          if (!mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail)) break;
+          if (lane == 0) {
+            mbar_expect_tx(su32(&full[slot]), (uint32_t)kChunkBytes);
+            for (int h = 0; h < 2; ++h)
+              tma_load_3d(su32(ring + (size_t)slot * kChunkBytes + h * kHalfBytes), &tmap,
+                          su32(&full[slot]), (int)(q0 + h * 64), c * kTcRows, (int)p);
+          }
+          __syncwarp();
+          if (++slot == nslots) {
+            slot = 0;
+            ph ^= 1u;
+          }
         }
       }
     }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    // ---- GEMM2: Y += B_t W (M = 128 rows per chunk, K = 128 columns) ----
-    if (tid == 0 && !s_fail) {
-      fence_after();
-      for (int c = 0; c < nchunk; ++c)
-        for (int ks = 0; ks < kTcCols / 16; ++ks) {
-          const uint32_t a_addr = su32(chunks + (size_t)c * kChunkBytes) + (ks >> 2) * kHalfBytes +
-                                  (ks & 3) * 32;
-          const uint64_t ad = desc_sw128(a_addr, 16, 1024);
-          const uint32_t b_addr = su32(wop) + (ks >> 2) * RP * 128 + (ks & 3) * 32;
-          const uint64_t bd = desc_sw128(b_addr, 16, 1024);
-          mma_bf16(t_y + c * RP, ad, bd, kIdesc, (first && ks == 0) ? 0u : 1u);
-        }
-      mma_commit(bar_g2);
-    }
-    __syncthreads();
-    if (!mbar_wait(bar_g2, ph_g2) && tid == 0) {
-      s_fail = 1;
-      s_pend_bar = bar_g2;
-      s_pend_par = ph_g2;
-    }
-    ph_g2 ^= 1;
-    fence_after();
-    first = 0;
-    __syncthreads();
-    if (s_fail) break;
-  }
-
-  // ---- Y partial: TMEM -> FP32 Ypart[bx][i][r] ----
-  if (!s_fail && !first) {
-    float* yp = a.Ypart + (size_t)blockIdx.x * a.I * a.R;
-    for (int c = 0; c < nchunk; ++c) {
-      const int i = c * kTcRows + warp * 32 + lane;
-#pragma unroll
-      for (int rb = 0; rb < RP; rb += 32) {
-        float v[32];
-        tmem_ld32(t_y + c * RP + ((uint32_t)(warp * 32) << 16) + rb, v);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int r = rb + k;
-          if (r < a.R) yp[(size_t)i * a.R + r] = v[k];
+  } else if (warp == 5) {
+    // ---------------- MMA issuer (whole warp waits, lane 0 issues) ----------------
+    constexpr uint32_t kIdesc = idesc_bf16(128, RP, 0, 0);
+    constexpr uint32_t kIdescMN = idesc_bf16(128, RP, 1, 0);
+    int slot = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (long long step = 0; step <= nt && ok; ++step) {
+      for (int kind = 0; kind < 2 && ok; ++kind) {
+        const long long lt = kind == 0 ? step : step - 1;
+        if (lt < 0 || lt >= nt) continue;
+        const int wb = (int)(lt & 1);
+        const uint32_t use = (uint32_t)(lt >> 1);
+        if (kind == 0) {
+          // GEMM1(lt) into TMEM W buffer wb, once the epilogue of lt-2 has read it
+          if (lt >= 2) ok = mbar_wait_b(su32(&wfree[wb]), (use - 1) & 1u, vfail);
+          fence_after();
+          for (int c = 0; c < nchunk && ok; ++c) {
+            ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+            if (!ok) break;
+            fence_after();
+            if (lane == 0) {
+              const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
+              for (int ks = 0; ks < kTcRows / 16; ++ks) {
+                const uint64_t ad = desc_sw128(abase + ks * 16 * 128, kHalfBytes, 1024);
+                const int k = c * kTcRows + ks * 16;
+                const uint64_t bd = desc_sw128(
+                    su32(qop) + (uint32_t)((k >> 6) * RP * 128 + ((k & 63) >> 4) * 32), 16, 1024);
+                mma_bf16(t_w0 + wb * RP, ad, bd, kIdescMN, (c | ks) ? 1u : 0u);
+              }
+              mma_commit(su32(&empty[slot]));
+            }
+            __syncwarp();
+            if (++slot == nslots) {
+              slot = 0;
+              ph ^= 1u;
+            }
+          }
+          if (ok && lane == 0) mma_commit(su32(&wfull[wb]));
+          __syncwarp();
+        } else {
+          // GEMM2(lt): Y += B_t W_t, once the epilogue has written the bf16 W operand
+          ok = mbar_wait_b(su32(&opfull[wb]), use & 1u, vfail);
+          fence_after();
+          unsigned char* wopb = wop + (size_t)wb * 2 * RP * 128;
+          for (int c = 0; c < nchunk && ok; ++c) {
+            ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+            if (!ok) break;
+            fence_after();
+            if (lane == 0) {
+              const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
+              for (int ks = 0; ks < kTcCols / 16; ++ks) {
+                const uint64_t ad =
+                    desc_sw128(abase + (ks >> 2) * kHalfBytes + (ks & 3) * 32, 16, 1024);
+                const uint64_t bd =
+                    desc_sw128(su32(wopb) + (ks >> 2) * RP * 128 + (ks & 3) * 32, 16, 1024);
+                mma_bf16(t_y + c * RP, ad, bd, kIdesc, (lt == 0 && ks == 0) ? 0u : 1u);
+              }
+              mma_commit(su32(&empty[slot]));
+            }
+            __syncwarp();
+            if (++slot == nslots) {
+              slot = 0;
+              ph ^= 1u;
+            }
+          }
+          if (ok && lane == 0) mma_commit(su32(&opfree[wb]));
+          __syncwarp();
         }
       }
     }
-  } else if (first) {
-    // no tile: the partial is zero
+    if (lane == 0) mma_commit(su32(ydone));   // completes once every MMA issued above has finished
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 0-3 (TMEM lanes 0-127) ----------------
+    const int col = warp * 32 + lane;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const int wb = (int)(lt & 1);
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ok = mbar_wait_b(su32(&wfull[wb]), use & 1u, vfail);
+      if (!ok) break;
+      fence_after();
+      float v[RP];
+#pragma unroll
+      for (int rb = 0; rb < RP; rb += 32) {
+        float t32[32];
+        tmem_ld32(t_w0 + wb * RP + ((uint32_t)(warp * 32) << 16) + rb, t32);
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (rb + k < RP) v[rb + k] = t32[k];
+      }
+      fence_before();
+      mbar_arrive(su32(&wfree[wb]));
+      if (lt >= 2) ok = mbar_wait_b(su32(&opfree[wb]), (use - 1) & 1u, vfail);
+      if (!ok) break;
+      unsigned char* wopb = wop + (size_t)wb * 2 * RP * 128;
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        const float w = r < a.R ? v[r] : 0.f;
+        wsq += (double)w * w;
+        *reinterpret_cast<__nv_bfloat16*>(wopb + (size_t)(col >> 6) * RP * 128 + sw128_off(r, col & 63)) =
+            __float2bfloat16_rn(w);
+      }
+      fence_async_smem();
+      mbar_arrive(su32(&opfull[wb]));
+    }
+    // final Y: wait for every MMA, then TMEM -> FP32 partials
     float* yp = a.Ypart + (size_t)blockIdx.x * a.I * a.R;
-    for (int e = tid; e < a.I * a.R; e += kTcThreads) yp[e] = 0.f;
+    if (ok && nt > 0 && mbar_wait_b(su32(ydone), 0u, vfail)) {
+      fence_after();
+      for (int c = 0; c < nchunk; ++c) {
+        const int i = c * kTcRows + warp * 32 + lane;
+#pragma unroll
+        for (int rb = 0; rb < RP; rb += 32) {
+          float t32[32];
+          tmem_ld32(t_y + c * RP + ((uint32_t)(warp * 32) << 16) + rb, t32);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int r = rb + k;
+            if (r < a.R) yp[(size_t)i * a.R + r] = t32[k];
+          }
+        }
+      }
+    } else if (nt == 0) {
+      for (int e = tid; e < a.I * a.R; e += 128) yp[e] = 0.f;
+    }
   }
   const double tot = block_sum(wsq, red);
   if (tid == 0) {
     a.spart[blockIdx.x] = tot;
-    if (s_fail) {
-      atomicExch(a.err, 5);   // TALS_ETIMEOUT
-      // let the copy or MMA group that timed out finish (bounded) before the
-      // shared and tensor memory it targets is released
-      if (s_pend_bar) mbar_wait(s_pend_bar, s_pend_par);
+    if (*vfail) atomicExch(a.err, 5);   // TALS_ETIMEOUT
+  }
+  // nothing may still write the shared or tensor memory released below: after a
+  // failure, wait (bounded) for the MMA group and the copies issued so far
+  if (*vfail && tid == 160) {
+    const long long t0 = clock64();
+    while (!mbar_try(su32(ydone), 0u) && clock64() - t0 < (1ll << 30)) {
     }
   }
   fence_before();
@@ -341,13 +415,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Host side
 // ---------------------------------------------------------------------------
 
+int tc_slots(long long I, int RP);
+
 bool tc_supported(const ModeView& v, int R) {
-  return v.I % kTcRows == 0 && v.I <= 512 && v.Q % kTcCols == 0 && R >= 1 && R <= 64;
+  return v.I % kTcRows == 0 && v.I <= 512 && v.Q % kTcCols == 0 && R >= 1 && R <= 64 &&
+         tc_slots(v.I, ((R + 15) / 16) * 16) >= 2;
 }
 
-size_t tc_smem_bytes(long long I, int RP) {
-  return 1024 + (size_t)(I / kTcRows) * kChunkBytes + (size_t)(I / 64) * RP * 128 +
-         2 * (size_t)RP * 128 + 64;
+size_t tc_smem_bytes(long long I, int RP, int nslots) {
+  return 1024 + (size_t)nslots * kChunkBytes + (size_t)(I / 64) * RP * 128 + 4 * (size_t)RP * 128 +
+         (2 * kMaxSlots + 9) * 8 + 16;
+}
+
+int tc_slots(long long I, int RP) {
+  const size_t fixed = 1024 + (size_t)(I / 64) * RP * 128 + 4 * (size_t)RP * 128 + 512;
+  const size_t cap = 227 * 1024 - 2048;   // dynamic smem budget (static smem: red + flag)
+  if (fixed >= cap) return 0;
+  return (int)std::min<size_t>(kMaxSlots, (cap - fixed) / kChunkBytes);
 }
 
 namespace {
@@ -404,7 +488,9 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
   a.Ypart = Ypart;
   a.spart = spart;
   a.err = err;
-  const size_t smem = tc_smem_bytes(v.I, RP);
+  const int nslots = tc_slots(v.I, RP);
+  if (nslots < 2) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(v.I, RP, nslots);
   void* fn = nullptr;
   switch (RP) {
     case 16: fn = (void*)&tc_pass_kernel<16>; break;
@@ -416,8 +502,8 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   grid = (int)std::min<long long>(grid, a.ntiles);
-  void* args[] = {&map, &a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads), args, smem, s);
+  void* args[] = {&map, &a, (void*)&nslots};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads2), args, smem, s);
 }
 
 // FP32 -> BF16 copy (round to nearest even), vectorised by 4.
