@@ -2,22 +2,26 @@
 // operands with FP32 accumulation in tensor memory.
 //
 // Same computation as the CUDA-core pass (Alg. 3 R-update and L-update fused
-// as in Eq. 2.2): per tile of 128 unfolding columns,
-//   GEMM1  W_t (128 x R) = B_t^T (128 x I) . Q (I x R)      -> TMEM, fp32
-//   GEMM2  Y   (I x R)  += B_t  (I x 128) . W_t (128 x R)   -> TMEM, fp32
+// as in Eq. 2.2): per tile of 64 unfolding columns,
+//   GEMM1  W_t (64 x R) = B_t^T (64 x I) . Q (I x R)      -> TMEM, fp32 (M = 64)
+//   GEMM2  Y   (I x R) += B_t  (I x 64) . W_t (64 x R)    -> TMEM, fp32 (M = 128)
 // B_t is a BF16 copy of the tensor, staged by TMA with 128-byte swizzle in
-// 128 x 128 chunks (two 64-column boxes). One staged chunk is read by GEMM1 as
-// an MN-major A operand (m = column, k = row i) and by GEMM2 as a K-major A
-// operand (m = row i, k = column): for 16-bit types the 128B-swizzled layout
-// with 128-byte rows is a canonical layout for both majors. W_t goes TMEM ->
-// registers -> BF16 -> shared memory (K-major, 128B swizzle) between the two
-// GEMMs; Y stays in TMEM across all the CTA's tiles and is written once as a
-// per-CTA FP32 partial, reduced in FP64 by the same kernel as the CUDA-core path.
+// 64-column x 128-row chunks (one box, 16 KiB). The staged chunk is read by
+// GEMM1 as an MN-major A operand (m = column, k = row i) and by GEMM2 as a
+// K-major A operand (m = row i, k = column): for 16-bit types the 128B-swizzled
+// layout with 128-byte rows is a canonical layout for both majors. A tile stays
+// in shared memory from its load until GEMM2 has used it, so the tensor crosses
+// HBM -> SM exactly once per sweep. W_t goes TMEM -> registers -> BF16 ->
+// shared memory (K-major, 128B swizzle) between the two GEMMs; Y stays in TMEM
+// across all the CTA's tiles and is written once as a per-CTA FP32 partial,
+// reduced in FP64 by the same kernel as the CUDA-core path.
 //
-// One thread issues every TMA load and every MMA; completion is tracked with
+// Warp-specialised: one producer warp issues the TMA loads, two MMA warps issue
+// the two GEMMs, four warps run the epilogue; completion is tracked with
 // mbarriers (tcgen05.commit for the MMAs). Every wait is bounded: on timeout
 // the CTA records an error code, stops issuing work, waits (again bounded) for
-// what it already issued and frees its tensor memory before it returns.
+// the copies and MMAs it already issued and frees its tensor memory before it
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -28,12 +32,9 @@
 
 namespace tals {
 
-constexpr int kTcCols = 128;     // unfolding columns per tile (GEMM1 M, GEMM2 K)
+constexpr int kTcCols = 64;      // unfolding columns per tile (GEMM1 M, GEMM2 K)
 constexpr int kTcRows = 128;     // rows i per staged chunk (GEMM1 K block, GEMM2 M)
-constexpr int kTcThreads = 128;  // one warpgroup: thread 0 issues, all four warps drain TMEM
-constexpr int kChunkBytes = kTcCols * kTcRows * 2;   // 32 KiB
-constexpr int kHalfBytes = kChunkBytes / 2;           // one 64-column box
-constexpr unsigned kWaitLimit = 1u << 26;
+constexpr int kChunkBytes = kTcCols * kTcRows * 2;   // 16 KiB, one TMA box
 
 struct TcArgs {
   int I, R, RP;                // R padded to RP (multiple of 16)
@@ -104,13 +105,6 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
-    if (mbar_try(mbar, parity)) return true;
-  return false;
-}
-
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
                                             int x, int y, int z) {
   asm volatile(
@@ -118,6 +112,19 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
       "l"(map), "r"(mbar), "r"(x), "r"(y), "r"(z)
       : "memory");
+}
+
+// 2D tensor store from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   map),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -142,12 +149,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Byte offset of element (row, col) in a K-major 128B-swizzled operand block
-// whose rows are 128 bytes (64 bf16 of K) and whose 8-row groups are 1024 B apart.
-__device__ __forceinline__ uint32_t sw128_off(int row, int kcol) {
-  return (uint32_t)(row * 128 + ((((kcol * 2) >> 4) ^ (row & 7)) << 4) + ((kcol * 2) & 15));
-}
-
 }  // namespace
 
 // Clock-bounded wait (about two seconds); gives up early when another role of
@@ -168,33 +169,40 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
-// Warp-specialised, pipelined pass. Warps 0-3 drain TMEM (W conversion, final Y),
-// warp 4 lane 0 issues TMA, warp 5 lane 0 issues MMAs. The chunk stream is
-// A(0), A(1), B(0), A(2), B(1), ..., B(last): A(t) feeds GEMM1 of tile t, B(t)
-// (the same chunks again, now from L2) feeds GEMM2 of tile t, so GEMM1 of the
-// next tile runs while the epilogue converts the current W.
-constexpr int kTcThreads2 = 192;
-constexpr int kMaxSlots = 8;
+// Warp roles (224 threads):
+//   warps 0-3  epilogue: W_t (TMEM) -> bf16 operand and ||W||^2; final Y
+//   warp 4     producer: TMA of tile t's chunks into the chunk ring
+//   warp 5     GEMM1 issuer (W_t into TMEM W buffer t % 2)
+//   warp 6     GEMM2 issuer (Y += B_t W_t); it releases the tile's ring slots
+// A ring slot is held from its load until GEMM2 has used it; the producer runs
+// ahead by whatever the ring holds beyond the tile waiting for GEMM2.
+// An M = 64 accumulator puts row m in TMEM lane (m / 16) * 32 + m % 16, so
+// lanes 0-15 of each epilogue warp hold W_t's rows.
+constexpr int kTcThreads = 224;
+constexpr int kMaxSlots = 16;
 
 template <int RP>
-__global__ void __launch_bounds__(kTcThreads2, 1)
-    tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a, int nslots) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap ymap,
+                   TcArgs a, int ns, int y_tma) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw;
   base += (1024u - (su32(base) & 1023u)) & 1023u;
   const int nchunk = a.I / kTcRows;
-  unsigned char* ring = base;                                           // nslots x 32 KiB
-  unsigned char* qop = ring + (size_t)nslots * kChunkBytes;            // (I/64) x RP x 128 B
-  unsigned char* wop = qop + (size_t)(a.I / 64) * RP * 128;             // 2 buffers x (2 x RP x 128 B)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wop + 4 * RP * 128);
-  uint64_t* full = bars;                     // [kMaxSlots]
-  uint64_t* empty = bars + kMaxSlots;        // [kMaxSlots]
+  unsigned char* ring = base;                                           // ns x 16 KiB
+  unsigned char* qop = ring + (size_t)ns * kChunkBytes;                 // (I/64) x RP x 128 B
+  unsigned char* wop = qop + (size_t)(a.I / 64) * RP * 128;             // 2 x RP x 128 B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wop + 2 * RP * 128);
+  uint64_t* full = bars;                     // [kMaxSlots] chunk landed
+  uint64_t* empty = bars + kMaxSlots;        // [kMaxSlots] GEMM2 done with the chunk
   uint64_t* wfull = bars + 2 * kMaxSlots;    // [2] GEMM1 done -> W in TMEM buffer
   uint64_t* wfree = wfull + 2;               // [2] epilogue read the TMEM W buffer
   uint64_t* opfull = wfree + 2;              // [2] bf16 W operand written
   uint64_t* opfree = opfull + 2;             // [2] GEMM2 done reading the operand
-  uint64_t* ydone = opfree + 2;              // [1] all MMAs done
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(ydone + 1);
+  uint64_t* ydone = opfree + 2;              // [1] all GEMM2 MMAs done
+  uint64_t* g1done = ydone + 1;              // [1] all GEMM1 MMAs done
+  uint64_t* ystaged = g1done + 1;            // [1] final Y staged in shared memory
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(ystaged + 1);
   __shared__ double red[32];
   __shared__ int s_fail;
   volatile int* vfail = &s_fail;
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long nt = a.ntiles > blockIdx.x ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   if (tid == 0) {
-    for (int k = 0; k < nslots; ++k) {
+    for (int k = 0; k < kMaxSlots; ++k) {
       mbar_init(su32(&full[k]), 1);
       mbar_init(su32(&empty[k]), 1);
     }
@@ -213,6 +221,8 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
       mbar_init(su32(&opfree[b]), 1);
     }
     mbar_init(su32(ydone), 1);
+    mbar_init(su32(g1done), 1);
+    mbar_init(su32(ystaged), 128);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -225,13 +235,6 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int e = tid; e < a.I * RP; e += kTcThreads2) {
-    const int i = e / RP, r = e % RP;
-    const float v = r < a.R ? a.L[(size_t)i * a.R + r] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(qop + (size_t)(i >> 6) * RP * 128 + sw128_off(r, i & 63)) =
-        __float2bfloat16_rn(v);
-  }
-  fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
@@ -239,108 +242,159 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
   const uint32_t t_w0 = tmem, t_y = tmem + 2 * RP;   // W buffers at 0 and RP; Y chunks after
   double wsq = 0.0;
 
+  if (warp != 4) {
+    // The basis as GEMM1's B operand (K-major, 128B swizzle): every warp but the
+    // producer, which starts streaming at once. One unit = 8 consecutive rows i
+    // of one column r -> one 16-byte store; lanes take consecutive r, so each of
+    // the 8 loads of a unit is coalesced across the warp.
+    const int ft = tid < 128 ? tid : tid - 32;   // 0..191
+    constexpr int kFill = kTcThreads - 32;
+    constexpr int kUn = 4;
+    const int nunits = (a.I / 8) * RP;
+    for (int u0 = ft; u0 < nunits; u0 += kFill * kUn) {
+      float x[kUn][8];
+#pragma unroll
+      for (int w = 0; w < kUn; ++w) {
+        const int u = u0 + w * kFill;
+        const int r = u % RP, i0 = (u / RP) * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          x[w][k] = (u < nunits && r < a.R) ? __ldg(a.L + (size_t)(i0 + k) * a.R + r) : 0.f;
+      }
+#pragma unroll
+      for (int w = 0; w < kUn; ++w) {
+        const int u = u0 + w * kFill;
+        if (u >= nunits) break;
+        const int r = u % RP, i0 = (u / RP) * 8;
+        uint4 pk;
+        pk.x = pack_bf16(x[w][0], x[w][1]);
+        pk.y = pack_bf16(x[w][2], x[w][3]);
+        pk.z = pack_bf16(x[w][4], x[w][5]);
+        pk.w = pack_bf16(x[w][6], x[w][7]);
+        *reinterpret_cast<uint4*>(qop + (size_t)(i0 >> 6) * RP * 128 + r * 128 +
+                                  ((((i0 & 63) >> 3) ^ (r & 7)) << 4)) = pk;
+      }
+    }
+    fence_async_smem();
+    asm volatile("bar.sync 1, %0;" ::"r"(kFill) : "memory");
+  }
+
   if (warp == 4) {
     // ---------------- producer (whole warp waits, lane 0 issues) ----------------
     int slot = 0;
     uint32_t ph = 0;
-    for (long long step = 0; step <= nt && !*vfail; ++step) {
-      for (int kind = 0; kind < 2 && !*vfail; ++kind) {   // kind 0: A(step), 1: B(step-1)
-        const long long lt = kind == 0 ? step : step - 1;
-        if (lt < 0 || lt >= nt) continue;
-        const long long j0 = (blockIdx.x + lt * gridDim.x) * kTcCols;
-        const long long p = j0 / a.Q, q0 = j0 - p * a.Q;
-        for (int c = 0; c < nchunk; ++c) {
-          if (!mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail)) break;
-          if (lane == 0) {
-            mbar_expect_tx(su32(&full[slot]), (uint32_t)kChunkBytes);
-            for (int h = 0; h < 2; ++h)
-              tma_load_3d(su32(ring + (size_t)slot * kChunkBytes + h * kHalfBytes), &tmap,
-                          su32(&full[slot]), (int)(q0 + h * 64), c * kTcRows, (int)p);
-          }
-          __syncwarp();
-          if (++slot == nslots) {
-            slot = 0;
-            ph ^= 1u;
-          }
+    long long fills = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const long long j0 = (blockIdx.x + lt * gridDim.x) * kTcCols;
+      const long long p = j0 / a.Q, q0 = j0 - p * a.Q;
+      for (int c = 0; c < nchunk && ok; ++c) {
+        ok = mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail);
+        if (!ok) break;
+        if (lane == 0) {
+          mbar_expect_tx(su32(&full[slot]), (uint32_t)kChunkBytes);
+          tma_load_3d(su32(ring + (size_t)slot * kChunkBytes), &tmap, su32(&full[slot]), (int)q0,
+                      c * kTcRows, (int)p);
+        }
+        __syncwarp();
+        ++fills;
+        if (++slot == ns) {
+          slot = 0;
+          ph ^= 1u;
         }
       }
     }
+    // every copy issued must have landed before the shared memory is released
+    if (lane == 0) {
+      for (int sl = 0; sl < ns && sl < fills; ++sl) {
+        const long long nfill = fills / ns + (sl < fills % ns ? 1 : 0);
+        const uint32_t par = (uint32_t)((nfill - 1) & 1);
+        const long long t0 = clock64();
+        while (!mbar_try(su32(&full[sl]), par) && clock64() - t0 < (1ll << 30)) {
+        }
+      }
+    }
+    __syncwarp();
   } else if (warp == 5) {
-    // ---------------- MMA issuer (whole warp waits, lane 0 issues) ----------------
-    constexpr uint32_t kIdesc = idesc_bf16(128, RP, 0, 0);
-    constexpr uint32_t kIdescMN = idesc_bf16(128, RP, 1, 0);
+    // ---------------- GEMM1 issuer: W_t = B_t^T Q (M = 64 columns) ----------------
+    constexpr uint32_t kIdesc1 = idesc_bf16(64, RP, 1, 0);
     int slot = 0;
     uint32_t ph = 0;
     bool ok = true;
-    for (long long step = 0; step <= nt && ok; ++step) {
-      for (int kind = 0; kind < 2 && ok; ++kind) {
-        const long long lt = kind == 0 ? step : step - 1;
-        if (lt < 0 || lt >= nt) continue;
-        const int wb = (int)(lt & 1);
-        const uint32_t use = (uint32_t)(lt >> 1);
-        if (kind == 0) {
-          // GEMM1(lt) into TMEM W buffer wb, once the epilogue of lt-2 has read it
-          if (lt >= 2) ok = mbar_wait_b(su32(&wfree[wb]), (use - 1) & 1u, vfail);
-          fence_after();
-          for (int c = 0; c < nchunk && ok; ++c) {
-            ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
-            if (!ok) break;
-            fence_after();
-            if (lane == 0) {
-              const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
-              for (int ks = 0; ks < kTcRows / 16; ++ks) {
-                const uint64_t ad = desc_sw128(abase + ks * 16 * 128, kHalfBytes, 1024);
-                const int k = c * kTcRows + ks * 16;
-                const uint64_t bd = desc_sw128(
-                    su32(qop) + (uint32_t)((k >> 6) * RP * 128 + ((k & 63) >> 4) * 32), 16, 1024);
-                mma_bf16(t_w0 + wb * RP, ad, bd, kIdescMN, (c | ks) ? 1u : 0u);
-              }
-              mma_commit(su32(&empty[slot]));
-            }
-            __syncwarp();
-            if (++slot == nslots) {
-              slot = 0;
-              ph ^= 1u;
-            }
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const int wb = (int)(lt & 1);
+      const uint32_t use = (uint32_t)(lt >> 1);
+      if (lt >= 2) ok = mbar_wait_b(su32(&wfree[wb]), (use - 1) & 1u, vfail);
+      fence_after();
+      for (int c = 0; c < nchunk && ok; ++c) {
+        ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+        if (!ok) break;
+        fence_after();
+        if (lane == 0) {
+          const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
+#pragma unroll
+          for (int ks = 0; ks < kTcRows / 16; ++ks) {
+            const uint64_t ad = desc_sw128(abase + ks * 16 * 128, kChunkBytes, 1024);
+            const int k = c * kTcRows + ks * 16;
+            const uint64_t bd = desc_sw128(
+                su32(qop) + (uint32_t)((k >> 6) * RP * 128 + ((k & 63) >> 4) * 32), 16, 1024);
+            mma_bf16(t_w0 + wb * RP, ad, bd, kIdesc1, (c | ks) ? 1u : 0u);
           }
-          if (ok && lane == 0) mma_commit(su32(&wfull[wb]));
-          __syncwarp();
-        } else {
-          // GEMM2(lt): Y += B_t W_t, once the epilogue has written the bf16 W operand
-          ok = mbar_wait_b(su32(&opfull[wb]), use & 1u, vfail);
-          fence_after();
-          unsigned char* wopb = wop + (size_t)wb * 2 * RP * 128;
-          for (int c = 0; c < nchunk && ok; ++c) {
-            ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
-            if (!ok) break;
-            fence_after();
-            if (lane == 0) {
-              const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
-              for (int ks = 0; ks < kTcCols / 16; ++ks) {
-                const uint64_t ad =
-                    desc_sw128(abase + (ks >> 2) * kHalfBytes + (ks & 3) * 32, 16, 1024);
-                const uint64_t bd =
-                    desc_sw128(su32(wopb) + (ks >> 2) * RP * 128 + (ks & 3) * 32, 16, 1024);
-                mma_bf16(t_y + c * RP, ad, bd, kIdesc, (lt == 0 && ks == 0) ? 0u : 1u);
-              }
-              mma_commit(su32(&empty[slot]));
-            }
-            __syncwarp();
-            if (++slot == nslots) {
-              slot = 0;
-              ph ^= 1u;
-            }
-          }
-          if (ok && lane == 0) mma_commit(su32(&opfree[wb]));
-          __syncwarp();
+        }
+        __syncwarp();
+        if (++slot == ns) {
+          slot = 0;
+          ph ^= 1u;
         }
       }
+      if (ok && lane == 0) mma_commit(su32(&wfull[wb]));
+      __syncwarp();
     }
-    if (lane == 0) mma_commit(su32(ydone));   // completes once every MMA issued above has finished
+    if (lane == 0) mma_commit(su32(g1done));
+    __syncwarp();
+  } else if (warp == 6) {
+    // ---------------- GEMM2 issuer: Y += B_t W_t (M = 128 rows) ----------------
+    constexpr uint32_t kIdesc2 = idesc_bf16(128, RP, 0, 0);
+    int slot = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const int wb = (int)(lt & 1);
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ok = mbar_wait_b(su32(&opfull[wb]), use & 1u, vfail);
+      fence_after();
+      const uint32_t bbase = su32(wop + (size_t)wb * RP * 128);
+      for (int c = 0; c < nchunk && ok; ++c) {
+        // already complete (GEMM1 waited on it; the slot is not refilled before
+        // this warp releases it): makes the TMA data visible to this thread too
+        ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+        if (!ok) break;
+        fence_after();
+        if (lane == 0) {
+          const uint32_t abase = su32(ring + (size_t)slot * kChunkBytes);
+#pragma unroll
+          for (int ks = 0; ks < kTcCols / 16; ++ks) {
+            const uint64_t ad = desc_sw128(abase + ks * 32, 16, 1024);
+            const uint64_t bd = desc_sw128(bbase + ks * 32, 16, 1024);
+            mma_bf16(t_y + c * RP, ad, bd, kIdesc2, (lt == 0 && ks == 0) ? 0u : 1u);
+          }
+          mma_commit(su32(&empty[slot]));
+        }
+        __syncwarp();
+        if (++slot == ns) {
+          slot = 0;
+          ph ^= 1u;
+        }
+      }
+      if (ok && lane == 0) mma_commit(su32(&opfree[wb]));
+      __syncwarp();
+    }
+    if (lane == 0) mma_commit(su32(ydone));
     __syncwarp();
   } else {
-    // ---------------- epilogue: warps 0-3 (TMEM lanes 0-127) ----------------
-    const int col = warp * 32 + lane;
+    // ---------------- epilogue: warps 0-3 ----------------
+    const bool wrow = lane < 16;               // this lane holds a row of W_t
+    const int m = warp * 16 + (lane & 15);     // tile column of that row
     bool ok = true;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const int wb = (int)(lt & 1);
@@ -361,36 +415,70 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
       mbar_arrive(su32(&wfree[wb]));
       if (lt >= 2) ok = mbar_wait_b(su32(&opfree[wb]), (use - 1) & 1u, vfail);
       if (!ok) break;
-      unsigned char* wopb = wop + (size_t)wb * 2 * RP * 128;
+      if (wrow) {
+        unsigned char* wrowp = wop + (size_t)wb * RP * 128 + (m & 7) * 2;
+        const int c8 = m >> 3;
+        float tsq = 0.f;
 #pragma unroll
-      for (int r = 0; r < RP; ++r) {
-        const float w = r < a.R ? v[r] : 0.f;
-        wsq += (double)w * w;
-        *reinterpret_cast<__nv_bfloat16*>(wopb + (size_t)(col >> 6) * RP * 128 + sw128_off(r, col & 63)) =
-            __float2bfloat16_rn(w);
+        for (int r = 0; r < RP; ++r) {
+          const float w = r < a.R ? v[r] : 0.f;
+          tsq = fmaf(w, w, tsq);
+          *reinterpret_cast<__nv_bfloat16*>(wrowp + r * 128 + ((c8 ^ (r & 7)) << 4)) =
+              __float2bfloat16_rn(w);
+        }
+        wsq += (double)tsq;
       }
       fence_async_smem();
       mbar_arrive(su32(&opfull[wb]));
     }
-    // final Y: wait for every MMA, then TMEM -> FP32 partials
+    // final Y: wait for every GEMM2, then TMEM -> FP32 partials
     float* yp = a.Ypart + (size_t)blockIdx.x * a.I * a.R;
-    if (ok && nt > 0 && mbar_wait_b(su32(ydone), 0u, vfail)) {
+    if (ok && mbar_wait_b(su32(ydone), 0u, vfail)) {
       fence_after();
-      for (int c = 0; c < nchunk; ++c) {
-        const int i = c * kTcRows + warp * 32 + lane;
+      if (y_tma) {
+        // Stage 128 x 32 boxes with 128B swizzle in the (now idle) ring and
+        // operand memory, then one thread stores them with TMA; the swizzle
+        // spreads each warp's 16-byte writes over all banks.
+        const int nxb = (a.R + 31) / 32;
+        const int row = warp * 32 + lane;
+        for (int c = 0; c < nchunk; ++c) {
 #pragma unroll
-        for (int rb = 0; rb < RP; rb += 32) {
-          float t32[32];
-          tmem_ld32(t_y + c * RP + ((uint32_t)(warp * 32) << 16) + rb, t32);
+          for (int rb = 0; rb < RP; rb += 32) {
+            if (rb / 32 >= nxb) break;
+            float t32[32];
+            tmem_ld32(t_y + c * RP + ((uint32_t)(warp * 32) << 16) + rb, t32);
+            unsigned char* box = base + (size_t)(c * nxb + rb / 32) * 16384 + row * 128;
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int r = rb + k;
-            if (r < a.R) yp[(size_t)i * a.R + r] = t32[k];
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<float4*>(box + ((j ^ (row & 7)) << 4)) =
+                  make_float4(t32[4 * j], t32[4 * j + 1], t32[4 * j + 2], t32[4 * j + 3]);
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(su32(ystaged));
+        if (tid == 0 && mbar_wait_b(su32(ystaged), 0u, vfail)) {
+          for (int c = 0; c < nchunk; ++c)
+            for (int xb = 0; xb < nxb; ++xb)
+              tma_store_2d(&ymap, su32(base + (size_t)(c * nxb + xb) * 16384), xb * 32,
+                           (int)(blockIdx.x * a.I + c * kTcRows));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+      } else {
+        for (int c = 0; c < nchunk; ++c) {
+          const int i = c * kTcRows + warp * 32 + lane;
+#pragma unroll
+          for (int rb = 0; rb < RP; rb += 32) {
+            float t32[32];
+            tmem_ld32(t_y + c * RP + ((uint32_t)(warp * 32) << 16) + rb, t32);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int r = rb + k;
+              if (r < a.R) yp[(size_t)i * a.R + r] = t32[k];
+            }
           }
         }
       }
-    } else if (nt == 0) {
-      for (int e = tid; e < a.I * a.R; e += 128) yp[e] = 0.f;
     }
   }
   const double tot = block_sum(wsq, red);
@@ -399,10 +487,11 @@ __global__ void __launch_bounds__(kTcThreads2, 1)
     if (*vfail) atomicExch(a.err, 5);   // TALS_ETIMEOUT
   }
   // nothing may still write the shared or tensor memory released below: after a
-  // failure, wait (bounded) for the MMA group and the copies issued so far
-  if (*vfail && tid == 160) {
+  // failure, wait (bounded) for both MMA groups issued so far
+  if (*vfail && (tid == 160 || tid == 192)) {
+    const uint32_t b = tid == 160 ? su32(g1done) : su32(ydone);
     const long long t0 = clock64();
-    while (!mbar_try(su32(ydone), 0u) && clock64() - t0 < (1ll << 30)) {
+    while (!mbar_try(b, 0u) && clock64() - t0 < (1ll << 30)) {
     }
   }
   fence_before();
@@ -419,16 +508,17 @@ int tc_slots(long long I, int RP);
 
 bool tc_supported(const ModeView& v, int R) {
   return v.I % kTcRows == 0 && v.I <= 512 && v.Q % kTcCols == 0 && R >= 1 && R <= 64 &&
-         tc_slots(v.I, ((R + 15) / 16) * 16) >= 2;
+         tc_slots(v.I, ((R + 15) / 16) * 16) >= v.I / kTcRows;
 }
 
-size_t tc_smem_bytes(long long I, int RP, int nslots) {
-  return 1024 + (size_t)nslots * kChunkBytes + (size_t)(I / 64) * RP * 128 + 4 * (size_t)RP * 128 +
-         (2 * kMaxSlots + 9) * 8 + 16;
+size_t tc_smem_bytes(long long I, int RP, int ns) {
+  return 1024 + (size_t)ns * kChunkBytes + (size_t)(I / 64) * RP * 128 + 2 * (size_t)RP * 128 +
+         (2 * kMaxSlots + 11) * 8 + 16;
 }
 
+// Ring slots that fit next to the operands (at least one tile's worth is needed).
 int tc_slots(long long I, int RP) {
-  const size_t fixed = 1024 + (size_t)(I / 64) * RP * 128 + 4 * (size_t)RP * 128 + 512;
+  const size_t fixed = 1024 + (size_t)(I / 64) * RP * 128 + 2 * (size_t)RP * 128 + 512;
   const size_t cap = 227 * 1024 - 2048;   // dynamic smem budget (static smem: red + flag)
   if (fixed >= cap) return 0;
   return (int)std::min<size_t>(kMaxSlots, (cap - fixed) / kChunkBytes);
@@ -470,6 +560,22 @@ bool tc_make_map(const void* Xb, const ModeView& v, CUtensorMap* map) {
   return r == CUDA_SUCCESS;
 }
 
+// Tensor map of the per-CTA FP32 partials Ypart viewed as (R, rows), boxes of
+// 32 x 128 with 128B swizzle (the staging layout of the final Y store).
+bool tc_make_ymap(float* Ypart, int R, long long rows, CUtensorMap* map) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if ((uintptr_t)Ypart % 16 != 0 || R % 4 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)R * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)kTcRows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Ypart, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
                            double* spart, int* err, int grid, cudaStream_t s) {
   if (!tc_supported(v, R)) return cudaErrorInvalidValue;
@@ -488,9 +594,9 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
   a.Ypart = Ypart;
   a.spart = spart;
   a.err = err;
-  const int nslots = tc_slots(v.I, RP);
-  if (nslots < 2) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(v.I, RP, nslots);
+  const int ns = tc_slots(v.I, RP);
+  if (ns < v.I / kTcRows) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(v.I, RP, ns);
   void* fn = nullptr;
   switch (RP) {
     case 16: fn = (void*)&tc_pass_kernel<16>; break;
@@ -502,8 +608,16 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   grid = (int)std::min<long long>(grid, a.ntiles);
-  void* args[] = {&map, &a, (void*)&nslots};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads2), args, smem, s);
+  // final Y through TMA when the rows are 16-byte multiples and the staged
+  // boxes fit in the ring and basis-operand memory
+  CUtensorMap ymap;
+  std::memset(&ymap, 0, sizeof(ymap));
+  const size_t nbox = (size_t)(v.I / kTcRows) * ((R + 31) / 32);
+  const size_t region = (size_t)ns * kChunkBytes + (size_t)(v.I / 64) * RP * 128;
+  int y_tma = (nbox * 16384 <= region && tc_make_ymap(Ypart, R, (long long)grid * v.I, &ymap)) ? 1 : 0;
+  int ns_ = ns;
+  void* args[] = {&map, &ymap, &a, (void*)&ns_, (void*)&y_tma};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads), args, smem, s);
 }
 
 // FP32 -> BF16 copy (round to nearest even), vectorised by 4.

@@ -29,8 +29,13 @@ def _bf16(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
+# R = 30 takes the scalar store of the final Y (rows not 16-byte multiples);
+# R = 20 the TMA store with a ragged box; (256, 128, 384) and (128, 512, 256)
+# give every CTA several tiles; Q = 192 is a multiple of the 64-column tile but
+# not of 128.
 PASS_CASES = [((128, 64, 256), 0, 16), ((512, 16, 256), 0, 32), ((8, 256, 128), 1, 48),
-              ((6, 384, 256), 1, 64)]
+              ((6, 384, 256), 1, 64), ((256, 128, 384), 0, 30), ((128, 512, 256), 1, 20),
+              ((4, 128, 192), 1, 16)]
 
 
 @pytest.mark.parametrize("dims,mode,R", PASS_CASES)
