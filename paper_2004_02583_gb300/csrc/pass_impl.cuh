@@ -198,6 +198,11 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
   for (int k = 0; k < RPT; ++k)
 #pragma unroll
     for (int v = 0; v < RW; ++v) yacc[k][v] = T(0);
+  float2 yacc2[RPT][RW / 2];   // FP32 accumulators of step 2 (paired along r)
+#pragma unroll
+  for (int k = 0; k < RPT; ++k)
+#pragma unroll
+    for (int v = 0; v < RW / 2; ++v) yacc2[k][v] = make_float2(0.f, 0.f);
   double sacc = 0.0;   // this thread's share of the pass's FP64 sum
 
   const int rgrp = tid / S::ROWT;            // step-2 r-group (warp-uniform)
@@ -236,43 +241,84 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
     if (do_w) {
       // ---- step 1: W_t = B_t^T Qb, split over the warps along i ----
       T acc[4][S::RL];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < S::RL; ++v) acc[u][v] = T(0);
       const T* trow = Tb + cg * 4;
       const T* lrow = Ls + rg * S::RL;
-      if (ilo < ihi) {
-        T tv[4], lv[S::RL];
-        ld4(trow + ilo * kJTP, tv);
+      const int nrow = (int)(ihi - ilo);
+      if constexpr (sizeof(T) == 4 && S::RL % 2 == 0) {
+        // FP32: paired FMAs (two lanes of r per instruction), same rounding as fmaf
+        float2 acc2[4][S::RL / 2];
 #pragma unroll
-        for (int v = 0; v < S::RL; ++v) lv[v] = lrow[ilo * RC + v];
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < S::RL / 2; ++v) acc2[u][v] = make_float2(0.f, 0.f);
+        const float* tp = reinterpret_cast<const float*>(trow) + (int)ilo * kJTP;
+        const float* lp = reinterpret_cast<const float*>(lrow) + (int)ilo * RC;
 #pragma unroll 4
-        for (long long i = ilo; i < ihi; ++i) {
-          // operands of row i+1 are loaded before row i is multiplied
-          const long long inx = (i + 1 < ihi) ? i + 1 : i;
-          T tn4[4], ln[S::RL];
-          ld4(trow + inx * kJTP, tn4);
+        for (int ii = 0; ii < nrow; ++ii) {
+          const float4 t4 = *reinterpret_cast<const float4*>(tp + ii * kJTP);
+          float2 l2[S::RL / 2];
           if constexpr (S::RL % 4 == 0) {
 #pragma unroll
             for (int v = 0; v < S::RL; v += 4) {
-              T q4[4];
-              ld4(lrow + inx * RC + v, q4);
-#pragma unroll
-              for (int w = 0; w < 4; ++w) ln[v + w] = q4[w];
+              const float4 q4 = *reinterpret_cast<const float4*>(lp + ii * RC + v);
+              l2[v / 2] = make_float2(q4.x, q4.y);
+              l2[v / 2 + 1] = make_float2(q4.z, q4.w);
             }
           } else {
-#pragma unroll
-            for (int v = 0; v < S::RL; ++v) ln[v] = lrow[inx * RC + v];
+            l2[0] = *reinterpret_cast<const float2*>(lp + ii * RC);
           }
+          const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < 4; ++u) {
+            const float2 t2 = make_float2(tv[u], tv[u]);
 #pragma unroll
-            for (int v = 0; v < S::RL; ++v) acc[u][v] = fma(tv[u], lv[v], acc[u][v]);
+            for (int v = 0; v < S::RL / 2; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+          }
+        }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) tv[u] = tn4[u];
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < S::RL; ++v) lv[v] = ln[v];
+          for (int v = 0; v < S::RL / 2; ++v) {
+            acc[u][2 * v] = acc2[u][v].x;
+            acc[u][2 * v + 1] = acc2[u][v].y;
+          }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < S::RL; ++v) acc[u][v] = T(0);
+        if (ilo < ihi) {
+          T tv[4], lv[S::RL];
+          ld4(trow + ilo * kJTP, tv);
+#pragma unroll
+          for (int v = 0; v < S::RL; ++v) lv[v] = lrow[ilo * RC + v];
+#pragma unroll 4
+          for (long long i = ilo; i < ihi; ++i) {
+            // operands of row i+1 are loaded before row i is multiplied
+            const long long inx = (i + 1 < ihi) ? i + 1 : i;
+            T tn4[4], ln[S::RL];
+            ld4(trow + inx * kJTP, tn4);
+            if constexpr (S::RL % 4 == 0) {
+#pragma unroll
+              for (int v = 0; v < S::RL; v += 4) {
+                T q4[4];
+                ld4(lrow + inx * RC + v, q4);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) ln[v + w] = q4[w];
+              }
+            } else {
+#pragma unroll
+              for (int v = 0; v < S::RL; ++v) ln[v] = lrow[inx * RC + v];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < S::RL; ++v) acc[u][v] = fma(tv[u], lv[v], acc[u][v]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tv[u] = tn4[u];
+#pragma unroll
+            for (int v = 0; v < S::RL; ++v) lv[v] = ln[v];
+          }
         }
       }
       T* wr = Wred + (size_t)warp * kJT * WSP;
@@ -350,25 +396,56 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       // ---- step 2: Y[i, r] += sum_c B_t[i, c] W_t[c, r] ----
       const T* wrow = Ws + rgrp * RW;
       const T* tbase = Tb + (size_t)ti * kJTP;
+      if constexpr (sizeof(T) == 4) {
+        // FP32: paired FMAs along r, same rounding as fmaf
+        const float* wp = reinterpret_cast<const float*>(wrow);
+        const float* tp = reinterpret_cast<const float*>(tbase);
 #pragma unroll
-      for (int c4 = 0; c4 < kJT; c4 += 4) {
-        T tv[RPT][4];
+        for (int c4 = 0; c4 < kJT; c4 += 4) {
+          float tv[RPT][4];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) ld4(tbase + (size_t)k * S::ROWT * kJTP + c4, tv[k]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          T wv[RW];
-#pragma unroll
-          for (int v = 0; v < RW; v += 4) {
-            T q4[4];
-            ld4(wrow + (c4 + u) * WSP + v, q4);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) wv[v + w] = q4[w];
+          for (int k = 0; k < RPT; ++k) {
+            const float4 x = *reinterpret_cast<const float4*>(tp + k * S::ROWT * kJTP + c4);
+            tv[k][0] = x.x; tv[k][1] = x.y; tv[k][2] = x.z; tv[k][3] = x.w;
           }
 #pragma unroll
-          for (int k = 0; k < RPT; ++k)
+          for (int u = 0; u < 4; ++u) {
+            float2 w2[RW / 2];
 #pragma unroll
-            for (int v = 0; v < RW; ++v) yacc[k][v] = fma(tv[k][u], wv[v], yacc[k][v]);
+            for (int v = 0; v < RW; v += 4) {
+              const float4 q4 = *reinterpret_cast<const float4*>(wp + (c4 + u) * WSP + v);
+              w2[v / 2] = make_float2(q4.x, q4.y);
+              w2[v / 2 + 1] = make_float2(q4.z, q4.w);
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+              const float2 b2 = make_float2(tv[k][u], tv[k][u]);
+#pragma unroll
+              for (int v = 0; v < RW / 2; ++v) yacc2[k][v] = __ffma2_rn(b2, w2[v], yacc2[k][v]);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c4 = 0; c4 < kJT; c4 += 4) {
+          T tv[RPT][4];
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) ld4(tbase + (size_t)k * S::ROWT * kJTP + c4, tv[k]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            T wv[RW];
+#pragma unroll
+            for (int v = 0; v < RW; v += 4) {
+              T q4[4];
+              ld4(wrow + (c4 + u) * WSP + v, q4);
+#pragma unroll
+              for (int w = 0; w < 4; ++w) wv[v + w] = q4[w];
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+#pragma unroll
+              for (int v = 0; v < RW; ++v) yacc[k][v] = fma(tv[k][u], wv[v], yacc[k][v]);
+          }
         }
       }
     }
@@ -382,6 +459,15 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
   }
   cp_async_wait<0>();
 
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+      for (int v = 0; v < RW / 2; ++v) {
+        yacc[k][2 * v] = yacc2[k][v].x;
+        yacc[k][2 * v + 1] = yacc2[k][v].y;
+      }
+  }
   if (do_y) {
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {

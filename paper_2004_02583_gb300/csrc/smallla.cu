@@ -14,12 +14,15 @@ namespace tals {
 // ---------------------------------------------------------------------------
 // Reduce per-CTA Y partials to FP64 and form Gram partials of a row block.
 // ---------------------------------------------------------------------------
+constexpr int kMaxSlices = 16;
+constexpr int kReduceThreads = 1024;
+
 template <typename T>
 __global__ void reduce_rows_kernel(const T* __restrict__ Ypart, int gx, long long I, int R,
                                    double* __restrict__ Y64, int gram_mode,
                                    const double* __restrict__ L64, double* __restrict__ Gpart,
                                    int rows_per_block, const double* __restrict__ spart, int nsp,
-                                   int which, ModeState* st, double* norm_a2, T* YT) {
+                                   int which, ModeState* st, double* norm_a2, T* YT, int S) {
   if (st != nullptr && st->done) return;
   extern __shared__ double sh[];
   double* Ys = sh;                                   // [rows_per_block][R]
@@ -27,11 +30,54 @@ __global__ void reduce_rows_kernel(const T* __restrict__ Ypart, int gx, long lon
   const long long row0 = (long long)blockIdx.x * rows_per_block;
   const int nrows = (int)min((long long)rows_per_block, I - row0);
   const int nent = nrows * R;
+  const size_t stride = (size_t)I * R;
+  // The partials are read with many loads in flight: when the block has more
+  // threads than entries, each entry's partials are split over S slices
+  // (b = sl, sl + S, ...) whose sums are then added in a fixed order.
+  double* slice_sum = As + (size_t)rows_per_block * R;   // [S][nent]
+  for (int e0 = threadIdx.x; e0 < S * nent; e0 += blockDim.x) {
+    const int sl = e0 / nent, e = e0 - sl * nent;
+    const long long i = row0 + e / R;
+    const int r = e % R;
+    const T* src = Ypart + (size_t)i * R + r + (size_t)sl * stride;
+    const size_t sstride = (size_t)S * stride;
+    const int nb = gx > sl ? (gx - sl + S - 1) / S : 0;
+    double s;
+    if constexpr (sizeof(T) == 4) {
+      // FP32 partials: Neumaier-compensated FP32 sum (the running sum and its
+      // exact rounding error), FP64-level accuracy at FP32 arithmetic rates
+      float hi = 0.f, lo = 0.f;
+      int b = 0;
+      for (; b + 8 <= nb; b += 8) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(b + u) * sstride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float t = hi + x[u];
+          lo += fabsf(hi) >= fabsf(x[u]) ? (hi - t) + x[u] : (x[u] - t) + hi;
+          hi = t;
+        }
+      }
+      for (; b < nb; ++b) {
+        const float xv = src[(size_t)b * sstride];
+        const float t = hi + xv;
+        lo += fabsf(hi) >= fabsf(xv) ? (hi - t) + xv : (xv - t) + hi;
+        hi = t;
+      }
+      s = (double)hi + (double)lo;
+    } else {
+      s = 0.0;
+      for (int b = 0; b < nb; ++b) s += (double)src[(size_t)b * sstride];
+    }
+    slice_sum[(size_t)sl * nent + e] = s;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < nent; e += blockDim.x) {
     const long long i = row0 + e / R;
     const int r = e % R;
     double s = 0.0;
-    for (int b = 0; b < gx; ++b) s += (double)Ypart[((size_t)b * I + i) * R + r];
+    for (int sl = 0; sl < S; ++sl) s += slice_sum[(size_t)sl * nent + e];
     Ys[e] = s;
     if (Y64 != nullptr) Y64[i * R + r] = s;
     if (YT != nullptr) YT[i * R + r] = (T)s;
@@ -79,17 +125,26 @@ cudaError_t launch_reduce_rows(int dtype, const void* Ypart, int gx, long long I
                                double* Y64, int gram_mode, const double* L64, double* Gpart,
                                const RowPlan& rp, const double* spart, int nsp, int which,
                                ModeState* st, double* norm_a2, cudaStream_t s, void* YT) {
-  const size_t sm = (size_t)2 * rp.rows_per_block * R * sizeof(double);
+  const int nent = rp.rows_per_block * R;
+  int S = std::max(1, std::min(kMaxSlices, kReduceThreads / std::max(1, nent)));
+  while (S > 1 && ((size_t)2 + S) * nent * sizeof(double) > 200 * 1024) --S;
+  const size_t sm = ((size_t)2 + S) * nent * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(dtype == 1 ? (const void*)reduce_rows_kernel<float>
+                                                    : (const void*)reduce_rows_kernel<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
   if (dtype == 1)
-    reduce_rows_kernel<float><<<rp.blocks, 256, sm, s>>>((const float*)Ypart, gx, I, R, Y64,
+    reduce_rows_kernel<float><<<rp.blocks, kReduceThreads, sm, s>>>((const float*)Ypart, gx, I, R, Y64,
                                                          gram_mode, L64, Gpart,
                                                          rp.rows_per_block, spart, nsp, which,
-                                                         st, norm_a2, (float*)YT);
+                                                         st, norm_a2, (float*)YT, S);
   else
-    reduce_rows_kernel<double><<<rp.blocks, 256, sm, s>>>((const double*)Ypart, gx, I, R, Y64,
+    reduce_rows_kernel<double><<<rp.blocks, kReduceThreads, sm, s>>>((const double*)Ypart, gx, I, R, Y64,
                                                           gram_mode, L64, Gpart,
                                                           rp.rows_per_block, spart, nsp, which,
-                                                          st, norm_a2, (double*)YT);
+                                                          st, norm_a2, (double*)YT, S);
   return cudaGetLastError();
 }
 
@@ -97,6 +152,33 @@ cudaError_t launch_reduce_rows(int dtype, const void* Ypart, int gx, long long I
 // Single-CTA kernel: Gram sum, Eq. 5.01 stop rule, Cholesky.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
+constexpr int kMaxR = 64;                                              // rank limit of the solves
+
+// d > tiny for a pivot, on the bit patterns (both non-negative; NaN fails):
+// integer compares keep FP64 instructions off the serial chain.
+__device__ __forceinline__ bool pivot_ok(double d, long long tiny_bits) {
+  const long long b = __double_as_longlong(d);
+  return b > tiny_bits && ((b >> 52) & 0x7ff) != 0x7ff;
+}
+
+// 1/d for a positive normal double: FP32 reciprocal of the leading bits, then
+// x = x0 (1 + e + e^2) with e = 1 - d x0 (Newton's method continued to third
+// order), ~2^-66 relative before the last rounding. Three dependent FP64
+// operations instead of a full double division.
+__device__ __forceinline__ double fast_rcp64(double d) {
+  const int hi = __double2hiint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  if (ex < -120 || ex > 120) return 1.0 / d;   // callers pass d > 0
+  const unsigned lo = (unsigned)__double2loint(d);
+  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
+  const float rf = __frcp_rn(f);
+  const int rb = __float_as_int(rf);
+  const int rex = ((rb >> 23) & 0xff) - 127;
+  const double x0 = __hiloint2double(((rex + 1023) << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+  const double e = fma(-d, x0, 1.0);
+  const double e2 = fma(e, e, e);
+  return fma(x0, e2, x0);
+}
 
 __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __restrict__ Gpart,
                                                               int nb, int R, int op,
@@ -110,7 +192,6 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
-  extern __shared__ double G[];   // [R][R]
   __shared__ int fail;
   const int tid = threadIdx.x;
 
@@ -168,51 +249,105 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     }
   }
 
-  for (int o = tid; o < R * R; o += kSmallThreads) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += Gpart[(size_t)b * R * R + o];   // nb = 1 after gram_sum
-    G[o] = s;
-  }
-  if (tid == 0) fail = 0;
-  __syncthreads();
-  // symmetrise (the cross Gram Q^T B B^T Q is symmetric in exact arithmetic)
+  // Right-looking Cholesky in LDL^T form on the symmetrised Gram S (lower
+  // triangle in shared memory). FP64 on this part is slow per instruction
+  // (~64-cycle latency; a warp instruction holds an SMSP's FP64 pipe ~76
+  // cycles whatever its active lanes), so the serial chain per step is kept
+  // short: warp 0 finishes column k+1 (one FMA per lane), takes the pivot's
+  // reciprocal (FP32 seed, one third-order FP64 correction) and forms
+  // L_j = S[j][k+1] / d_{k+1}, while warps 1.. update the rest of the trailing
+  // block, densely enumerated -- one barrier per step. Square roots come at
+  // the end, in parallel: C[i][k] = S_k[i][k] / sqrt(d_k).
+  __shared__ double S[kMaxR * kMaxR];
+  __shared__ double Lc[2][kMaxR];
+  __shared__ double rs[kMaxR];
+  __shared__ long long tiny_bits;
   for (int o = tid; o < R * R; o += kSmallThreads) {
     const int r = o / R, c = o % R;
-    if (r > c) {
-      const double v = 0.5 * (G[r * R + c] + G[c * R + r]);
-      G[r * R + c] = v;
-      G[c * R + r] = v;
+    if (c <= r) {
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < nb; ++q) {   // nb = 1 after gram_sum
+        a += Gpart[(size_t)q * R * R + r * R + c];
+        b += Gpart[(size_t)q * R * R + c * R + r];
+      }
+      // symmetrise (the cross Gram Q^T B B^T Q is symmetric in exact arithmetic)
+      S[r * R + c] = 0.5 * (a + b);
     }
   }
+  if (tid == 0) fail = 0;
+  // largest diagonal entry, from the high words of the (positive) doubles
+  if (tid < 32) {
+    int hmax = 0;
+    for (int r = tid; r < R; r += 32) hmax = max(hmax, __double2hiint(Gpart[r * R + r]));
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    if (tid == 0)
+      tiny_bits = __double_as_longlong(64.0 * 2.220446049250313e-16 * __hiloint2double(hmax, 0));
+  }
   __syncthreads();
-  double maxd = 0.0;
-  for (int r = 0; r < R; ++r) maxd = fmax(maxd, G[r * R + r]);
-  const double tiny = 64.0 * 2.220446049250313e-16 * maxd;
-  // right-looking Cholesky, lower factor in place
-  for (int k = 0; k < R; ++k) {
-    if (tid == 0) {
-      const double d = G[k * R + k];
-      if (!(d > tiny)) {
-        fail = 1;
-        G[k * R + k] = 1.0;
-      } else {
-        G[k * R + k] = sqrt(d);
+  const int lane = tid & 31, warp = tid >> 5;
+  // column 0: pivot and L_j = S[j][0] / d_0 (warp 0)
+  if (warp == 0) {
+    double d = S[0];
+    if (lane == 0 && !pivot_ok(d, tiny_bits)) {
+      d = 1.0;
+      S[0] = 1.0;
+      fail = 1;
+    }
+    const double dinv = __shfl_sync(0xffffffffu, lane == 0 ? fast_rcp64(d) : 0.0, 0);
+    for (int j = 1 + lane; j < R; j += 32) Lc[0][j] = S[j * R] * dinv;
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < R; ++k) {
+    const int cb = k & 1;
+    const int c1 = k + 1;   // the column finished this step
+    if (warp == 0) {
+      // column k+1: S[i][k+1] -= S[i][k] L_{k+1}, i >= k+1
+      const double lk = Lc[cb][c1];
+      double v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = c1 + lane + 32 * h;
+        v[h] = i < R ? fma(-S[i * R + k], lk, S[i * R + c1]) : 0.0;
+      }
+      double dinv = 0.0;
+      if (lane == 0) {
+        double d = v[0];
+        if (!pivot_ok(d, tiny_bits)) {
+          d = 1.0;
+          v[0] = 1.0;
+          fail = 1;
+        }
+        dinv = fast_rcp64(d);
+      }
+      dinv = __shfl_sync(0xffffffffu, dinv, 0);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = c1 + lane + 32 * h;
+        if (i < R) {
+          S[i * R + c1] = v[h];
+          if (i > c1) Lc[cb ^ 1][i] = v[h] * dinv;
+        }
+      }
+    } else {
+      // the rest of the trailing block: i >= j >= k+2
+      const int m = R - 2 - k;
+      const int na = m * (m + 1) / 2;
+      for (int a = tid - 32; a < na; a += kSmallThreads - 32) {
+        // a = i'(i'+1)/2 + j', 0 <= j' <= i' < m
+        int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
+        while (ip * (ip + 1) / 2 > a) --ip;
+        while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
+        const int i = k + 2 + ip, j = k + 2 + (a - ip * (ip + 1) / 2);
+        S[i * R + j] = fma(-S[i * R + k], Lc[cb][j], S[i * R + j]);
       }
     }
     __syncthreads();
-    const double rk = 1.0 / G[k * R + k];
-    for (int i = k + 1 + tid; i < R; i += kSmallThreads) G[i * R + k] *= rk;
-    __syncthreads();
-    const int m = R - k - 1;
-    for (int o = tid; o < m * m; o += kSmallThreads) {
-      const int i = k + 1 + o / m, j = k + 1 + o % m;
-      if (j <= i) G[i * R + j] -= G[i * R + k] * G[j * R + k];
-    }
-    __syncthreads();
   }
+  for (int r = tid; r < R; r += kSmallThreads) rs[r] = rsqrt(S[r * R + r]);
+  __syncthreads();
   for (int o = tid; o < R * R; o += kSmallThreads) {
     const int r = o / R, c = o % R;
-    F[o] = (c <= r) ? G[o] : 0.0;
+    F[o] = c <= r ? S[o] * rs[c] : 0.0;   // C[r][c]; sqrt(d_c) on the diagonal
   }
   if (tid == 0 && fail) {
     st->status = 4;   // TALS_ESINGULAR: Gram not numerically SPD (Remark 3)
@@ -225,13 +360,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
 cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F, ModeState* st,
                          const double* norm_a2, unsigned long long cond, int has_cond,
                          cudaStream_t s, const double* GL) {
-  const size_t sm = (size_t)R * R * sizeof(double);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  small_kernel<<<1, kSmallThreads, sm, s>>>(Gpart, nb, R, op, F, st, norm_a2,
+  if (R > kMaxR) return cudaErrorInvalidValue;
+  small_kernel<<<1, kSmallThreads, 0, s>>>(Gpart, nb, R, op, F, st, norm_a2,
                                             (cudaGraphConditionalHandle)cond, has_cond, GL);
   return cudaGetLastError();
 }
