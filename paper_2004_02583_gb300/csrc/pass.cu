@@ -80,9 +80,12 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
       if (sm > smem_max) continue;
       const int chunks = (R + in.rc - 1) / in.rc;
       const double waste = (double)(in.rc * chunks - R) / (double)(in.rc * chunks);
-      // prefer more resident warps, then fewer idle rows
+      const double idle = (double)((long long)rowt * in.rpt - v.I) / (double)((long long)rowt * in.rpt);
+      // fewer rank chunks and less padding first; then fewer idle rows; among
+      // equals the larger per-thread tile (more FMAs per shared-memory load:
+      // 4 rows x 16 ranks at 256 threads beats 2 x 16 at 512 when no row idles)
       const double score = chunks * (nbuf == 1 ? 1.35 : 1.0) * (1.0 + waste) +
-                           (in.nt == 512 ? 0.0 : 2e-3) + 1e-3 * in.rpt;
+                           (idle > 0.0 ? 0.01 + 0.5 * idle : 0.0) - 1e-3 * in.rpt * in.rw / 16.0;
       if (score < best) {
         best = score;
         cfg.rc = in.rc;

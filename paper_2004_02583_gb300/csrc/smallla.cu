@@ -368,9 +368,10 @@ cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F, 
 
 // ---------------------------------------------------------------------------
 // Row-wise triangular solves: one warp per row, lane j owns columns j and j+32
-// (R <= 64). Each solved entry is broadcast with a shuffle and every lane
-// updates its own running sums, so the dependent chain per row is R short steps
-// (no per-thread R^2 chain). Pivot reciprocals are taken once per block.
+// (R <= 64). The factor's rows (forward) and columns (backward) are scaled by
+// the pivot reciprocals once per block; each solved entry is broadcast with a
+// shuffle and every lane updates its own scaled running value, so the
+// dependent chain per row is R steps of one shuffle and one FMA.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int R,
@@ -379,11 +380,18 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
                                  int rows_per_block, const ModeState* st, int gram_rounded) {
   if (st != nullptr && st->done) return;
   extern __shared__ double sh[];
-  double* Fs = sh;                                   // [R][R]
-  double* dinv = sh + (size_t)R * R;                 // [R]
+  double* Ff = sh;                                   // [R][R] F[j][c] / F[j][j]  (forward)
+  double* Fb = Ff + (size_t)R * R;                   // [R][R] F[c][j] / F[j][j]  (backward)
+  double* dinv = Fb + (size_t)R * R;                 // [R]
   double* Os = dinv + R;                             // [rows_per_block][R]
-  for (int o = threadIdx.x; o < R * R; o += blockDim.x) Fs[o] = F[o];
   for (int r = threadIdx.x; r < R; r += blockDim.x) dinv[r] = 1.0 / F[r * R + r];
+  __syncthreads();
+  for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
+    const int r = o / R, c = o % R;
+    const double f = F[o];
+    Ff[o] = f * dinv[r];
+    Fb[o] = f * dinv[c];
+  }
   __syncthreads();
   const long long row0 = (long long)blockIdx.x * rows_per_block;
   const int nrows = (int)min((long long)rows_per_block, I - row0);
@@ -391,37 +399,34 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
   const int j0 = lane, j1 = lane + 32;
   for (int lr = warp; lr < nrows; lr += nwarp) {
     const long long i = row0 + lr;
-    double b0 = j0 < R ? In[i * R + j0] : 0.0, b1 = j1 < R ? In[i * R + j1] : 0.0;
-    double a0 = 0.0, a1 = 0.0;   // running sums of the solve
+    // Lane j keeps e_j = (b_j - sum_{c<j, solved} F[j][c] x_c) / F[j][j], updated
+    // as each x_c is broadcast; e_r is final when step r begins, so x_r = e_r and
+    // each step's serial chain is one shuffle and one FMA.
+    double e0 = j0 < R ? In[i * R + j0] * dinv[j0] : 0.0;
+    double e1 = j1 < R ? In[i * R + j1] * dinv[j1] : 0.0;
     double x0 = 0.0, x1 = 0.0;   // solved entries owned by this lane
-    // forward: F x^T = b^T, x_r = (b_r - sum_{c<r} F[r][c] x_c) / F[r][r]
+    // forward: F x^T = b^T
     for (int r = 0; r < R; ++r) {
       const int owner = r & 31;
-      double v = 0.0;
-      if (lane == owner) v = ((r < 32 ? b0 : b1) - (r < 32 ? a0 : a1)) * dinv[r];
-      v = __shfl_sync(0xffffffffu, v, owner);
+      const double v = __shfl_sync(0xffffffffu, r < 32 ? e0 : e1, owner);
       if (lane == owner) {
         if (r < 32) x0 = v; else x1 = v;
       }
-      if (j0 > r && j0 < R) a0 = fma(Fs[j0 * R + r], v, a0);
-      if (j1 > r && j1 < R) a1 = fma(Fs[j1 * R + r], v, a1);
+      if (j0 > r && j0 < R) e0 = fma(-Ff[j0 * R + r], v, e0);
+      if (j1 > r && j1 < R) e1 = fma(-Ff[j1 * R + r], v, e1);
     }
     if (op == 1) {
       // backward: F^T z^T = x^T, z_r = (x_r - sum_{c>r} F[c][r] z_c) / F[r][r]
-      b0 = x0;
-      b1 = x1;
-      a0 = 0.0;
-      a1 = 0.0;
+      e0 = j0 < R ? x0 * dinv[j0] : 0.0;
+      e1 = j1 < R ? x1 * dinv[j1] : 0.0;
       for (int r = R - 1; r >= 0; --r) {
         const int owner = r & 31;
-        double v = 0.0;
-        if (lane == owner) v = ((r < 32 ? b0 : b1) - (r < 32 ? a0 : a1)) * dinv[r];
-        v = __shfl_sync(0xffffffffu, v, owner);
+        const double v = __shfl_sync(0xffffffffu, r < 32 ? e0 : e1, owner);
         if (lane == owner) {
           if (r < 32) x0 = v; else x1 = v;
         }
-        if (j0 < r) a0 = fma(Fs[r * R + j0], v, a0);
-        if (j1 < r && j1 < R) a1 = fma(Fs[r * R + j1], v, a1);
+        if (j0 < r) e0 = fma(-Fb[r * R + j0], v, e0);
+        if (j1 < r && j1 < R) e1 = fma(-Fb[r * R + j1], v, e1);
       }
     }
     double* xs = Os + (size_t)lr * R;
@@ -467,7 +472,7 @@ cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, co
                              int op, double* Out, void* OutT, double* Gpart, const RowPlan& rp,
                              const ModeState* st, cudaStream_t s, int gram_rounded) {
   if (R > 64) return cudaErrorInvalidValue;
-  const size_t sm = ((size_t)R * R + R + (size_t)rp.rows_per_block * R) * sizeof(double);
+  const size_t sm = ((size_t)2 * R * R + R + (size_t)rp.rows_per_block * R) * sizeof(double);
   const int threads = 32 * std::max(1, std::min(8, rp.rows_per_block));
   if (dtype == 1) {
     if (sm > 48 * 1024)
