@@ -208,9 +208,22 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   // Sec. 4: Y0 = B_(n) S and ||B_(n)||^2 in one pass
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_INIT, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr,
                       sketch_state(c->opts.seed, j.n), j.st, 1 << 30, s));
-  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, j.pc.grid_x, I, R, c->Y64, 1, nullptr, c->Gpart,
-                             j.rp, c->spart, j.pc.grid_x * j.pc.grid_y, 0, j.st,
-                             set_norm_a ? c->norm_a2 : nullptr, s));
+#undef TALS_CK
+  return mode_init_tail(c, j, set_norm_a, j.pc.grid_x, c->spart, j.pc.grid_x * j.pc.grid_y);
+}
+
+// Y0 partials are in Ypart (gx of them), the ||B||^2 partials in sp (nsp):
+// reduce, then L0 = Q of QR(Y0).
+tals_status mode_init_tail(tals_ctx* c, const ModeJob& j, bool set_norm_a, int gx, const double* sp,
+                           int nsp) {
+  cudaStream_t s = c->stream;
+  const int R = j.R;
+  const long long I = j.v.I;
+  cudaError_t e;
+#define TALS_CK(x)                                   \
+  if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
+  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, gx, I, R, c->Y64, 1, nullptr, c->Gpart, j.rp, sp,
+                             nsp, 0, j.st, set_norm_a ? c->norm_a2 : nullptr, s));
   // L0 = Q of QR(Y0) by CholeskyQR2 (two rounds; Y0 can be ill-conditioned)
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
   TALS_CK(launch_small(c->Gfin, 1, R, 0, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s));

@@ -41,6 +41,9 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j);
 // The sweep chain after the pass: reduce, TEST (op), CholeskyQR update.
 tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int test_op);
 tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a, int bulk_max);
+uint64_t sketch_state(uint64_t seed, int mode);
+tals_status mode_init_tail(tals_ctx* c, const ModeJob& j, bool set_norm_a, int gx, const double* sp,
+                           int nsp);
 tals_status read_states(tals_ctx* c);
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a);
 tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters);

@@ -91,7 +91,10 @@ cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int res
 // Tensor-core (tcgen05, BF16) sweep pass; see tc_pass.cu.
 bool tc_supported(const ModeView& v, int R);
 cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
-                           double* spart, int* err, int grid, cudaStream_t s);
-cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s);
+                           double* spart, int* err, int grid, cudaStream_t s, int init = 0,
+                           uint64_t sketch = 0);
+cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s,
+                           double* sq = nullptr);
+int to_bf16_blocks(size_t n, int sms);
 
 }  // namespace tals

@@ -22,6 +22,8 @@ struct MixedState {
   void* shadow = nullptr;       // BF16 copy of A
   size_t shadow_elems = 0;
   int* err = nullptr;           // tensor-core pass error flag
+  double* sq = nullptr;         // per-block ||A||^2 partials of the conversion
+  int sq_n = 0;
   const void* converted = nullptr;
 };
 
@@ -33,6 +35,9 @@ tals_status mixed_alloc(tals_ctx* c) {
   cudaError_t e = cudaMallocAsync(&c->mixed->shadow, n * 2, c->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&c->mixed->err, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->mixed->err, 0, sizeof(int), c->stream);
+  c->mixed->sq_n = to_bf16_blocks(n, c->sms);
+  if (e == cudaSuccess)
+    e = cudaMallocAsync((void**)&c->mixed->sq, (size_t)c->mixed->sq_n * sizeof(double), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 shadow allocation");
   c->mixed->shadow_elems = n;
   return TALS_OK;
@@ -42,6 +47,7 @@ void mixed_free(tals_ctx* c) {
   if (!c->mixed) return;
   if (c->mixed->shadow) cudaFreeAsync(c->mixed->shadow, c->stream);
   if (c->mixed->err) cudaFreeAsync(c->mixed->err, c->stream);
+  if (c->mixed->sq) cudaFreeAsync(c->mixed->sq, c->stream);
   delete c->mixed;
   c->mixed = nullptr;
 }
@@ -57,15 +63,24 @@ tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   }
   cudaStream_t s = c->stream;
   cudaError_t e;
-  // BF16 copy of the tensor (once per decomposition call)
-  e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms, s);
-  if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
-  if ((st = mode_init_launch_bulk(c, j, set_norm_a, c->opts.bulk_sweeps)) != TALS_OK) return st;
   // one CTA per SM, within the capacity of the per-CTA partial buffers
   int grid = std::min<int>(c->sms, (int)((j.v.J() + 127) / 128));
   grid = (int)std::min<size_t>((size_t)grid, c->ypart_elems / ((size_t)j.v.I * j.R));
   grid = (int)std::min<size_t>((size_t)grid, c->spart_n);
   if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
+  // BF16 copy of the tensor and ||A||^2 of the FP32 data in one read
+  e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms, s,
+                     c->mixed->sq);
+  if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
+  // Sec. 4 init on the tensor cores: Y0 = B S over the BF16 copy (the sketch in
+  // BF16 too: any full-rank start serves, Thm. 2)
+  e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s, c->opts.bulk_sweeps);
+  if (e == cudaSuccess)
+    e = launch_tc_pass(c->mixed->shadow, j.v, j.R, nullptr, (float*)c->Ypart, c->spart,
+                       c->mixed->err, grid, s, 1, sketch_state(c->opts.seed, j.n));
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core init pass");
+  if ((st = mode_init_tail(c, j, set_norm_a, grid, c->mixed->sq, c->mixed->sq_n)) != TALS_OK)
+    return st;
   for (int k = 0; k < c->opts.max_sweeps; ++k) {
     if ((st = read_states(c)) != TALS_OK) return st;
     const ModeState& ms = c->st_host[j.n];

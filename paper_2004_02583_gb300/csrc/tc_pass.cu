@@ -43,6 +43,8 @@ struct TcArgs {
   float* Ypart;                // [gridDim.x][I][R]
   double* spart;               // [gridDim.x]
   int* err;                    // error flag (timeout)
+  int init;                    // Sec. 4 init: W_t is the seeded sketch S_t, no GEMM1
+  uint64_t sketch;             // sketch state (seed and mode)
 };
 
 namespace {
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int ft = tid < 128 ? tid : tid - 32;   // 0..191
     constexpr int kFill = kTcThreads - 32;
     constexpr int kUn = 4;
-    const int nunits = (a.I / 8) * RP;
+    const int nunits = a.init ? 0 : (a.I / 8) * RP;   // no basis operand in the init pass
     for (int u0 = ft; u0 < nunits; u0 += kFill * kUn) {
       float x[kUn][8];
 #pragma unroll
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int slot = 0;
     uint32_t ph = 0;
     bool ok = true;
-    for (long long lt = 0; lt < nt && ok; ++lt) {
+    for (long long lt = 0; lt < nt && ok && !a.init; ++lt) {
       const int wb = (int)(lt & 1);
       const uint32_t use = (uint32_t)(lt >> 1);
       if (lt >= 2) ok = mbar_wait_b(su32(&wfree[wb]), (use - 1) & 1u, vfail);
@@ -399,6 +401,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const int wb = (int)(lt & 1);
       const uint32_t use = (uint32_t)(lt >> 1);
+      if (a.init) {
+        // Sec. 4: W_t = S restricted to the tile's columns, drawn from the
+        // counter-based generator (entry (j, r) from output j R + r)
+        if (lt >= 2) ok = mbar_wait_b(su32(&opfree[wb]), (use - 1) & 1u, vfail);
+        if (!ok) break;
+        if (wrow) {
+          const long long j = (blockIdx.x + lt * gridDim.x) * kTcCols + m;
+          unsigned char* wrowp = wop + (size_t)wb * RP * 128 + (m & 7) * 2;
+          const int c8 = m >> 3;
+#pragma unroll 4
+          for (int r = 0; r < RP; ++r) {
+            const float w = r < a.R ? sketch_entry(a.sketch, (uint64_t)j, a.R, r) : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(wrowp + r * 128 + ((c8 ^ (r & 7)) << 4)) =
+                __float2bfloat16_rn(w);
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(su32(&opfull[wb]));
+        continue;
+      }
       ok = mbar_wait_b(su32(&wfull[wb]), use & 1u, vfail);
       if (!ok) break;
       fence_after();
@@ -577,7 +599,8 @@ bool tc_make_ymap(float* Ypart, int R, long long rows, CUtensorMap* map) {
 }
 
 cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
-                           double* spart, int* err, int grid, cudaStream_t s) {
+                           double* spart, int* err, int grid, cudaStream_t s, int init,
+                           uint64_t sketch) {
   if (!tc_supported(v, R)) return cudaErrorInvalidValue;
   CUtensorMap map;
   if (!tc_make_map(Xb, v, &map)) return cudaErrorInvalidValue;
@@ -594,6 +617,8 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
   a.Ypart = Ypart;
   a.spart = spart;
   a.err = err;
+  a.init = init;
+  a.sketch = sketch;
   const int ns = tc_slots(v.I, RP);
   if (ns < v.I / kTcRows) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(v.I, RP, ns);
@@ -621,25 +646,55 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
 }
 
 // FP32 -> BF16 copy (round to nearest even), vectorised by 4.
-__global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t n) {
+// FP32 -> BF16 copy (round to nearest even), vectorised by 4. With sq != null
+// each block also writes the FP64 sum of squares of the FP32 elements it read
+// (||B||^2 for the stop rule, from the original data): exact products
+// (x^2 = p + e via FMA) in a Neumaier-compensated FP32 sum per thread, then a
+// fixed-order FP64 block sum.
+__global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t n,
+                               double* __restrict__ sq) {
+  __shared__ double red[32];
   const size_t i4 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   const size_t stride = (size_t)gridDim.x * blockDim.x * 4;
+  float hi = 0.f, lo = 0.f;
+  auto acc = [&](float v) {
+    const float p = v * v, pe = fmaf(v, v, -p);
+    const float t = hi + p;
+    lo += (hi >= p ? (hi - t) + p : (p - t) + hi) + pe;
+    hi = t;
+  };
   for (size_t i = i4; i < n; i += stride) {
     if (i + 3 < n) {
       const float4 v = *reinterpret_cast<const float4*>(x + i);
-      __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-      *reinterpret_cast<__nv_bfloat162*>(y + i) = lo;
-      *reinterpret_cast<__nv_bfloat162*>(y + i + 2) = hi;
+      __nv_bfloat162 l2 = __floats2bfloat162_rn(v.x, v.y), h2 = __floats2bfloat162_rn(v.z, v.w);
+      *reinterpret_cast<__nv_bfloat162*>(y + i) = l2;
+      *reinterpret_cast<__nv_bfloat162*>(y + i + 2) = h2;
+      if (sq) {
+        acc(v.x);
+        acc(v.y);
+        acc(v.z);
+        acc(v.w);
+      }
     } else {
-      for (size_t k = i; k < n; ++k) y[k] = __float2bfloat16_rn(x[k]);
+      for (size_t k = i; k < n; ++k) {
+        y[k] = __float2bfloat16_rn(x[k]);
+        if (sq) acc(x[k]);
+      }
     }
+  }
+  if (sq) {
+    const double t = block_sum((double)hi + (double)lo, red);
+    if (threadIdx.x == 0) sq[blockIdx.x] = t;
   }
 }
 
-cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s) {
+int to_bf16_blocks(size_t n, int sms) {
   const int threads = 256;
-  const long long blocks = std::min<long long>((long long)sms * 8, (long long)((n / 4 + threads - 1) / threads) + 1);
-  to_bf16_kernel<<<(unsigned)blocks, threads, 0, s>>>(x, (__nv_bfloat16*)y, n);
+  return (int)std::min<long long>((long long)sms * 8, (long long)((n / 4 + threads - 1) / threads) + 1);
+}
+
+cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s, double* sq) {
+  to_bf16_kernel<<<(unsigned)to_bf16_blocks(n, sms), 256, 0, s>>>(x, (__nv_bfloat16*)y, n, sq);
   return cudaGetLastError();
 }
 

@@ -80,5 +80,9 @@ def test_mixed_st_hosvd_matches_oracle(tals):
     ref2 = O.st_hosvd_als(a64, ranks, eta=1e-6, seed=3, order=[0, 1, 2])
     rel2 = O.rel_error(a64, G2.double().cpu().numpy(), [u.double().cpu().numpy() for u in Us2])
     assert abs(rel2 - O.rel_error(a64, ref2.G, ref2.U)) <= 1e-6
+    for n in range(3):
+        assert O.principal_angles(Us2[n].double().cpu().numpy(), ref2.U[n]).max() <= 1e-4
+    # the reported error rests on ||A||^2 taken during the BF16 conversion
+    assert abs(st2["rel_err"] - rel2) <= 1e-6
     assert st2["bulk_sweeps"][0] >= 1
     assert st2["sweeps"][0] >= st2["bulk_sweeps"][0] + 2   # at least two FP32 sweeps finish
