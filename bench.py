@@ -7,6 +7,11 @@ decomposition (all modes: initial guess, ALS sweeps until the stop rule, the
 truncations) -- one graph launch through the C ABI. The input (512 MiB) is
 larger than L2, so no flush is needed between steps.
 
+The timed path is the mixed-precision one (BF16 tensor-core bulk sweeps, FP32
+finishing sweeps, FP64 small algebra); the plain FP32 path is timed in the same
+run and reported beside it with both errors ("mixed vs FP32 plain at equal
+error"). --precision native makes the plain path the timed one.
+
 Prints one JSON line (see the keys below). Under torchrun each rank runs an
 independent replica on its own GPU (weak scaling, no collective on the data
 path); the time is the max over ranks.
@@ -26,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at equal error"
+# DRAM bytes (read + write) per launch of the two passes on the 512^3 mode-1 view,
+# from ncu captures of the 512x512x256 case scaled by 2 (traffic grows with the
+# columns processed): profiles/pass_kernel_sweep_512x512x256.md and
+# profiles/tc_pass_512x512x256.md. None until a capture of the current kernel.
+PASS_TRAFFIC = None
+TC_TRAFFIC = None
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
@@ -172,7 +183,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tals", choices=["tals", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="native", choices=["native", "mixed_bf16"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["native", "mixed_bf16"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--dims", default=None, help="override tensor sizes (profiling), e.g. 512,512,256")
     ap.add_argument("--no-graph", action="store_true",
@@ -241,9 +252,32 @@ def main():
         dist.barrier()
     clk = clocks.stop() if rank == 0 else {}
 
-    # dominant kernel: the mode-1 sweep pass over the full tensor, timed with CUDA
-    # events on the stream it is launched on, same configuration as inside the step
-    pass_ms, pass_bytes, pass_flops = ctx.time_pass(mode=st["order"][0], iters=10)
+    # the other precision path on the same input, for the equal-error comparison
+    other = "native" if args.precision == "mixed_bf16" else "mixed_bf16"
+    octx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=other, use_graph=not args.no_graph)
+    for _ in range(3):
+        octx.st_hosvd(G, Us)
+    torch.cuda.synchronize()
+    oev0 = torch.cuda.Event(enable_timing=True)
+    oev1 = torch.cuda.Event(enable_timing=True)
+    oev0.record(stream)
+    for _ in range(args.steps):
+        _, _, ost = octx.st_hosvd(G, Us)
+    oev1.record(stream)
+    torch.cuda.synchronize()
+    o_ms = oev0.elapsed_time(oev1) / args.steps
+    # re-run the timed path once so G and U hold its result
+    _, _, st = ctx.st_hosvd(G, Us)
+    nctx = ctx if args.precision == "native" else octx
+    mctx = ctx if args.precision == "mixed_bf16" else octx
+
+    # dominant kernel (largest share of the step in both paths): the CUDA-core FP32
+    # sweep pass over the full tensor (mode-1 view), timed with CUDA events on the
+    # stream it is launched on, same configuration as inside the step
+    pass_ms, pass_bytes, pass_flops = nctx.time_pass(mode=st["order"][0], iters=10)
+    # the tensor-core BF16 pass of the mixed path's bulk sweeps
+    tc_ms, tc_bytes, tc_flops = mctx.time_pass(mode=st["order"][0], iters=10)
+    octx_close = octx.close
 
     # end to end through the C ABI with host buffers (H2D of A, D2H of G and U)
     e_ms, h2d, d2h = None, 0, 0
@@ -275,35 +309,46 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
     achieved_tflops = pass_flops / (pass_ms * 1e-3) / 1e12
-    if args.precision == "native":
-        # CUDA-core pass: 152 SMs x 128 FP32 FMA x 2 flops x SM clock
-        comp_kind, comp_peak = "alu", sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-        comp_src = "FP32 FMA peak from SM count x median SM clock"
-    else:
-        # tensor-core pass (BF16): the measured dense BF16 burst peak
-        comp_kind, comp_peak = "tensor", float(peaks.get("bf16_tflops", 1900.0))
-        comp_src = "dense BF16 burst peak"
-    comp_frac = achieved_tflops / comp_peak
+    # CUDA-core pass: 152 SMs x 128 FP32 FMA x 2 flops x SM clock (an ALU roofline)
+    alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    comp_frac = achieved_tflops / alu_peak
     hbm_frac = achieved_gbs / hbm
-    bound_comp = comp_frac > hbm_frac
     roofline = {
-        "bound": comp_kind if bound_comp else "hbm",
-        "achieved": round(achieved_tflops if bound_comp else achieved_gbs, 2),
-        "peak": round(comp_peak if bound_comp else hbm, 2),
-        "unit": "TFLOP/s" if bound_comp else "GB/s",
-        "frac": round(comp_frac if bound_comp else hbm_frac, 4),
-        "traffic": None,
-        "kernel": ("tals::pass_kernel<float,32,2,16,512> (CUDA-core FP32 sweep" if args.precision == "native"
-                   else "tals::tc_pass_kernel<32> (tcgen05 BF16 sweep") + ", mode-1 view 1 x 512 x 262144)",
+        "bound": "alu",
+        "achieved": round(achieved_tflops, 2),
+        "peak": round(alu_peak, 2),
+        "unit": "TFLOP/s",
+        "frac": round(comp_frac, 4),
+        "traffic": PASS_TRAFFIC,
+        "kernel": "tals::pass_kernel<float,32,4,16,256> (CUDA-core FP32 fused sweep, mode-1 view "
+                  "1 x 512 x 262144; the largest share of the step in both precision paths)",
+        "algorithmic_bytes": pass_bytes, "algorithmic_flops": pass_flops,
         "hbm_gbs_achieved": round(achieved_gbs, 1),
         "hbm_frac": round(hbm_frac, 4),
-        "compute_tflops_achieved": round(achieved_tflops, 2),
-        "compute_frac": round(comp_frac, 4),
         "pass_ms": round(pass_ms, 4),
-        "peak_source": f"{peak_kind} HBM {hbm} GB/s (of measured); {comp_src}",
+        "peak_source": f"FP32 FMA peak from {sms} SMs x 128 lanes x 2 flops x median SM clock "
+                       f"{sm_mhz} MHz (derived); HBM {hbm} GB/s ({peak_kind})",
     }
-    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep
-    launches = sum(10 + 9 * s for s in st["sweeps"])
+    tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
+    tc_tflops = tc_flops / (tc_ms * 1e-3) / 1e12
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    roofline_tc = {
+        "bound": "hbm", "achieved": round(tc_gbs, 1), "peak": hbm, "unit": "GB/s",
+        "frac": round(tc_gbs / hbm, 4), "traffic": TC_TRAFFIC,
+        "kernel": "tals::tc_pass_kernel<32> (tcgen05 BF16 sweep of the mixed path's bulk sweeps, "
+                  "same view)",
+        "algorithmic_bytes": tc_bytes, "pass_ms": round(tc_ms, 4),
+        "tensor_tflops_achieved": round(tc_tflops, 2),
+        "tensor_frac": round(tc_tflops / bf16_peak, 4),
+        "peak_source": f"HBM {hbm} GB/s ({peak_kind}); dense BF16 burst {bf16_peak} TFLOP/s ({peak_kind})",
+    }
+    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep, plus the
+    # BF16 conversion of each mode that runs tensor-core sweeps
+    launches = sum(10 + 9 * s for s in st["sweeps"]) + sum(1 for b in st["bulk_sweeps"] if b > 0)
+    mixed_st = st if args.precision == "mixed_bf16" else ost
+    plain_st = st if args.precision == "native" else ost
+    mixed_ms = ms if args.precision == "mixed_bf16" else o_ms
+    plain_ms = ms if args.precision == "native" else o_ms
     value = world * 1e3 / ms
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "st-HOSVD/s", "n_gpus": world,
@@ -313,10 +358,18 @@ def main():
         "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
                                "1e-2 noise eta 1e-6", "precision": args.precision,
                    "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
-                   "rel_err": st["rel_err"], "l2": "inputs (512 MiB) larger than L2",
+                   "bulk_sweeps": st["bulk_sweeps"], "rel_err": st["rel_err"],
+                   "mixed_vs_fp32_plain": {
+                       "mixed_ms": round(mixed_ms, 4), "fp32_plain_ms": round(plain_ms, 4),
+                       "speedup": round(plain_ms / mixed_ms, 3),
+                       "mixed_rel_err": mixed_st["rel_err"], "fp32_plain_rel_err": plain_st["rel_err"],
+                       "rel_err_gap": abs(mixed_st["rel_err"] - plain_st["rel_err"]),
+                       "fp32_plain_sweeps": plain_st["sweeps"]},
+                   "l2": "inputs (512 MiB) larger than L2",
                    "driver": "host loop" if args.no_graph else "CUDA graph with device-side while",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "roofline_tc": roofline_tc,
         "e2e": None if e_ms is None else
                {"value": round(world * 1e3 / e_ms, 3), "unit": "st-HOSVD/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 3)},
@@ -328,6 +381,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = _cpu_sample()
     print(json.dumps(line), flush=True)
+    octx_close()
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
