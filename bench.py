@@ -34,9 +34,9 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # DRAM bytes (read + write) per launch of the two passes on the 512^3 mode-1 view,
 # from ncu captures of the 512x512x256 case scaled by 2 (traffic grows with the
 # columns processed): profiles/pass_kernel_sweep_512x512x256.md and
-# profiles/tc_pass_512x512x256.md. None until a capture of the current kernel.
-PASS_TRAFFIC = None
-TC_TRAFFIC = None
+# profiles/tc_pass_512x512x256.md.
+PASS_TRAFFIC = 2 * (268605952 + 14885120)   # bytes per launch
+TC_TRAFFIC = 2 * (134336000 + 3278080)
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; ncu "
                          "cannot profile kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other precision path (per-path launch lists under ncu)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
     args = ap.parse_args()
@@ -253,6 +255,10 @@ def main():
     clk = clocks.stop() if rank == 0 else {}
 
     # the other precision path on the same input, for the equal-error comparison
+    if args.no_compare:
+        ctx.close()
+        print(json.dumps({"precision": args.precision, "ms_per_step": ms, "sweeps": st["sweeps"]}))
+        return
     other = "native" if args.precision == "mixed_bf16" else "mixed_bf16"
     octx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=other, use_graph=not args.no_graph)
     for _ in range(3):
