@@ -193,9 +193,16 @@ def main():
                     help="skip the other precision path (per-path launch lists under ncu)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): 512^3 FP32 st-HOSVD, the benchmark line; c1: 64^3 FP64; "
+                         "c3: 128^4 FP32 mixed vs plain; c4: 4096 small tensors batched vs "
+                         "per-tensor loop; c5: 1024x1024x512 forward + reconstruction-loss backward")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        from_extra = {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload]
+        return from_extra(args)
     global DIMS
     if args.dims:
         DIMS = tuple(int(x) for x in args.dims.split(","))
@@ -391,6 +398,315 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The other configurations (parity cases of the test suite), measured the same
+# way: CUDA events on the launching stream, >= 3 warm-up runs, an L2 flush
+# between runs whose inputs fit in L2, the oracle timed on the host beside it.
+# ---------------------------------------------------------------------------
+
+def _clock_line(clk):
+    return {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+            "reasons": clk.get("reasons", [])}
+
+
+def _time_gpu(fn, steps, warmup, flush_bytes=0):
+    """Mean ms of fn() over `steps` runs, each bracketed by CUDA events; with
+    flush_bytes > 0 a buffer that large is written before every run (outside
+    the events) so no input stays in L2."""
+    import torch
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda") if flush_bytes else None
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    tot, out = 0.0, None
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps, out
+
+
+def _oracle_time(fn, budget_s=10.0):
+    """Repeat the oracle call until about budget_s has passed; mean seconds."""
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        fn()
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el / n * (n + 1) > 3 * budget_s:
+            return el / n, n
+
+
+def _alu_peaks(sms, sm_mhz):
+    # FP32: 128 FMA lanes per SM; FP64: the nominal 1.25 TFLOP/s of the part,
+    # scaled to the observed clock (the max SM clock is 2070 MHz)
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, 1.25 * sm_mhz / 2070.0
+
+
+def run_c1(args):
+    """64^3 FP64 st-HOSVD-ALS, rank (8,8,8), eta 1e-8."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    cfg = W.CONFIGS["st64_f64"]
+    p = W.make(cfg)
+    A = torch.from_numpy(p.A).cuda()
+    ctx = tals.Context(A, cfg.ranks, eta=cfg.eta, seed=1, precision="native")
+    G = torch.empty(cfg.ranks, dtype=torch.float64, device="cuda")
+    Us = [torch.empty((d, r), dtype=torch.float64, device="cuda") for d, r in zip(cfg.dims, cfg.ranks)]
+    clocks = Clocks(0)
+    clocks.start()
+    ms, (_, _, st) = _time_gpu(lambda: ctx.st_hosvd(G, Us), args.steps, args.warmup, 256 << 20)
+    clk = clocks.stop()
+    pass_ms, by, fl = ctx.time_pass(mode=st["order"][0], iters=20)
+    ref = O.st_hosvd_als(p.A, cfg.ranks, eta=cfg.eta, seed=1)
+    rel_own = O.rel_error(p.A, G.cpu().numpy(), [u.cpu().numpy() for u in Us])
+    rel_ref = O.rel_error(p.A, ref.G, ref.U)
+    ang = max(float(O.principal_angles(u.cpu().numpy(), r).max()) for u, r in zip(Us, ref.U))
+    sec, n = _oracle_time(lambda: O.st_hosvd_als(p.A, cfg.ranks, eta=cfg.eta, seed=1))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    _, fp64_peak = _alu_peaks(sms, clk.get("sm_mhz") or 2070.0)
+    tf = fl / (pass_ms * 1e-3) / 1e12
+    line = {"metric": "st-HOSVD-ALS time-to-tol (64^3 FP64)", "value": round(1e3 / ms, 2),
+            "unit": "st-HOSVD/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "st-HOSVD-ALS 64x64x64 FP64 rank (8,8,8) Gaussian core 1e-3 noise "
+                                   "eta 1e-8", "sweeps": st["sweeps"], "l2": "L2 flushed between steps",
+                       "rel_err": rel_own, "oracle_rel_err": rel_ref, "rel_err_gap": abs(rel_own - rel_ref),
+                       "max_principal_angle": ang},
+            "roofline": {"bound": "alu", "achieved": round(tf, 4), "peak": round(fp64_peak, 3),
+                         "unit": "TFLOP/s", "frac": round(tf / fp64_peak, 4), "traffic": None,
+                         "kernel": "tals::pass_kernel<double,...> (FP64 fused sweep, first mode, "
+                                   "L2-resident when timed alone)",
+                         "pass_ms": round(pass_ms, 5), "algorithmic_bytes": by, "algorithmic_flops": fl,
+                         "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the SM clock"},
+            "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": round(1.0 / sec, 2), "unit": "st-HOSVD/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"the full 64^3 decomposition, {n} runs"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def _pass_rooflines(nctx, mctx, mode, sm_mhz, sms, peaks):
+    pms, pby, pfl = nctx.time_pass(mode=mode, iters=10)
+    tms, tby, tfl = mctx.time_pass(mode=mode, iters=10)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu, _ = _alu_peaks(sms, sm_mhz)
+    ptf = pfl / (pms * 1e-3) / 1e12
+    pgb = pby / (pms * 1e-3) / 1e9
+    tgb = tby / (tms * 1e-3) / 1e9
+    roof = {"bound": "alu" if ptf / alu > pgb / hbm else "hbm",
+            "achieved": round(ptf, 2) if ptf / alu > pgb / hbm else round(pgb, 1),
+            "peak": round(alu, 2) if ptf / alu > pgb / hbm else hbm,
+            "unit": "TFLOP/s" if ptf / alu > pgb / hbm else "GB/s",
+            "frac": round(max(ptf / alu, pgb / hbm), 4), "traffic": None,
+            "kernel": "tals::pass_kernel<float,...> (CUDA-core FP32 fused sweep, first mode)",
+            "pass_ms": round(pms, 4), "hbm_gbs_achieved": round(pgb, 1),
+            "alu_tflops_achieved": round(ptf, 2)}
+    roof_tc = {"bound": "hbm", "achieved": round(tgb, 1), "peak": hbm, "unit": "GB/s",
+               "frac": round(tgb / hbm, 4), "traffic": None,
+               "kernel": "tals::tc_pass_kernel (tcgen05 BF16 sweep, first mode)", "pass_ms": round(tms, 4)}
+    return roof, roof_tc
+
+
+def run_c3(args):
+    """128^4 FP32 rank (16,16,16,16), 0.8^k spectrum, 1e-3 noise: mixed vs plain."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    cfg = W.CONFIGS["q128_f32"]
+    p = W.make(cfg)
+    A = torch.from_numpy(p.A).cuda()
+    peaks, _ = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    G = torch.empty(cfg.ranks, device="cuda")
+    Us = [torch.empty((d, r), device="cuda") for d, r in zip(cfg.dims, cfg.ranks)]
+    res = {}
+    clocks = Clocks(0)
+    clocks.start()
+    ctxs = {}
+    for prec in ("mixed_bf16", "native"):
+        ctx = tals.Context(A, cfg.ranks, eta=cfg.eta, seed=1, precision=prec)
+        ms, (_, _, st) = _time_gpu(lambda: ctx.st_hosvd(G, Us), args.steps, args.warmup)
+        res[prec] = (ms, st)
+        ctxs[prec] = ctx
+    clk = clocks.stop()
+    roof, roof_tc = _pass_rooflines(ctxs["native"], ctxs["mixed_bf16"], res["native"][1]["order"][0],
+                                    clk.get("sm_mhz") or 2070.0, sms, peaks)
+    # oracle on a 128^3 x S slab of the same recipe, scaled to the full tensor
+    S = 16
+    q = W.planted(cfg.seed, cfg.dims[:3] + (S,), cfg.ranks, cfg.core, cfg.noise_rel, dtype=np.float32)
+    a64 = q.A.astype(np.float64)
+    sec, n = _oracle_time(lambda: O.st_hosvd_als(a64, cfg.ranks, eta=cfg.eta, seed=1), 10.0)
+    mms, mst = res["mixed_bf16"]
+    pms, pst = res["native"]
+    line = {"metric": "st-HOSVD-ALS time-to-tol, mixed vs FP32 plain at equal error (128^4)",
+            "value": round(1e3 / mms, 3), "unit": "st-HOSVD/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(mms, 4), "higher_is_better": True,
+            "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": "st-HOSVD-ALS 128^4 FP32 rank (16,16,16,16) 0.8^k spectrum 1e-3 "
+                                   "noise eta 1e-6", "l2": "inputs (1 GiB) larger than L2",
+                       "mixed_ms": round(mms, 4), "fp32_plain_ms": round(pms, 4),
+                       "speedup": round(pms / mms, 3), "mixed_rel_err": mst["rel_err"],
+                       "fp32_plain_rel_err": pst["rel_err"],
+                       "rel_err_gap": abs(mst["rel_err"] - pst["rel_err"]),
+                       "sweeps": mst["sweeps"], "bulk_sweeps": mst["bulk_sweeps"],
+                       "fp32_plain_sweeps": pst["sweeps"]},
+            "roofline": roof, "roofline_tc": roof_tc, "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": (S / 128.0) / sec, "unit": "st-HOSVD/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle on a 128^3 x {S} slab ({sec:.1f} s, {n} runs), "
+                                       f"scaled by {S}/128"}}
+    print(json.dumps(line), flush=True)
+    for c in ctxs.values():
+        c.close()
+
+
+def run_c4(args):
+    """4096 small FP32 tensors (modes ~ U{16..96}, ranks ~ U{4..16}): one batched
+    graph-captured launch vs a per-tensor loop of the plain path."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    count, eta = 4096, 1e-6
+    items = W.batched(W.SEED_BASE + 3, count)
+    As = [torch.from_numpy(a).cuda() for a, _, _ in items]
+    ranks = [r for _, _, r in items]
+    clocks = Clocks(0)
+    clocks.start()
+    ms, (Gs, Us, sts) = _time_gpu(lambda: tals.batched_st_hosvd(As, ranks, eta=eta, seed=1),
+                                  args.steps, args.warmup)
+    clk = clocks.stop()
+    # algorithmic bytes: every pass (initial guess + sweeps) reads the current tensor
+    byt = 0
+    for (a, dims, rk), st in zip(items, sts):
+        cur = list(dims)
+        for n in st["order"]:
+            byt += (st["sweeps"][n] + 1) * int(np.prod(cur)) * 4
+            cur[n] = rk[n]
+    gbs = byt / (ms * 1e-3) / 1e9
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # per-tensor loop of the plain path on a subset, contexts made beforehand
+    sub = 256
+    ctxs = [tals.Context(As[t], ranks[t], eta=eta, seed=1) for t in range(sub)]
+    loop_ms, _ = _time_gpu(lambda: [c.st_hosvd() for c in ctxs], 1, 1)
+    loop_ms *= count / sub
+    for c in ctxs:
+        c.close()
+    # parity on a few tensors against the oracle
+    gaps = []
+    for t in range(8):
+        a, dims, rk = items[t]
+        ref = O.st_hosvd_als(a.astype(np.float64), rk, eta=eta, seed=1)
+        own = O.rel_error(a.astype(np.float64), Gs[t].double().cpu().numpy(),
+                          [u.double().cpu().numpy() for u in Us[t]])
+        gaps.append(abs(own - O.rel_error(a.astype(np.float64), ref.G, ref.U)))
+    osub = 64
+    sec, n = _oracle_time(lambda: [O.st_hosvd_als(items[t][0].astype(np.float64), items[t][2], eta=eta,
+                                                  seed=1) for t in range(osub)], 10.0)
+    line = {"metric": "batched st-HOSVD-ALS throughput (4096 uneven small tensors)",
+            "value": round(count * 1e3 / ms, 1), "unit": "tensors/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4096 x st-HOSVD-ALS FP32, I ~ U{16..96}, R ~ U{4..16}, 1e-2 noise, "
+                                   "eta 1e-6, one persistent graph-captured launch",
+                       "total_input_bytes": int(sum(a.nbytes for a, _, _ in items)),
+                       "l2": "inputs (GBs) larger than L2",
+                       "per_tensor_loop_ms": round(loop_ms, 2),
+                       "per_tensor_loop_sample": f"{sub} tensors, scaled by {count}/{sub}",
+                       "speedup_vs_loop": round(loop_ms / ms, 2),
+                       "max_rel_err_gap_vs_oracle_8_tensors": max(gaps)},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(gbs / hbm, 4), "traffic": None,
+                         "kernel": "tals::batched_kernel (whole decomposition per CTA; algorithmic "
+                                   "bytes = one read of the current tensor per pass)",
+                         "algorithmic_bytes": byt},
+            "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": round(osub / sec, 2), "unit": "tensors/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle on the first {osub} tensors ({sec:.1f} s)"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_c5(args):
+    """1024x1024x512 FP32, rank (64,64,32): st-HOSVD-ALS forward, then the gradient
+    of ||A - G x1 U1 x2 U2 x3 U3||^2 w.r.t. A and the factors through the
+    projection / reconstruction kernels and their hand-written adjoints."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    cfg = W.CONFIGS["d1024_f32"]
+    p = W.make(cfg)
+    A = torch.from_numpy(p.A).cuda()
+    peaks, _ = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    clocks = Clocks(0)
+    clocks.start()
+    ctx = tals.Context(A, cfg.ranks, eta=cfg.eta, seed=1, precision="native")
+    fwd_ms, (G, Us, st) = _time_gpu(lambda: ctx.st_hosvd(), args.steps, args.warmup)
+    Us = [u.detach().clone() for u in Us]
+
+    def loss_and_grad():
+        Ar = A.detach().requires_grad_(True)
+        Ur = [u.detach().requires_grad_(True) for u in Us]
+        B = tals.tucker_reconstruct(tals.tucker_project(Ar, Ur), Ur)
+        loss = ((Ar - B) ** 2).sum()
+        loss.backward()
+        return Ar.grad, [u.grad for u in Ur]
+
+    bwd_ms, _ = _time_gpu(loss_and_grad, max(3, args.steps // 2), args.warmup)
+    # the reconstruction alone (writes the 2 GiB tensor): HBM-bound roofline
+    Gd = G.detach().contiguous()
+    rec_ms, _ = _time_gpu(lambda: tals.reconstruct(Gd, Us), args.steps, args.warmup)
+    clk = clocks.stop()
+    rec_bytes = A.numel() * 4 + Gd.numel() * 4 + sum(u.numel() * 4 for u in Us)
+    gbs = rec_bytes / (rec_ms * 1e-3) / 1e9
+    # oracle: the loss gradient on a 1024 x 1024 x S slab, scaled
+    S = 8
+    a_s = p.A[:, :, :S].astype(np.float64)
+    us_np = [u.double().cpu().numpy() for u in Us]
+    us_s = [us_np[0], us_np[1], np.linalg.qr(us_np[2][:S])[0][:, :min(S, cfg.ranks[2])]]
+    sec, n = _oracle_time(lambda: O.recon_loss_grad(a_s, us_s), 10.0)
+    line = {"metric": "st-HOSVD-ALS forward + reconstruction-loss backward (1024x1024x512)",
+            "value": round(1e3 / (fwd_ms + bwd_ms), 3), "unit": "forward+backward/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(fwd_ms + bwd_ms, 3),
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1024x1024x512 FP32 rank (64,64,32) 1/k spectrum 1e-2 noise eta 1e-6",
+                       "forward_ms": round(fwd_ms, 3), "backward_ms": round(bwd_ms, 3),
+                       "sweeps": st["sweeps"], "rel_err": st["rel_err"],
+                       "l2": "inputs (2 GiB) larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(gbs / hbm, 4), "traffic": None,
+                         "kernel": "reconstruct (B = G x1 U1 x2 U2 x3 U3, the 2 GiB write of the "
+                                   "backward's largest pass)", "pass_ms": round(rec_ms, 3),
+                         "algorithmic_bytes": rec_bytes},
+            "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": round((S / 512.0) / sec, 4), "unit": "loss-gradients/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle loss gradient on a 1024x1024x{S} slab "
+                                       f"({sec:.1f} s, {n} runs), scaled by {S}/512"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 if __name__ == "__main__":

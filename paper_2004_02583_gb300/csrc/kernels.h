@@ -93,6 +93,10 @@ bool tc_supported(const ModeView& v, int R);
 cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
                            double* spart, int* err, int grid, cudaStream_t s, int init = 0,
                            uint64_t sketch = 0);
+// out[p, a, q] = sum_b M[a*sa + b*sb] X[p, b, q] (FP32; cudaErrorNotSupported for
+// views other than Q >= 64 or Q == 1).
+cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,
+                             long long sa, long long sb, long long Aout, float* out, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s,
                            double* sq = nullptr);
 int to_bf16_blocks(size_t n, int sms);

@@ -65,6 +65,13 @@ size_t numel(const long long* d, int N) {
 tals_status apply_mode(OpCtx& o, const void* X, const long long* d, int n, const void* L,
                        int R_out, void* out) {
   ModeView v = view_of(d, o.N, n);
+  if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1)) {
+    // register-tiled mode product: M = L^T, element (a, b) = L[b * R_out + a]
+    cudaError_t e = launch_mode_gemm((const float*)X, v.P, v.I, v.Q, (const float*)L, 1, R_out, R_out,
+                                     (float*)out, o.s);
+    if (e == cudaSuccess) return TALS_OK;
+    if (e != cudaErrorNotSupported) return cuda_fail(e, "mode product");
+  }
   PassConfig pc = pass_config(o.dtype, v, R_out, o.sms);
   if (!pc.ok) return fail(TALS_ENOTSUP, "mode product of mode %d (size %lld -> %d) exceeds the "
                           "kernel limits", n, v.I, R_out);
@@ -241,14 +248,34 @@ tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
   cudaError_t e;
   for (size_t k = 0; k < ord.size(); ++k) {
     const int m = ord[k];
+    long long nd[TALS_MAX_NDIM];
+    std::copy(d, d + o.N, nd);
+    nd[m] = o.dims[m];
+    {
+      // register-tiled expansion with M = U_m (element (i, r) = U[i * R + r])
+      ModeView v = view_of(d, o.N, m);
+      if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1)) {
+        void* dst = B_out;
+        if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
+        if (e != cudaSuccess) return cuda_fail(e, "scratch");
+        e = launch_mode_gemm((const float*)cur, v.P, v.I, v.Q, (const float*)o.U[m], o.ranks[m], 1,
+                             o.dims[m], (float*)dst, o.s);
+        if (e == cudaSuccess) {
+          if (owned) o.sc->release(owned);
+          owned = (dst == B_out) ? nullptr : dst;
+          cur = dst;
+          d[m] = o.dims[m];
+          continue;
+        }
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "expansion");
+        if (dst != B_out) o.sc->release(dst);
+      }
+    }
     // expand mode m: X x_m U_m = X x_m (U_m^T)^T with L = U_m^T (R_m x I_m)
     void* Lt = o.sc->get((size_t)o.dims[m] * o.ranks[m] * o.esz, &e);
     if (e != cudaSuccess) return cuda_fail(e, "scratch");
     e = launch_transpose(o.dtype, o.U[m], o.dims[m], o.ranks[m], Lt, o.s);
     if (e != cudaSuccess) return cuda_fail(e, "transpose");
-    long long nd[TALS_MAX_NDIM];
-    std::copy(d, d + o.N, nd);
-    nd[m] = o.dims[m];
     void* dst = B_out;
     if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
     if (e != cudaSuccess) return cuda_fail(e, "scratch");
