@@ -470,8 +470,7 @@ static void fill_mode_stats(tals_ctx* c, int n, tals_stats* st) {
 
 tals_status st_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* stats) {
   if (!c || !G_out) return fail(TALS_EINVAL, "ctx and G_out must not be NULL");
-  if (c->opts.use_graph && c->opts.precision == TALS_PREC_NATIVE)
-    return st_hosvd_graph(c, G_out, U_out, stats);
+  if (c->opts.use_graph) return st_hosvd_graph(c, G_out, U_out, stats);
   const int N = c->N;
   long long d[TALS_MAX_NDIM];
   for (int m = 0; m < N; ++m) d[m] = c->dims[m];
@@ -519,8 +518,7 @@ tals_status t_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st
   if (!U_out) return fail(TALS_EINVAL, "t_hosvd needs U_out (the projections read the factors)");
   for (int n = 0; n < c->N; ++n)
     if (!U_out[n]) return fail(TALS_EINVAL, "U_out[%d] is NULL", n);
-  if (c->opts.use_graph && c->opts.precision == TALS_PREC_NATIVE)
-    return t_hosvd_graph(c, G_out, U_out, stats);
+  if (c->opts.use_graph) return t_hosvd_graph(c, G_out, U_out, stats);
   const int N = c->N;
   tals_stats local;
   std::memset(&local, 0, sizeof(local));

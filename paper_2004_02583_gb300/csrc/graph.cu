@@ -2,7 +2,8 @@
 //
 // Per mode the graph holds the initial-guess chain (Sec. 4) followed by a
 // conditional WHILE node whose body is one ALS sweep (one tensor pass plus the
-// small FP64 kernels). The stop rule (Eq. 5.01) is evaluated on the device by
+// small FP64 kernels); mixed-precision modes have a first WHILE node of
+// tensor-core bulk sweeps. The stop rule (Eq. 5.01) is evaluated on the device by
 // the single-CTA TEST kernel, which clears the loop condition when the mode is
 // done, so a full st-HOSVD-ALS or t-HOSVD-ALS runs with no host round trip.
 // Graphs are built once per context and output-pointer set and replayed.
@@ -39,16 +40,12 @@ tals_status ensure_streams(tals_ctx* c) {
   return TALS_OK;
 }
 
-// Capture, on c->cap[0] (already capturing), the init chain, the WHILE node
-// and the factor copy of one mode.
-tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) {
-  tals_status st = mode_setup(c, j);
-  if (st != TALS_OK) return st;
+// Append, on c->cap[0] (capturing), a conditional WHILE node whose body (captured
+// on c->cap[1]) is `body`; the loop's handle goes to j.cond for the body's TEST
+// kernel.
+template <typename Body>
+tals_status capture_while(tals_ctx* c, ModeJob& j, Body body) {
   cudaStream_t cs = c->cap[0];
-  c->stream = cs;
-  j.has_cond = 0;
-  if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-
   cudaStreamCaptureStatus cst;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -68,24 +65,46 @@ tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) 
   if (e != cudaSuccess) return cuda_fail(e, "while node");
   e = cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e != cudaSuccess) return cuda_fail(e, "capture dependencies");
-
-  // body: one sweep, captured on the second private stream
-  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaGraph_t bg = p.conditional.phGraph_out[0];
   cudaStream_t bs = c->cap[1];
-  e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  e = cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return cuda_fail(e, "body capture");
   c->stream = bs;
   j.cond = (unsigned long long)h;
   j.has_cond = 1;
-  st = mode_sweep_launch(c, j);
+  tals_status st = body();
   cudaGraph_t body_out = nullptr;
   e = cudaStreamEndCapture(bs, &body_out);
   c->stream = cs;
+  j.has_cond = 0;
   if (st != TALS_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "body capture end");
+  return TALS_OK;
+}
 
+// Capture, on c->cap[0] (already capturing), the init chain, the sweep loop(s)
+// and the factor copy of one mode. Modes that run mixed-precision bulk sweeps
+// get two loops: the tensor-core sweeps (left when the bulk phase ends) and the
+// FP32 sweeps (left when Eq. 5.01 fires).
+tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) {
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  cudaStream_t cs = c->cap[0];
+  c->stream = cs;
+  j.has_cond = 0;
+  if (mixed_tc_mode(c, j)) {
+    const int grid = mixed_grid(c, j);
+    if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
+    if ((st = mixed_init_launch(c, j, set_norm_a, grid)) != TALS_OK) return st;
+    if ((st = capture_while(c, j, [&] { return mixed_bulk_sweep_launch(c, j, grid); })) != TALS_OK)
+      return st;
+  } else {
+    if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
+  }
+  if ((st = capture_while(c, j, [&] { return mode_sweep_launch(c, j); })) != TALS_OK) return st;
   if (U_out) {
-    e = cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, cudaMemcpyDeviceToDevice, cs);
+    cudaError_t e =
+        cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, cudaMemcpyDeviceToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "factor copy");
   }
   return TALS_OK;
@@ -191,6 +210,7 @@ tals_status run(tals_ctx* c, int kind, void* G_out, void* const* U_out, tals_sta
   cudaError_t e = cudaGraphLaunch(en->exec, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  if ((st = mixed_check(c)) != TALS_OK) return st;
   // statistics from the pinned copies written by the graph's last nodes
   tals_stats local;
   std::memset(&local, 0, sizeof(local));

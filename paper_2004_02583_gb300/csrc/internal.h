@@ -56,6 +56,11 @@ void graphs_destroy(tals_ctx* c);
 // mixed.cu: BF16 shadow + tcgen05 bulk sweeps
 tals_status mixed_alloc(tals_ctx* c);
 void mixed_free(tals_ctx* c);
+bool mixed_tc_mode(const tals_ctx* c, const ModeJob& j);
+int mixed_grid(const tals_ctx* c, const ModeJob& j);
+tals_status mixed_init_launch(tals_ctx* c, ModeJob& j, bool set_norm_a, int grid);
+tals_status mixed_bulk_sweep_launch(tals_ctx* c, ModeJob& j, int grid);
+tals_status mixed_check(tals_ctx* c);
 tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a);
 tals_status time_tc_pass(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes,
                          double* flops);

@@ -26,6 +26,7 @@ struct PassConfig {
   size_t smem = 0;   // dynamic shared memory
   int nbuf = 2;      // tile buffers (2: cp.async double buffering)
   int nt = 256;      // threads per CTA
+  int jt = 16;       // unfolding columns per tile
   bool ok = false;
 };
 

@@ -52,53 +52,73 @@ void mixed_free(tals_ctx* c) {
   c->mixed = nullptr;
 }
 
-tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
-  tals_status st = mode_setup(c, j);
-  if (st != TALS_OK) return st;
-  const bool tc = c->mixed && j.X == c->A && c->dtype == TALS_F32 && tc_supported(j.v, j.R) &&
-                  c->opts.bulk_sweeps > 0;
-  if (!tc) {
-    if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-    return mode_loop_host(c, j, c->opts.max_sweeps);
-  }
-  cudaStream_t s = c->stream;
-  cudaError_t e;
-  // one CTA per SM, within the capacity of the per-CTA partial buffers
+// Whether mode job j runs its bulk sweeps on the tensor cores.
+bool mixed_tc_mode(const tals_ctx* c, const ModeJob& j) {
+  return c->mixed && j.X == c->A && c->dtype == TALS_F32 && tc_supported(j.v, j.R) &&
+         c->opts.bulk_sweeps > 0;
+}
+
+// One CTA per SM, within the capacity of the per-CTA partial buffers (0: no room).
+int mixed_grid(const tals_ctx* c, const ModeJob& j) {
   int grid = std::min<int>(c->sms, (int)((j.v.J() + 127) / 128));
   grid = (int)std::min<size_t>((size_t)grid, c->ypart_elems / ((size_t)j.v.I * j.R));
   grid = (int)std::min<size_t>((size_t)grid, c->spart_n);
-  if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
-  // BF16 copy of the tensor and ||A||^2 of the FP32 data in one read
-  e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms, s,
-                     c->mixed->sq);
+  return std::max(grid, 0);
+}
+
+// BF16 copy and ||A||^2 in one read, then the Sec. 4 initial guess on the tensor
+// cores: Y0 = B S over the BF16 copy (the sketch in BF16 too: any full-rank
+// start serves, Thm. 2), then L0 = Q(Y0).
+tals_status mixed_init_launch(tals_ctx* c, ModeJob& j, bool set_norm_a, int grid) {
+  cudaStream_t s = c->stream;
+  cudaError_t e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms,
+                                 s, c->mixed->sq);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
-  // Sec. 4 init on the tensor cores: Y0 = B S over the BF16 copy (the sketch in
-  // BF16 too: any full-rank start serves, Thm. 2)
   e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s, c->opts.bulk_sweeps);
   if (e == cudaSuccess)
     e = launch_tc_pass(c->mixed->shadow, j.v, j.R, nullptr, (float*)c->Ypart, c->spart,
                        c->mixed->err, grid, s, 1, sketch_state(c->opts.seed, j.n));
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core init pass");
-  if ((st = mode_init_tail(c, j, set_norm_a, grid, c->mixed->sq, c->mixed->sq_n)) != TALS_OK)
-    return st;
+  return mode_init_tail(c, j, set_norm_a, grid, c->mixed->sq, c->mixed->sq_n);
+}
+
+// One bulk sweep: the fused pass on the tensor cores, then the FP64 tail with
+// the bulk-phase test (op 2).
+tals_status mixed_bulk_sweep_launch(tals_ctx* c, ModeJob& j, int grid) {
+  cudaError_t e = launch_tc_pass(c->mixed->shadow, j.v, j.R, (const float*)c->Lt, (float*)c->Ypart,
+                                 c->spart, c->mixed->err, grid, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
+  return mode_sweep_tail(c, j, grid, grid, 2);
+}
+
+tals_status mixed_check(tals_ctx* c) {
+  if (!c->mixed) return TALS_OK;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, c->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
+  if (err) return fail(TALS_ETIMEOUT, "tensor-core pass gave up waiting (code %d)", err);
+  return TALS_OK;
+}
+
+tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  if (!mixed_tc_mode(c, j)) {
+    if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
+    return mode_loop_host(c, j, c->opts.max_sweeps);
+  }
+  const int grid = mixed_grid(c, j);
+  if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
+  if ((st = mixed_init_launch(c, j, set_norm_a, grid)) != TALS_OK) return st;
   for (int k = 0; k < c->opts.max_sweeps; ++k) {
     if ((st = read_states(c)) != TALS_OK) return st;
     const ModeState& ms = c->st_host[j.n];
     if (ms.done) break;
-    if (ms.bulk_mode) {
-      e = launch_tc_pass(c->mixed->shadow, j.v, j.R, (const float*)c->Lt, (float*)c->Ypart,
-                         c->spart, c->mixed->err, grid, s);
-      if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
-      if ((st = mode_sweep_tail(c, j, grid, grid, 2)) != TALS_OK) return st;
-    } else {
-      if ((st = mode_sweep_launch(c, j)) != TALS_OK) return st;
-    }
+    st = ms.bulk_mode ? mixed_bulk_sweep_launch(c, j, grid) : mode_sweep_launch(c, j);
+    if (st != TALS_OK) return st;
   }
-  int err = 0;
-  e = cudaMemcpyAsync(&err, c->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
-  if (err) return fail(TALS_ETIMEOUT, "tensor-core pass gave up waiting (code %d)", err);
+  if ((st = mixed_check(c)) != TALS_OK) return st;
   return read_states(c);
 }
 

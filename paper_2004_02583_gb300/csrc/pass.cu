@@ -5,13 +5,13 @@
 
 namespace tals {
 
-template <typename T, int RC, int RPT, int RW, int NT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT>
 __global__ void __launch_bounds__(NT, 1) pass_kernel(PassArgs<T> a) {
   if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* yp = a.Ypart != nullptr ? a.Ypart + (size_t)blockIdx.x * a.I * a.R : nullptr;
   const double tot =
-      pass_cta<T, RC, RPT, RW, NT>(a, blockIdx.x, gridDim.x, blockIdx.y, smem_raw, yp);
+      pass_cta<T, RC, RPT, RW, NT, JT>(a, blockIdx.x, gridDim.x, blockIdx.y, smem_raw, yp);
   if (threadIdx.x == 0) a.spart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -22,36 +22,43 @@ __global__ void __launch_bounds__(NT, 1) pass_kernel(PassArgs<T> a) {
 namespace {
 
 struct Inst {
-  int rc, rpt, rw, nt;
+  int rc, rpt, rw, nt, jt;
 };
 
 // Candidate instantiations per dtype. 512-thread shapes keep <= 128 registers
 // per thread (16 warps per SM for latency hiding); 256-thread shapes serve
 // larger per-thread tiles.
-const Inst kInstF32[] = {{32, 1, 16, 512}, {32, 2, 16, 512}, {32, 4, 16, 256},
-                         {16, 1, 16, 512}, {16, 2, 16, 512}, {16, 4, 16, 256},
-                         {8, 1, 8, 512},   {8, 2, 8, 512},   {8, 4, 8, 512},  {8, 8, 8, 256}};
-const Inst kInstF64[] = {{16, 1, 8, 256}, {16, 2, 8, 256}, {16, 4, 8, 256},
-                         {8, 1, 8, 256},  {8, 2, 8, 256},  {8, 4, 8, 256}};
+// Wider tiles (32 or 64 unfolding columns) keep the work per tile up for short
+// modes, where a 16-column tile is only a few thousand elements.
+const Inst kInstF32[] = {{32, 1, 16, 512, 16}, {32, 2, 16, 512, 16}, {32, 4, 16, 256, 16},
+                         {16, 1, 16, 512, 16}, {16, 2, 16, 512, 16}, {16, 4, 16, 256, 16},
+                         {8, 1, 8, 512, 16},   {8, 2, 8, 512, 16},   {8, 4, 8, 512, 16},
+                         {8, 8, 8, 256, 16},
+                         {32, 2, 8, 256, 64},  {16, 2, 4, 256, 64},  {16, 2, 8, 128, 64},
+                         {8, 2, 4, 128, 64},   {32, 2, 16, 256, 32}, {16, 2, 8, 256, 32}};
+const Inst kInstF64[] = {{16, 1, 8, 256, 16}, {16, 2, 8, 256, 16}, {16, 4, 8, 256, 16},
+                         {8, 1, 8, 256, 16},  {8, 2, 8, 256, 16},  {8, 4, 8, 256, 16}};
 
-template <typename T, int RC, int RPT, int RW, int NT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&pass_kernel<T, RC, RPT, RW, NT>);
+  return reinterpret_cast<void*>(&pass_kernel<T, RC, RPT, RW, NT, JT>);
 }
 
 template <typename T>
 void* lookup(const Inst& in) {
-#define TALS_CASE(RC, RPT, RW, NT)                                            \
-  if (in.rc == RC && in.rpt == RPT && in.rw == RW && in.nt == NT)             \
-    return kernel_ptr<T, RC, RPT, RW, NT>();
+#define TALS_CASE(RC, RPT, RW, NT, JT)                                               \
+  if (in.rc == RC && in.rpt == RPT && in.rw == RW && in.nt == NT && in.jt == JT)     \
+    return kernel_ptr<T, RC, RPT, RW, NT, JT>();
   if constexpr (sizeof(T) == 4) {
-    TALS_CASE(32, 1, 16, 512) TALS_CASE(32, 2, 16, 512) TALS_CASE(32, 4, 16, 256)
-    TALS_CASE(16, 1, 16, 512) TALS_CASE(16, 2, 16, 512) TALS_CASE(16, 4, 16, 256)
-    TALS_CASE(8, 1, 8, 512) TALS_CASE(8, 2, 8, 512) TALS_CASE(8, 4, 8, 512)
-    TALS_CASE(8, 8, 8, 256)
+    TALS_CASE(32, 1, 16, 512, 16) TALS_CASE(32, 2, 16, 512, 16) TALS_CASE(32, 4, 16, 256, 16)
+    TALS_CASE(16, 1, 16, 512, 16) TALS_CASE(16, 2, 16, 512, 16) TALS_CASE(16, 4, 16, 256, 16)
+    TALS_CASE(8, 1, 8, 512, 16) TALS_CASE(8, 2, 8, 512, 16) TALS_CASE(8, 4, 8, 512, 16)
+    TALS_CASE(8, 8, 8, 256, 16)
+    TALS_CASE(32, 2, 8, 256, 64) TALS_CASE(16, 2, 4, 256, 64) TALS_CASE(16, 2, 8, 128, 64)
+    TALS_CASE(8, 2, 4, 128, 64) TALS_CASE(32, 2, 16, 256, 32) TALS_CASE(16, 2, 8, 256, 32)
   } else {
-    TALS_CASE(16, 1, 8, 256) TALS_CASE(16, 2, 8, 256) TALS_CASE(16, 4, 8, 256)
-    TALS_CASE(8, 1, 8, 256) TALS_CASE(8, 2, 8, 256) TALS_CASE(8, 4, 8, 256)
+    TALS_CASE(16, 1, 8, 256, 16) TALS_CASE(16, 2, 8, 256, 16) TALS_CASE(16, 4, 8, 256, 16)
+    TALS_CASE(8, 1, 8, 256, 16) TALS_CASE(8, 2, 8, 256, 16) TALS_CASE(8, 4, 8, 256, 16)
   }
 #undef TALS_CASE
   return nullptr;
@@ -75,8 +82,8 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
       const int nrg = in.rc / in.rw;
       const int rowt = in.nt / nrg;
       if ((long long)rowt * in.rpt < v.I) continue;
-      size_t sm = f32 ? pass_smem_bytes<float>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt)
-                      : pass_smem_bytes<double>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt);
+      size_t sm = f32 ? pass_smem_bytes<float>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt, in.jt)
+                      : pass_smem_bytes<double>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt, in.jt);
       if (sm > smem_max) continue;
       const int chunks = (R + in.rc - 1) / in.rc;
       const double waste = (double)(in.rc * chunks - R) / (double)(in.rc * chunks);
@@ -84,14 +91,19 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
       // fewer rank chunks and less padding first; then fewer idle rows; among
       // equals the larger per-thread tile (more FMAs per shared-memory load:
       // 4 rows x 16 ranks at 256 threads beats 2 x 16 at 512 when no row idles)
+      // short tiles (I x columns well under 8K elements) are dominated by their
+      // per-tile barriers and cross-warp reduction
+      const double small_tile = std::max(0.0, 1.0 - (double)v.I * in.jt / 8192.0);
       const double score = chunks * (nbuf == 1 ? 1.35 : 1.0) * (1.0 + waste) +
-                           (idle > 0.0 ? 0.01 + 0.5 * idle : 0.0) - 1e-3 * in.rpt * in.rw / 16.0;
+                           (idle > 0.0 ? 0.01 + 0.5 * idle : 0.0) + 0.3 * small_tile -
+                           1e-3 * in.rpt * in.rw / 16.0;
       if (score < best) {
         best = score;
         cfg.rc = in.rc;
         cfg.rpt = in.rpt;
         cfg.rw = in.rw;
         cfg.nt = in.nt;
+        cfg.jt = in.jt;
         cfg.smem = sm;
         cfg.nbuf = nbuf;
         cfg.ok = true;
@@ -100,7 +112,7 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
   }
   if (!cfg.ok) return cfg;
   cfg.grid_y = (R + cfg.rc - 1) / cfg.rc;
-  const long long ntiles = (v.J() + kJT - 1) / kJT;
+  const long long ntiles = (v.J() + cfg.jt - 1) / cfg.jt;
   int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (cfg.smem + 1024));
   per_sm = std::min(per_sm, 2);
   long long gx = std::max<long long>(1, (long long)num_sms * per_sm / cfg.grid_y);
@@ -115,14 +127,14 @@ cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* 
                         cudaStream_t s, const void* Win, int resid) {
   if (!cfg.ok) return cudaErrorInvalidConfiguration;
   if (resid && cfg.grid_y != 1) return cudaErrorInvalidValue;
-  const Inst in{cfg.rc, cfg.rpt, cfg.rw, cfg.nt};
+  const Inst in{cfg.rc, cfg.rpt, cfg.rw, cfg.nt, cfg.jt};
   void* fn = dtype == 1 ? lookup<float>(in) : lookup<double>(in);
   if (fn == nullptr) return cudaErrorInvalidDeviceFunction;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfg.smem);
   if (e != cudaSuccess) return e;
   dim3 grid(cfg.grid_x, cfg.grid_y);
-  const long long ntiles = (v.J() + kJT - 1) / kJT;
+  const long long ntiles = (v.J() + cfg.jt - 1) / cfg.jt;
   const size_t esz = dtype == 1 ? 4 : 8;
   const int vec_ok = ((uintptr_t)X % 16 == 0) && ((v.Q * esz) % 16 == 0);
   if (dtype == 1) {

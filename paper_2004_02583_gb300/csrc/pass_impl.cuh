@@ -53,14 +53,17 @@ struct PassArgs {
   int resid;         // SWEEP: accumulate ||B - Qb W^T||^2 instead of ||W||^2 (one chunk only)
 };
 
-template <typename T, int RC, int RPT, int RW, int NT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT = kJT>
 struct PassShape {
   static constexpr int NRG = RC / RW;              // r-groups of the Y accumulation
   static constexpr int ROWT = NT / NRG;            // row-threads per r-group
-  static constexpr int RL = RC / 8;                // r-columns per lane in step 1 (8 r-groups)
+  static constexpr int CG = JT / 4;                // step-1 column groups of 4 per warp
+  static constexpr int RG = 32 / CG;               // step-1 r-groups per warp
+  static constexpr int RL = RC / RG;               // r-columns per lane in step 1
   static constexpr int NW = NT / 32;               // warps (step 1 splits I over them)
   static constexpr int WSP = RC + 4;               // padded row stride of W tiles
-  static_assert(RC % RW == 0 && RC % 8 == 0 && RW % 4 == 0, "bad chunk");
+  static_assert(RC % RW == 0 && RC % RG == 0 && RW % 4 == 0 && JT % 16 == 0 && JT <= 128,
+                "bad chunk");
   static_assert(NT % NRG == 0 && (ROWT % 32) == 0, "r-groups must be warp-uniform");
 };
 
@@ -72,11 +75,12 @@ __host__ __device__ inline long long slack_rows(long long I, int rowspan) {
 
 template <typename T>
 __host__ __device__ inline size_t pass_smem_bytes(long long I, int RC, int rowspan, int nbuf,
-                                                  int nt = kThreads) {
-  size_t ts = (size_t)nbuf * ((size_t)I * kJTP) + (size_t)slack_rows(I, rowspan) * kJTP;
+                                                  int nt = kThreads, int jt = kJT) {
+  const size_t jtp = (size_t)jt + 4;
+  size_t ts = (size_t)nbuf * ((size_t)I * jtp) + (size_t)slack_rows(I, rowspan) * jtp;
   size_t ls = (size_t)I * RC;
-  size_t wr = (size_t)(nt / 32) * kJT * (RC + 4);
-  size_t ws = (size_t)kJT * (RC + 4);
+  size_t wr = (size_t)(nt / 32) * jt * (RC + 4);
+  size_t ws = (size_t)jt * (RC + 4);
   return (ts + ls + wr + ws) * sizeof(T) + 32 * sizeof(double);
 }
 
@@ -100,42 +104,42 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Issue the copies of tile t into Tb (I x kJTP). Columns beyond J are zero-filled.
-template <typename T>
+// Issue the copies of tile t (JT columns) into Tb (I x (JT + 4)). Columns beyond J are zero-filled.
+template <typename T, int JT = kJT>
 __device__ __forceinline__ void issue_tile(const PassArgs<T>& a, long long t, T* Tb) {
   const long long I = a.I, Q = a.Q;
-  const long long j0 = t * kJT;
+  const long long j0 = t * JT;
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long p0 = j0 / Q, q0 = j0 - p0 * Q;
   constexpr int EPV = 16 / sizeof(T);   // elements per 16-byte chunk
-  if (a.vec_ok && q0 + kJT <= Q && j0 + kJT <= a.J) {
-    // whole tile inside one p: every row is kJT contiguous elements
+  if (a.vec_ok && q0 + JT <= Q && j0 + JT <= a.J) {
+    // whole tile inside one p: every row is JT contiguous elements
     const T* base = a.X + p0 * I * Q + q0;
-    constexpr int CPR = kJT / EPV;      // chunks per row
+    constexpr int CPR = JT / EPV;      // chunks per row
     for (long long e = tid; e < I * CPR; e += nt) {
       const long long i = e / CPR;
       const int k = (int)(e - i * CPR);
-      cp_async16(Tb + i * kJTP + k * EPV, base + i * Q + k * EPV, 16);
+      cp_async16(Tb + i * (JT + 4) + k * EPV, base + i * Q + k * EPV, 16);
     }
-  } else if (Q >= kJT) {
+  } else if (Q >= JT) {
     // column-fastest element copies (rows may straddle two p)
-    for (long long e = tid; e < I * kJT; e += nt) {
-      const long long i = e / kJT;
-      const int c = (int)(e - i * kJT);
+    for (long long e = tid; e < I * JT; e += nt) {
+      const long long i = e / JT;
+      const int c = (int)(e - i * JT);
       const long long j = j0 + c;
       const bool ok = j < a.J;
       const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
-      cp_async_elem<sizeof(T)>(Tb + i * kJTP + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+      cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
     }
   } else {
     // row-fastest element copies: consecutive threads read consecutive i
-    for (long long e = tid; e < I * kJT; e += nt) {
+    for (long long e = tid; e < I * JT; e += nt) {
       const int c = (int)(e / I);
       const long long i = e - (long long)c * I;
       const long long j = j0 + c;
       const bool ok = j < a.J;
       const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
-      cp_async_elem<sizeof(T)>(Tb + i * kJTP + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+      cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
     }
   }
 }
@@ -156,31 +160,32 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
 // One CTA's share of a pass: tiles t_begin, t_begin + t_step, ... of rank chunk
 // `rchunk`. Y (this chunk's columns) is written to Yout (I x R, row stride R);
 // returns the CTA's FP64 sum (||B||^2, ||W||^2 or ||B - Qb W^T||^2) in thread 0.
-template <typename T, int RC, int RPT, int RW, int NT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT = kJT>
 __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_begin, long long t_step,
                                            int rchunk, unsigned char* smem_raw, T* Yout) {
-  using S = PassShape<T, RC, RPT, RW, NT>;
+  using S = PassShape<T, RC, RPT, RW, NT, JT>;
+  constexpr int JTP = JT + 4;
   constexpr int WSP = S::WSP;
   const long long I = a.I;
-  T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][I][kJTP]
-  T* Ls = Tbuf + (size_t)a.nbuf * I * kJTP + (size_t)slack_rows(I, S::ROWT * RPT) * kJTP;  // [I][RC]
-  T* Wred = Ls + (size_t)I * RC;                                           // [NW][kJT][WSP]
-  T* Ws = Wred + (size_t)S::NW * kJT * WSP;                                // [kJT][WSP]
-  double* red = reinterpret_cast<double*>(Ws + (size_t)kJT * WSP);
+  T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][I][JTP]
+  T* Ls = Tbuf + (size_t)a.nbuf * I * JTP + (size_t)slack_rows(I, S::ROWT * RPT) * JTP;  // [I][RC]
+  T* Wred = Ls + (size_t)I * RC;                                           // [NW][JT][WSP]
+  T* Ws = Wred + (size_t)S::NW * JT * WSP;                                // [JT][WSP]
+  double* red = reinterpret_cast<double*>(Ws + (size_t)JT * WSP);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = rchunk * RC;
   const bool do_w = a.mode == PASS_SWEEP || a.mode == PASS_PROJECT;
   const bool do_y = a.mode != PASS_PROJECT;
   const bool resid = a.resid && a.mode == PASS_SWEEP;
-  const bool cfast = a.Q >= kJT;   // W output mapping: q-contiguous or r-contiguous
+  const bool cfast = a.Q >= JT;   // W output mapping: q-contiguous or r-contiguous
   bool write_w = a.Wout != nullptr;
   if (write_w && a.st != nullptr)
     write_w = (a.st->k >= a.w_from_k) || (a.st->k + 1 >= a.st->max_sweeps);
 
   // first tile in flight before anything else
   long long t = t_begin;
-  if (t < a.ntiles) issue_tile(a, t, Tbuf);
+  if (t < a.ntiles) issue_tile<T, JT>(a, t, Tbuf);
   cp_async_commit();
 
   // Qb columns r0 .. r0+RC-1 (zero beyond R) into shared memory.
@@ -209,30 +214,30 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
   const int ti = tid - rgrp * S::ROWT;       // step-2 row-thread index
   const long long IW = (I + S::NW - 1) / S::NW;
   const long long ilo = min(I, warp * IW), ihi = min(I, ilo + IW);
-  const int cg = lane & 3, rg = lane >> 2;   // step-1 lane layout: 4 col groups x 8 r groups
+  const int cg = lane % S::CG, rg = lane / S::CG;   // step-1 lane layout: CG col groups x RG r groups
 
   int buf = 0;
   for (; t < a.ntiles; t += t_step) {
     const long long tn = t + t_step;
-    T* Tb = Tbuf + (size_t)buf * I * kJTP;
+    T* Tb = Tbuf + (size_t)buf * I * JTP;
     if (a.nbuf > 1) {
       // stream the next tile into the other buffer while this one is used
-      if (tn < a.ntiles) issue_tile(a, tn, Tbuf + (size_t)(buf ^ 1) * I * kJTP);
+      if (tn < a.ntiles) issue_tile<T, JT>(a, tn, Tbuf + (size_t)(buf ^ 1) * I * JTP);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const long long j0 = t * kJT;
-    const int ncol = (int)min((long long)kJT, a.J - j0);
+    const long long j0 = t * JT;
+    const int ncol = (int)min((long long)JT, a.J - j0);
 
     if (a.mode == PASS_INIT && rchunk == 0) {
       T nacc = T(0);
-      for (long long e = tid; e < I * kJT; e += NT) {
-        const long long i = e / kJT;
-        const int c = (int)(e - i * kJT);
-        const T x = Tb[i * kJTP + c];
+      for (long long e = tid; e < I * JT; e += NT) {
+        const long long i = e / JT;
+        const int c = (int)(e - i * JT);
+        const T x = Tb[i * JTP + c];
         nacc += (c < ncol) ? x * x : T(0);
       }
       sacc += (double)nacc;
@@ -251,11 +256,11 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < S::RL / 2; ++v) acc2[u][v] = make_float2(0.f, 0.f);
-        const float* tp = reinterpret_cast<const float*>(trow) + (int)ilo * kJTP;
+        const float* tp = reinterpret_cast<const float*>(trow) + (int)ilo * JTP;
         const float* lp = reinterpret_cast<const float*>(lrow) + (int)ilo * RC;
 #pragma unroll 4
         for (int ii = 0; ii < nrow; ++ii) {
-          const float4 t4 = *reinterpret_cast<const float4*>(tp + ii * kJTP);
+          const float4 t4 = *reinterpret_cast<const float4*>(tp + ii * JTP);
           float2 l2[S::RL / 2];
           if constexpr (S::RL % 4 == 0) {
 #pragma unroll
@@ -289,7 +294,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
           for (int v = 0; v < S::RL; ++v) acc[u][v] = T(0);
         if (ilo < ihi) {
           T tv[4], lv[S::RL];
-          ld4(trow + ilo * kJTP, tv);
+          ld4(trow + ilo * JTP, tv);
 #pragma unroll
           for (int v = 0; v < S::RL; ++v) lv[v] = lrow[ilo * RC + v];
 #pragma unroll 4
@@ -297,7 +302,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
             // operands of row i+1 are loaded before row i is multiplied
             const long long inx = (i + 1 < ihi) ? i + 1 : i;
             T tn4[4], ln[S::RL];
-            ld4(trow + inx * kJTP, tn4);
+            ld4(trow + inx * JTP, tn4);
             if constexpr (S::RL % 4 == 0) {
 #pragma unroll
               for (int v = 0; v < S::RL; v += 4) {
@@ -321,7 +326,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
           }
         }
       }
-      T* wr = Wred + (size_t)warp * kJT * WSP;
+      T* wr = Wred + (size_t)warp * JT * WSP;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -329,12 +334,12 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       __syncthreads();
       // final W: consecutive threads -> consecutive q (cfast) or consecutive r
       T wsq = T(0);
-      for (int o = tid; o < kJT * RC; o += NT) {
-        const int c = cfast ? (o % kJT) : (o / RC);
-        const int rl = cfast ? (o / kJT) : (o % RC);
+      for (int o = tid; o < JT * RC; o += NT) {
+        const int c = cfast ? (o % JT) : (o / RC);
+        const int rl = cfast ? (o / JT) : (o % RC);
         T w = T(0);
 #pragma unroll
-        for (int g = 0; g < S::NW; ++g) w += Wred[((size_t)g * kJT + c) * WSP + rl];
+        for (int g = 0; g < S::NW; ++g) w += Wred[((size_t)g * JT + c) * WSP + rl];
         const int r = r0 + rl;
         const bool valid = (c < ncol) && (r < a.R);
         w = valid ? w : T(0);
@@ -350,9 +355,9 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         // ||B_t - Qb W_t^T||^2 from the tile: no cancellation against ||B||^2
         __syncthreads();
         T racc = T(0);
-        for (long long e = tid; e < I * kJT; e += NT) {
-          const long long i = e / kJT;
-          const int c = (int)(e - i * kJT);
+        for (long long e = tid; e < I * JT; e += NT) {
+          const long long i = e / JT;
+          const int c = (int)(e - i * JT);
           T dot = T(0);
 #pragma unroll
           for (int v = 0; v < RC; v += 4) {
@@ -362,16 +367,16 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 #pragma unroll
             for (int q = 0; q < 4; ++q) dot = fma(l4[q], w4[q], dot);
           }
-          const T rsd = Tb[i * kJTP + c] - dot;
+          const T rsd = Tb[i * JTP + c] - dot;
           racc += (c < ncol) ? rsd * rsd : T(0);
         }
         sacc += (double)racc;
       }
     } else if (a.mode == PASS_GIVEN) {
       // W_t read from the given tensor (P x R x Q layout)
-      for (int o = tid; o < kJT * RC; o += NT) {
-        const int c = cfast ? (o % kJT) : (o / RC);
-        const int rl = cfast ? (o / kJT) : (o % RC);
+      for (int o = tid; o < JT * RC; o += NT) {
+        const int c = cfast ? (o % JT) : (o / RC);
+        const int rl = cfast ? (o / JT) : (o % RC);
         const int r = r0 + rl;
         T w = T(0);
         if (c < ncol && r < a.R) {
@@ -382,8 +387,8 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       }
     } else {
       // INIT: W_t is the seeded sketch S restricted to the tile's columns
-      for (int o = tid; o < kJT * RC; o += NT) {
-        const int c = o % kJT, rl = o / kJT;
+      for (int o = tid; o < JT * RC; o += NT) {
+        const int c = o % JT, rl = o / JT;
         const int r = r0 + rl;
         T w = T(0);
         if (c < ncol && r < a.R) w = (T)sketch_entry(a.sketch_state, (uint64_t)(j0 + c), a.R, r);
@@ -395,17 +400,17 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       __syncthreads();
       // ---- step 2: Y[i, r] += sum_c B_t[i, c] W_t[c, r] ----
       const T* wrow = Ws + rgrp * RW;
-      const T* tbase = Tb + (size_t)ti * kJTP;
+      const T* tbase = Tb + (size_t)ti * JTP;
       if constexpr (sizeof(T) == 4) {
         // FP32: paired FMAs along r, same rounding as fmaf
         const float* wp = reinterpret_cast<const float*>(wrow);
         const float* tp = reinterpret_cast<const float*>(tbase);
 #pragma unroll
-        for (int c4 = 0; c4 < kJT; c4 += 4) {
+        for (int c4 = 0; c4 < JT; c4 += 4) {
           float tv[RPT][4];
 #pragma unroll
           for (int k = 0; k < RPT; ++k) {
-            const float4 x = *reinterpret_cast<const float4*>(tp + k * S::ROWT * kJTP + c4);
+            const float4 x = *reinterpret_cast<const float4*>(tp + k * S::ROWT * JTP + c4);
             tv[k][0] = x.x; tv[k][1] = x.y; tv[k][2] = x.z; tv[k][3] = x.w;
           }
 #pragma unroll
@@ -427,10 +432,10 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         }
       } else {
 #pragma unroll
-        for (int c4 = 0; c4 < kJT; c4 += 4) {
+        for (int c4 = 0; c4 < JT; c4 += 4) {
           T tv[RPT][4];
 #pragma unroll
-          for (int k = 0; k < RPT; ++k) ld4(tbase + (size_t)k * S::ROWT * kJTP + c4, tv[k]);
+          for (int k = 0; k < RPT; ++k) ld4(tbase + (size_t)k * S::ROWT * JTP + c4, tv[k]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             T wv[RW];
@@ -453,7 +458,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
     if (a.nbuf > 1) {
       buf ^= 1;
     } else if (tn < a.ntiles) {
-      issue_tile(a, tn, Tbuf);
+      issue_tile<T, JT>(a, tn, Tbuf);
       cp_async_commit();
     }
   }

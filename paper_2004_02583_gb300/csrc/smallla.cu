@@ -199,8 +199,9 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     // Eq. 5.01 on e_k^2 = ||B_(n)||^2 - ||W||^2 (W = B^T Q_k is the LS optimum for Q_k),
     // plus tr((Q'^T Q' - I) X), the first-order term of the projector onto the
     // rounded basis Q' actually used, X = Q^T B B^T Q' (the cross Gram below)
-    __shared__ int stop;
+    __shared__ int stop, phase_end;
     __shared__ double red[32];
+    if (tid == 0) phase_end = 0;
     double c = 0.0;
     if (GL != nullptr)
       for (int o = tid; o < R * R; o += kSmallThreads) {
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
         if (flat || st->bulk + 1 >= st->bulk_max) {
           st->bulk_mode = 0;
           st->kf = 0;
+          phase_end = 1;
         }
         st->bulk += 1;
       } else {
@@ -247,6 +249,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       if (has_cond && tid == 0) cudaGraphSetConditional(cond, 0u);
       return;
     }
+    // the bulk loop ends after this sweep; its L-update still runs below
+    if (phase_end && has_cond && tid == 0) cudaGraphSetConditional(cond, 0u);
   }
 
   // Right-looking Cholesky in LDL^T form on the symmetrised Gram S (lower

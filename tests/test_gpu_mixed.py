@@ -86,3 +86,31 @@ def test_mixed_st_hosvd_matches_oracle(tals):
     assert abs(st2["rel_err"] - rel2) <= 1e-6
     assert st2["bulk_sweeps"][0] >= 1
     assert st2["sweeps"][0] >= st2["bulk_sweeps"][0] + 2   # at least two FP32 sweeps finish
+
+
+@pytest.mark.parametrize("kind", ["st", "t"])
+def test_mixed_graph_matches_host_loop(tals, kind):
+    # the graph (device-side bulk and FP32 WHILE loops) runs the same kernels in
+    # the same order as the host-driven loop: identical results and sweep counts
+    dims, ranks = (256, 96, 128), (16, 24, 20)
+    p = W.planted(W.SEED_BASE + 22, dims, ranks, "inv_k", 1e-2, dtype=np.float32)
+    A = torch.from_numpy(p.A).cuda()
+    fn = tals.st_hosvd if kind == "st" else tals.t_hosvd
+    kw = dict(eta=1e-6, seed=5, precision="mixed_bf16", order=[0, 1, 2]) if kind == "st" else \
+        dict(eta=1e-6, seed=5, precision="mixed_bf16")
+    Gh, Uh, sh = fn(A, ranks, use_graph=False, **kw)
+    Gg, Ug, sg = fn(A, ranks, use_graph=True, **kw)
+    assert sh["sweeps"] == sg["sweeps"] and sh["bulk_sweeps"] == sg["bulk_sweeps"]
+    assert sg["bulk_sweeps"][0] >= 1
+    assert torch.equal(Gh, Gg)
+    for a, b in zip(Uh, Ug):
+        assert torch.equal(a, b)
+    assert sh["rel_err"] == sg["rel_err"]
+    # and the result is the oracle's to the FP32 tolerances
+    a64 = p.A.astype(np.float64)
+    ref = O.st_hosvd_als(a64, ranks, eta=1e-6, seed=5, order=[0, 1, 2]) if kind == "st" else \
+        O.t_hosvd_als(a64, ranks, eta=1e-6, seed=5)
+    rel = O.rel_error(a64, Gg.double().cpu().numpy(), [u.double().cpu().numpy() for u in Ug])
+    assert abs(rel - O.rel_error(a64, ref.G, ref.U)) <= 1e-6
+    for n in range(3):
+        assert O.principal_angles(Ug[n].double().cpu().numpy(), ref.U[n]).max() <= 1e-4
