@@ -591,9 +591,10 @@ def run_c4(args):
     ranks = [r for _, _, r in items]
     clocks = Clocks(0)
     clocks.start()
-    ms, (Gs, Us, sts) = _time_gpu(lambda: tals.batched_st_hosvd(As, ranks, eta=eta, seed=1),
-                                  args.steps, args.warmup)
+    runner = tals.BatchedRunner(As, ranks, eta=eta, seed=1)
+    ms, _ = _time_gpu(runner.run, args.steps, args.warmup)
     clk = clocks.stop()
+    Gs, Us, sts = runner.Gs, runner.Us, runner.stats()
     # algorithmic bytes: every pass (initial guess + sweeps) reads the current tensor
     byt = 0
     for (a, dims, rk), st in zip(items, sts):

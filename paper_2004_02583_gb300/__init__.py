@@ -421,27 +421,50 @@ def tucker_reconstruct(G, Us):
     return _autograd()[1].apply(G, *Us)
 
 
+class BatchedRunner:
+    """st-HOSVD-ALS of many small third-order FP32 CUDA tensors in one persistent,
+    graph-captured launch, with the outputs and the argument arrays prepared once
+    so that repeated runs cost one C-ABI call each. ranks: list of 3-tuples."""
+
+    def __init__(self, As, ranks, eta=1e-4, max_sweeps=50, seed=0, stream=None):
+        torch = _torch()
+        count = len(As)
+        if len(ranks) != count:
+            raise ValueError("one rank triple per tensor")
+        for a in As:
+            _require_cuda(a)
+            if a.dtype != torch.float32 or a.dim() != 3:
+                raise ValueError("batched tensors are third-order float32")
+        self.count = count
+        self.As = list(As)
+        self.Gs = [torch.empty(tuple(r), dtype=torch.float32, device=a.device) for a, r in zip(As, ranks)]
+        self._Uflat = [torch.empty((int(a.shape[n]), int(r[n])), dtype=torch.float32, device=a.device)
+                       for a, r in zip(As, ranks) for n in range(3)]
+        self.Us = [self._Uflat[3 * t:3 * t + 3] for t in range(count)]
+        self._a = _ptrs(self.As)
+        self._g = _ptrs(self.Gs)
+        self._u = _ptrs(self._Uflat)
+        self._dims = (ctypes.c_int64 * (3 * count))(*[int(d) for a in As for d in a.shape])
+        self._rk = (ctypes.c_int * (3 * count))(*[int(x) for r in ranks for x in r])
+        self._o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed))
+        self._stats = (tals_stats * max(count, 1))()
+        self._stream = stream
+
+    def run(self):
+        _check(lib().tals_batched_st_hosvd(self.count, self._a, self._dims, self._rk,
+                                           ctypes.byref(self._o), self._g, self._u, self._stats,
+                                           _stream_ptr(self._stream)))
+
+    def stats(self):
+        return [self._stats[t].to_dict(3) for t in range(self.count)]
+
+
 def batched_st_hosvd(As, ranks, eta=1e-4, max_sweeps=50, seed=0, stream=None):
     """st-HOSVD-ALS of many small third-order FP32 CUDA tensors in one persistent,
     graph-captured launch. ranks: list of 3-tuples. Returns (Gs, Us, stats)."""
-    torch = _torch()
-    count = len(As)
-    if len(ranks) != count:
-        raise ValueError("one rank triple per tensor")
-    for a in As:
-        _require_cuda(a)
-        if a.dtype != torch.float32 or a.dim() != 3:
-            raise ValueError("batched tensors are third-order float32")
-    Gs = [torch.empty(tuple(r), dtype=torch.float32, device=a.device) for a, r in zip(As, ranks)]
-    Us = [torch.empty((int(a.shape[n]), int(r[n])), dtype=torch.float32, device=a.device)
-          for a, r in zip(As, ranks) for n in range(3)]
-    dims = (ctypes.c_int64 * (3 * count))(*[int(d) for a in As for d in a.shape])
-    rk = (ctypes.c_int * (3 * count))(*[int(x) for r in ranks for x in r])
-    o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed))
-    stats = (tals_stats * max(count, 1))()
-    _check(lib().tals_batched_st_hosvd(count, _ptrs(As), dims, rk, ctypes.byref(o), _ptrs(Gs),
-                                       _ptrs(Us), stats, _stream_ptr(stream)))
-    return Gs, [Us[3 * t:3 * t + 3] for t in range(count)], [stats[t].to_dict(3) for t in range(count)]
+    r = BatchedRunner(As, ranks, eta, max_sweeps, seed, stream)
+    r.run()
+    return r.Gs, r.Us, r.stats()
 
 
 def sweep_pass(A, mode, Q, engine="cuda", stream=None):

@@ -55,75 +55,164 @@ struct BatchArgs {
 namespace {
 
 // ---- CTA-scope FP64 helpers (blockDim.x == kThreads) ----
+// FP64 on this part has ~64-cycle latency and a warp FP64 instruction holds an
+// SMSP's FP64 pipe ~76 cycles: the helpers keep several independent chains per
+// thread, skip the mirrored half of symmetric products and take no division
+// inside a dependent chain.
 
-__device__ void cta_gram(const double* A, const double* B, int I, int R, double* out) {
-  for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
-    const int r = o / R, s = o % R;
-    double g = 0.0;
-    for (int i = 0; i < I; ++i) g = fma(A[i * R + r], B[i * R + s], g);
-    out[o] = g;
+// out = A^T B (R x R). sym: A == B, only s <= r computed and mirrored.
+__device__ void cta_gram(const double* A, const double* B, int I, int R, double* out, bool sym) {
+  const int n = sym ? R * (R + 1) / 2 : R * R;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    int r, c;
+    if (sym) {
+      r = (int)((sqrtf(8.f * (float)o + 1.f) - 1.f) * 0.5f);
+      while (r * (r + 1) / 2 > o) --r;
+      while ((r + 1) * (r + 2) / 2 <= o) ++r;
+      c = o - r * (r + 1) / 2;
+    } else {
+      r = o / R;
+      c = o % R;
+    }
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= I; i += 4) {
+      g0 = fma(A[i * R + r], B[i * R + c], g0);
+      g1 = fma(A[(i + 1) * R + r], B[(i + 1) * R + c], g1);
+      g2 = fma(A[(i + 2) * R + r], B[(i + 2) * R + c], g2);
+      g3 = fma(A[(i + 3) * R + r], B[(i + 3) * R + c], g3);
+    }
+    for (; i < I; ++i) g0 = fma(A[i * R + r], B[i * R + c], g0);
+    const double g = (g0 + g1) + (g2 + g3);
+    out[r * R + c] = g;
+    if (sym) out[c * R + r] = g;
   }
   __syncthreads();
 }
 
-// Lower Cholesky factor of the (symmetrised) R x R matrix G in place; returns 1 on failure.
-__device__ int cta_chol(double* G, int R, int* flag) {
-  if (threadIdx.x == 0) *flag = 0;
-  for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
+// Lower Cholesky factor of the (symmetrised) R x R matrix G in place (R <= 16);
+// returns 1 on failure. Right-looking LDL^T: warp 0 finishes column k+1 and
+// takes its pivot reciprocal, the other warps update the rest of the trailing
+// block; square roots at the end. `w` holds 2 R doubles of scratch.
+__device__ int cta_chol(double* G, int R, int* flag, double* w) {
+  double* Lc = w;          // [2][kBatchMaxR]
+  __shared__ double rs[kBatchMaxR];
+  __shared__ long long tiny_bits;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int o = tid; o < R * R; o += blockDim.x) {
     const int r = o / R, c = o % R;
-    if (r > c) {
-      const double v = 0.5 * (G[r * R + c] + G[c * R + r]);
-      G[r * R + c] = v;
-      G[c * R + r] = v;
-    }
+    if (r > c) G[r * R + c] = 0.5 * (G[r * R + c] + G[c * R + r]);
+  }
+  if (tid == 0) *flag = 0;
+  if (tid < 32) {
+    const int hmax = __reduce_max_sync(0xffffffffu, lane < R ? max(0, __double2hiint(G[lane * R + lane])) : 0);
+    if (lane == 0)
+      tiny_bits = __double_as_longlong(64.0 * 2.220446049250313e-16 * __hiloint2double(hmax, 0));
   }
   __syncthreads();
-  double maxd = 0.0;
-  for (int r = 0; r < R; ++r) maxd = fmax(maxd, G[r * R + r]);
-  const double tiny = 64.0 * 2.220446049250313e-16 * maxd;
-  for (int k = 0; k < R; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = G[k * R + k];
-      if (!(d > tiny)) {
-        *flag = 1;
-        G[k * R + k] = 1.0;
-      } else {
-        G[k * R + k] = sqrt(d);
+  if (warp == 0) {
+    double d = G[0];
+    if (lane == 0 && !pivot_ok(d, tiny_bits)) {
+      d = 1.0;
+      G[0] = 1.0;
+      *flag = 1;
+    }
+    const double dinv = __shfl_sync(0xffffffffu, lane == 0 ? fast_rcp64(d) : 0.0, 0);
+    if (lane >= 1 && lane < R) Lc[lane] = G[lane * R] * dinv;
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < R; ++k) {
+    const int cb = (k & 1) * kBatchMaxR, c1 = k + 1;
+    if (warp == 0) {
+      const int i = c1 + lane;
+      double v = i < R ? fma(-G[i * R + k], Lc[cb + c1], G[i * R + c1]) : 0.0;
+      double dinv = 0.0;
+      if (lane == 0) {
+        double d = v;
+        if (!pivot_ok(d, tiny_bits)) {
+          d = 1.0;
+          v = 1.0;
+          *flag = 1;
+        }
+        dinv = fast_rcp64(d);
+      }
+      dinv = __shfl_sync(0xffffffffu, dinv, 0);
+      if (i < R) {
+        G[i * R + c1] = v;
+        if (i > c1) Lc[(kBatchMaxR - cb) + i] = v * dinv;
+      }
+    } else {
+      const int m = R - 2 - k, na = m * (m + 1) / 2;
+      for (int a = tid - 32; a < na; a += blockDim.x - 32) {
+        int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
+        while (ip * (ip + 1) / 2 > a) --ip;
+        while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
+        const int i = k + 2 + ip, j = k + 2 + (a - ip * (ip + 1) / 2);
+        G[i * R + j] = fma(-G[i * R + k], Lc[cb + j], G[i * R + j]);
       }
     }
     __syncthreads();
-    const double dk = G[k * R + k];
-    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) G[i * R + k] /= dk;
-    __syncthreads();
-    const int m = R - k - 1;
-    for (int o = threadIdx.x; o < m * m; o += blockDim.x) {
-      const int i = k + 1 + o / m, j = k + 1 + o % m;
-      if (j <= i) G[i * R + j] -= G[i * R + k] * G[j * R + k];
-    }
-    __syncthreads();
   }
+  for (int r = tid; r < R; r += blockDim.x) rs[r] = rsqrt(G[r * R + r]);
+  __syncthreads();
+  for (int o = tid; o < R * R; o += blockDim.x) {
+    const int r = o / R, c = o % R;
+    G[o] = c <= r ? G[o] * rs[c] : 0.0;
+  }
+  __syncthreads();
   const int f = *flag;
   __syncthreads();
   return f;
 }
 
 // Row solves with the lower factor F: op 0: Out = In F^-T, op 1: Out = In (F F^T)^-1.
-__device__ void cta_rowsolve(const double* In, const double* F, int op, double* Out, int I, int R) {
+// One thread per row, right-looking so each step's chain is one FMA; the factor
+// is scaled by its pivot reciprocals first (no division in the chains); the
+// row lives in registers (loops unrolled to the rank limit). `w` holds
+// 2 R^2 + R doubles of scratch.
+__device__ void cta_rowsolve(const double* In, const double* F, int op, double* Out, int I, int R,
+                             double* w) {
+  double* Ff = w;                          // F[r][c] / F[r][r]
+  double* Fb = w + kBatchMaxR * kBatchMaxR;  // F[c][r] / F[r][r], stored at [c][r]
+  double* dinv = Fb + kBatchMaxR * kBatchMaxR;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) dinv[r] = 1.0 / F[r * R + r];
+  __syncthreads();
+  for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
+    const int r = o / R, c = o % R;
+    Ff[r * kBatchMaxR + c] = F[o] * dinv[r];
+    Fb[r * kBatchMaxR + c] = F[o] * dinv[c];
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < I; i += blockDim.x) {
-    double x[kBatchMaxR];
-    for (int r = 0; r < R; ++r) x[r] = In[i * R + r];
-    for (int r = 0; r < R; ++r) {
-      double s = x[r];
-      for (int c = 0; c < r; ++c) s = fma(-F[r * R + c], x[c], s);
-      x[r] = s / F[r * R + r];
-    }
-    if (op == 1)
-      for (int r = R - 1; r >= 0; --r) {
-        double s = x[r];
-        for (int c = r + 1; c < R; ++c) s = fma(-F[c * R + r], x[c], s);
-        x[r] = s / F[r * R + r];
+    double s[kBatchMaxR];
+#pragma unroll
+    for (int r = 0; r < kBatchMaxR; ++r) s[r] = r < R ? In[i * R + r] * dinv[r] : 0.0;
+    // forward: F x^T = b^T
+#pragma unroll
+    for (int c = 0; c < kBatchMaxR; ++c) {
+      if (c < R) {
+        const double xc = s[c];
+#pragma unroll
+        for (int r = c + 1; r < kBatchMaxR; ++r)
+          if (r < R) s[r] = fma(-Ff[r * kBatchMaxR + c], xc, s[r]);
       }
-    for (int r = 0; r < R; ++r) Out[i * R + r] = x[r];
+    }
+    if (op == 1) {
+      // backward: F^T z^T = x^T
+#pragma unroll
+      for (int r = 0; r < kBatchMaxR; ++r) s[r] = r < R ? s[r] * dinv[r] : 0.0;
+#pragma unroll
+      for (int c = kBatchMaxR - 1; c >= 0; --c) {
+        if (c < R) {
+          const double zc = s[c];
+#pragma unroll
+          for (int r = 0; r < c; ++r) s[r] = fma(-Fb[c * kBatchMaxR + r], zc, s[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kBatchMaxR; ++r)
+      if (r < R) Out[i * R + r] = s[r];
   }
   __syncthreads();
 }
@@ -136,19 +225,20 @@ struct LaSmem {
   double* GL;   // [R][R]
   float* Yf;    // [I][R]
   float* Lt;    // [I][R]
+  double* work; // [2 R^2 + R] for the solves and the Cholesky
   int* flag;
 };
 
 // Q = orthonormal basis of In by CholeskyQR (one round): L = In F^-T; the
 // FP32 copy Lt and the Gram of its stored values GL. Returns failure.
 __device__ int cta_cholqr(const double* In, LaSmem& m, int I, int R, double* Out) {
-  cta_gram(In, In, I, R, m.X);
-  if (cta_chol(m.X, R, m.flag)) return 1;
-  cta_rowsolve(In, m.X, 0, Out, I, R);
+  cta_gram(In, In, I, R, m.X, true);
+  if (cta_chol(m.X, R, m.flag, m.work)) return 1;
+  cta_rowsolve(In, m.X, 0, Out, I, R, m.work);
   return 0;
 }
 
-template <int RC, int RPT, int RW>
+template <int RC, int RPT, int RW, int JT>
 __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_t pass_bytes) {
   const long long* dd = b.dims + 3 * (size_t)t;
   const int* rr = b.ranks + 3 * (size_t)t;
@@ -173,7 +263,8 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
   m.GL = m.X + kBatchMaxR * kBatchMaxR;
   m.Yf = reinterpret_cast<float*>(m.GL + kBatchMaxR * kBatchMaxR);
   m.Lt = m.Yf + IR;
-  m.flag = reinterpret_cast<int*>(m.Lt + IR);
+  m.work = reinterpret_cast<double*>(m.Lt + IR);
+  m.flag = reinterpret_cast<int*>(m.work + 2 * kBatchMaxR * kBatchMaxR + kBatchMaxR);
   __shared__ double s_norm, s_sum;
   __shared__ int s_stop;
 
@@ -198,7 +289,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
     a.Q = v.Q;
     a.J = v.J();
     a.R = Rn;
-    a.ntiles = (a.J + kJT - 1) / kJT;
+    a.ntiles = (a.J + JT - 1) / JT;
     a.nbuf = 2;
     a.vec_ok = (((uintptr_t)cur % 16) == 0) && ((v.Q * 4) % 16 == 0);
     a.st = nullptr;
@@ -206,7 +297,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
     // ---- Sec. 4: Y0 = B_(n) S, ||B_(n)||^2; L0 = Q of QR(Y0) by CholeskyQR2 ----
     a.mode = PASS_INIT;
     a.sketch_state = b.seed ^ ((uint64_t)n << 56);
-    double nrm = pass_cta<float, RC, RPT, RW, kThreads>(a, 0, 1, 0, smem, m.Yf);
+    double nrm = pass_cta<float, RC, RPT, RW, kThreads, JT>(a, 0, 1, 0, smem, m.Yf);
     if (threadIdx.x == 0) s_norm = nrm;
     __syncthreads();
     const double normM2 = s_norm;
@@ -225,7 +316,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
       a.mode = PASS_SWEEP;
       a.L = m.Lt;
       a.Wout = (k >= 1 || k + 1 >= b.max_sweeps) ? dest : nullptr;
-      const double rs = pass_cta<float, RC, RPT, RW, kThreads>(a, 0, 1, 0, smem, m.Yf);
+      const double rs = pass_cta<float, RC, RPT, RW, kThreads, JT>(a, 0, 1, 0, smem, m.Yf);
       for (int e = threadIdx.x; e < I * Rn; e += blockDim.x) m.Y[e] = (double)m.Yf[e];
       // e_k and the Eq. 5.01 stop rule
       if (threadIdx.x == 0) {
@@ -245,12 +336,12 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
       ++k;
       if (s_stop) break;
       // ---- L_{k+1} = Y X^-1 with X = Q^T Y, then its Q factor ----
-      cta_gram(m.L, m.Y, I, Rn, m.X);
-      if (cta_chol(m.X, Rn, m.flag)) {
+      cta_gram(m.L, m.Y, I, Rn, m.X, false);
+      if (cta_chol(m.X, Rn, m.flag, m.work)) {
         fail = 1;
         break;
       }
-      cta_rowsolve(m.Y, m.X, 1, m.Z, I, Rn);
+      cta_rowsolve(m.Y, m.X, 1, m.Z, I, Rn, m.work);
       fail = cta_cholqr(m.Z, m, I, Rn, m.L);
     }
     if (threadIdx.x == 0) converged = s_stop ? converged : 0;
@@ -273,8 +364,8 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
   __syncthreads();
 }
 
-template <int RC, int RPT, int RW>
-__global__ void __launch_bounds__(kThreads) batched_kernel(BatchArgs b, size_t pass_bytes) {
+template <int RC, int RPT, int RW, int JT>
+__global__ void __launch_bounds__(kThreads, 1) batched_kernel(BatchArgs b, size_t pass_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_t;
   while (true) {
@@ -283,37 +374,39 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(BatchArgs b, size_t p
     const int t = s_t;
     __syncthreads();
     if (t >= b.count) return;
-    run_tensor<RC, RPT, RW>(b, t, smem_raw, pass_bytes);
+    run_tensor<RC, RPT, RW, JT>(b, t, smem_raw, pass_bytes);
   }
 }
 
 struct Variant {
-  int rc, rpt, rw;
+  int rc, rpt, rw, jt;
   void* fn;
 };
 
-template <int RC, int RPT, int RW>
+template <int RC, int RPT, int RW, int JT>
 Variant make_variant() {
-  return Variant{RC, RPT, RW, reinterpret_cast<void*>(&batched_kernel<RC, RPT, RW>)};
+  return Variant{RC, RPT, RW, JT, reinterpret_cast<void*>(&batched_kernel<RC, RPT, RW, JT>)};
 }
 
 std::vector<Variant> variants() {
-  // tile shapes the autotuner chooses between (all cover I <= 128, R <= 16)
-  return {make_variant<16, 2, 4>(), make_variant<16, 1, 8>(), make_variant<16, 2, 8>()};
+  // tile shapes the autotuner chooses between (all cover I <= 128, R <= 16);
+  // 32-column tiles halve the per-tile latency a CTA pays on a small tensor
+  return {make_variant<16, 2, 4, 16>(), make_variant<16, 1, 8, 16>(), make_variant<16, 2, 8, 16>(),
+          make_variant<16, 2, 4, 32>(), make_variant<16, 2, 8, 32>()};
 }
 
 size_t pass_region(const Variant& v) {
   const int rowt = kThreads / (v.rc / v.rw);
-  size_t b = pass_smem_bytes<float>(kBatchMaxI, v.rc, rowt * v.rpt, 2, kThreads);
+  size_t b = pass_smem_bytes<float>(kBatchMaxI, v.rc, rowt * v.rpt, 2, kThreads, v.jt);
   // slack rows are sized for the smallest I the shape serves
-  b += (size_t)slack_rows(16, rowt * v.rpt) * kJTP * sizeof(float);
+  b += (size_t)slack_rows(16, rowt * v.rpt) * (v.jt + 4) * sizeof(float);
   return (b + 15) / 16 * 16;
 }
 
 size_t la_region() {
   const size_t IR = (size_t)kBatchMaxI * kBatchMaxR;
   return 3 * IR * sizeof(double) + 2 * kBatchMaxR * kBatchMaxR * sizeof(double) +
-         2 * IR * sizeof(float) + 16;
+         2 * IR * sizeof(float) + (2 * kBatchMaxR * kBatchMaxR + kBatchMaxR) * sizeof(double) + 16;
 }
 
 struct Plan {

@@ -51,6 +51,32 @@ __device__ __forceinline__ float sketch_entry(uint64_t state, uint64_t j, int R,
   return (float)(uint32_t)(z >> 40) * (1.0f / 16777216.0f);
 }
 
+// d > tiny for a pivot, on the bit patterns (both non-negative; NaN fails):
+// integer compares keep FP64 instructions off the serial chain.
+__device__ __forceinline__ bool pivot_ok(double d, long long tiny_bits) {
+  const long long b = __double_as_longlong(d);
+  return b > tiny_bits && ((b >> 52) & 0x7ff) != 0x7ff;
+}
+
+// 1/d for a positive normal double: FP32 reciprocal of the leading bits, then
+// x = x0 (1 + e + e^2) with e = 1 - d x0 (Newton's method continued to third
+// order), ~2^-66 relative before the last rounding. Three dependent FP64
+// operations instead of a full double division.
+__device__ __forceinline__ double fast_rcp64(double d) {
+  const int hi = __double2hiint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  if (ex < -120 || ex > 120) return 1.0 / d;   // callers pass d > 0
+  const unsigned lo = (unsigned)__double2loint(d);
+  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
+  const float rf = __frcp_rn(f);
+  const int rb = __float_as_int(rf);
+  const int rex = ((rb >> 23) & 0xff) - 127;
+  const double x0 = __hiloint2double(((rex + 1023) << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+  const double e = fma(-d, x0, 1.0);
+  const double e2 = fma(e, e, e);
+  return fma(x0, e2, x0);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
