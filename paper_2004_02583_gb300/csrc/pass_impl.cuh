@@ -105,6 +105,8 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Issue the copies of tile t (JT columns) into Tb (I x (JT + 4)). Columns beyond J are zero-filled.
+// Column c of the tile is B[p, :, q] with (p, q) stepped from the tile's first
+// column: one division per tile, none per element.
 template <typename T, int JT = kJT>
 __device__ __forceinline__ void issue_tile(const PassArgs<T>& a, long long t, T* Tb) {
   const long long I = a.I, Q = a.Q;
@@ -122,24 +124,32 @@ __device__ __forceinline__ void issue_tile(const PassArgs<T>& a, long long t, T*
       cp_async16(Tb + i * (JT + 4) + k * EPV, base + i * Q + k * EPV, 16);
     }
   } else if (Q >= JT) {
-    // column-fastest element copies (rows may straddle two p)
+    // column-fastest element copies; the tile's columns span at most two p
     for (long long e = tid; e < I * JT; e += nt) {
       const long long i = e / JT;
       const int c = (int)(e - i * JT);
-      const long long j = j0 + c;
-      const bool ok = j < a.J;
-      const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
-      cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+      const bool ok = j0 + c < a.J;
+      long long q = q0 + c, p = p0;
+      if (q >= Q) {
+        q -= Q;
+        ++p;
+      }
+      cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, a.X + (ok ? (p * I + i) * Q + q : 0),
+                               ok ? (int)sizeof(T) : 0);
     }
   } else {
-    // row-fastest element copies: consecutive threads read consecutive i
-    for (long long e = tid; e < I * JT; e += nt) {
-      const int c = (int)(e / I);
-      const long long i = e - (long long)c * I;
-      const long long j = j0 + c;
-      const bool ok = j < a.J;
-      const long long p = ok ? j / Q : 0, q = ok ? j - p * Q : 0;
-      cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, a.X + (p * I + i) * Q + q, ok ? (int)sizeof(T) : 0);
+    // short rows (Q < JT; Q = 1 for the last mode): column by column, consecutive
+    // threads read consecutive i (contiguous when Q = 1)
+    long long p = p0, q = q0;
+    for (int c = 0; c < JT; ++c) {
+      const bool ok = j0 + c < a.J;
+      const T* col = a.X + (ok ? p * I * Q + q : 0);
+      for (long long i = tid; i < I; i += nt)
+        cp_async_elem<sizeof(T)>(Tb + i * (JT + 4) + c, col + (ok ? i * Q : 0), ok ? (int)sizeof(T) : 0);
+      if (++q == Q) {
+        q = 0;
+        ++p;
+      }
     }
   }
 }
