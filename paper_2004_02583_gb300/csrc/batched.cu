@@ -98,7 +98,14 @@ __device__ int cta_chol(double* G, int R, int* flag, double* w) {
   double* Lc = w;          // [2][kBatchMaxR]
   __shared__ double rs[kBatchMaxR];
   __shared__ long long tiny_bits;
+  __shared__ int tri[(kBatchMaxR - 1) * kBatchMaxR / 2];   // packed (i', j') of a dense index
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int a = tid; a < (R - 1) * R / 2; a += blockDim.x) {
+    int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
+    while (ip * (ip + 1) / 2 > a) --ip;
+    while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
+    tri[a] = (ip << 16) | (a - ip * (ip + 1) / 2);
+  }
   for (int o = tid; o < R * R; o += blockDim.x) {
     const int r = o / R, c = o % R;
     if (r > c) G[r * R + c] = 0.5 * (G[r * R + c] + G[c * R + r]);
@@ -126,28 +133,26 @@ __device__ int cta_chol(double* G, int R, int* flag, double* w) {
     if (warp == 0) {
       const int i = c1 + lane;
       double v = i < R ? fma(-G[i * R + k], Lc[cb + c1], G[i * R + c1]) : 0.0;
-      double dinv = 0.0;
-      if (lane == 0) {
-        double d = v;
-        if (!pivot_ok(d, tiny_bits)) {
-          d = 1.0;
+      double d = __shfl_sync(0xffffffffu, v, 0);
+      if (!pivot_ok(d, tiny_bits)) {
+        d = 1.0;
+        if (lane == 0) {
           v = 1.0;
           *flag = 1;
         }
-        dinv = fast_rcp64(d);
       }
-      dinv = __shfl_sync(0xffffffffu, dinv, 0);
+      const double dinv = fast_rcp64(d);
       if (i < R) {
         G[i * R + c1] = v;
         if (i > c1) Lc[(kBatchMaxR - cb) + i] = v * dinv;
       }
-    } else {
+    } else if (warp != 4) {
+      // warps sharing warp 0's SMSP stay off the FP64 pipe the serial chain uses
       const int m = R - 2 - k, na = m * (m + 1) / 2;
-      for (int a = tid - 32; a < na; a += blockDim.x - 32) {
-        int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
-        while (ip * (ip + 1) / 2 > a) --ip;
-        while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
-        const int i = k + 2 + ip, j = k + 2 + (a - ip * (ip + 1) / 2);
+      const int tt = tid < 128 ? tid - 32 : tid - 64;
+      for (int a = tt; a < na; a += blockDim.x - 64) {
+        const int ij = tri[a];
+        const int i = k + 2 + (ij >> 16), j = k + 2 + (ij & 0xffff);
         G[i * R + j] = fma(-G[i * R + k], Lc[cb + j], G[i * R + j]);
       }
     }

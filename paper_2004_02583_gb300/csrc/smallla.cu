@@ -240,6 +240,15 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
   __shared__ double Lc[2][kMaxR];
   __shared__ double rs[kMaxR];
   __shared__ long long tiny_bits;
+  // (i', j') of dense index a = i'(i'+1)/2 + j' over a lower triangle, packed
+  // 16:16; the trailing block of every step enumerates a prefix of it
+  __shared__ int tri[(kMaxR - 1) * kMaxR / 2];
+  for (int a = tid; a < (R - 1) * R / 2; a += kSmallThreads) {
+    int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
+    while (ip * (ip + 1) / 2 > a) --ip;
+    while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
+    tri[a] = (ip << 16) | (a - ip * (ip + 1) / 2);
+  }
   for (int o = tid; o < R * R; o += kSmallThreads) {
     const int r = o / R, c = o % R;
     if (c <= r) {
@@ -287,17 +296,17 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
         const int i = c1 + lane + 32 * h;
         v[h] = i < R ? fma(-S[i * R + k], lk, S[i * R + c1]) : 0.0;
       }
-      double dinv = 0.0;
-      if (lane == 0) {
-        double d = v[0];
-        if (!pivot_ok(d, tiny_bits)) {
-          d = 1.0;
+      // every lane takes the pivot's reciprocal (one warp instruction either
+      // way; no divergent branch and no shuffle after it)
+      double d = __shfl_sync(0xffffffffu, v[0], 0);
+      if (!pivot_ok(d, tiny_bits)) {
+        d = 1.0;
+        if (lane == 0) {
           v[0] = 1.0;
           fail = 1;
         }
-        dinv = fast_rcp64(d);
       }
-      dinv = __shfl_sync(0xffffffffu, dinv, 0);
+      const double dinv = fast_rcp64(d);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int i = c1 + lane + 32 * h;
@@ -306,16 +315,16 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
           if (i > c1) Lc[cb ^ 1][i] = v[h] * dinv;
         }
       }
-    } else {
-      // the rest of the trailing block: i >= j >= k+2
+    } else if (warp != 4) {
+      // the rest of the trailing block: i >= j >= k+2, on the warps that do not
+      // share warp 0's SMSP (warp w runs on SMSP w % 4): its FP64 pipe stays free
+      // for the serial chain
       const int m = R - 2 - k;
       const int na = m * (m + 1) / 2;
-      for (int a = tid - 32; a < na; a += kSmallThreads - 32) {
-        // a = i'(i'+1)/2 + j', 0 <= j' <= i' < m
-        int ip = (int)((sqrtf(8.f * (float)a + 1.f) - 1.f) * 0.5f);
-        while (ip * (ip + 1) / 2 > a) --ip;
-        while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
-        const int i = k + 2 + ip, j = k + 2 + (a - ip * (ip + 1) / 2);
+      const int tt = tid < 128 ? tid - 32 : tid - 64;   // 0 .. 191
+      for (int a = tt; a < na; a += kSmallThreads - 64) {
+        const int ij = tri[a];
+        const int i = k + 2 + (ij >> 16), j = k + 2 + (ij & 0xffff);
         S[i * R + j] = fma(-S[i * R + k], Lc[cb][j], S[i * R + j]);
       }
     }
