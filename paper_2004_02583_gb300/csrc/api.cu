@@ -186,6 +186,10 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   const long long mine = j.v.P * j.v.I * j.v.Q;
   j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 &&
             mine <= std::max(tot / 4, 16LL << 20);
+  // the same tensors with the rank split across CTAs cannot form the residual
+  // inside the pass: take it once, exactly, when the mode is done
+  j.final_resid = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr &&
+                  mine <= std::max(tot / 4, 16LL << 20);
   return TALS_OK;
 }
 
@@ -297,11 +301,21 @@ tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters) {
   return TALS_OK;
 }
 
+tals_status mode_final_resid(tals_ctx* c, const ModeJob& j) {
+  if (!j.final_resid) return TALS_OK;
+  cudaError_t e = launch_mode_residual((const float*)j.X, j.v, j.R, (const float*)j.Wdest,
+                                       (const float*)c->Lt, c->spart, (int)c->spart_n, j.st,
+                                       c->stream);
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "mode residual");
+}
+
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   tals_status st = mode_setup(c, j);
   if (st != TALS_OK) return st;
   if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-  return mode_loop_host(c, j, c->opts.max_sweeps);
+  if ((st = mode_loop_host(c, j, c->opts.max_sweeps)) != TALS_OK) return st;
+  if ((st = mode_final_resid(c, j)) != TALS_OK) return st;
+  return j.final_resid ? read_states(c) : TALS_OK;
 }
 
 tals_status mode_status(tals_ctx* c, int n) {

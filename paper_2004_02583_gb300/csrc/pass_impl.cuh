@@ -243,14 +243,30 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
     const int ncol = (int)min((long long)JT, a.J - j0);
 
     if (a.mode == PASS_INIT && rchunk == 0) {
-      T nacc = T(0);
-      for (long long e = tid; e < I * JT; e += NT) {
-        const long long i = e / JT;
-        const int c = (int)(e - i * JT);
-        const T x = Tb[i * JTP + c];
-        nacc += (c < ncol) ? x * x : T(0);
+      if constexpr (sizeof(T) == 4) {
+        // ||B||^2 for the stop rule: exact products (x^2 = p + e by FMA) in a
+        // Neumaier-compensated FP32 sum, added to the FP64 total per tile
+        float hi = 0.f, lo = 0.f;
+        for (long long e = tid; e < I * JT; e += NT) {
+          const long long i = e / JT;
+          const int c = (int)(e - i * JT);
+          const float x = (c < ncol) ? Tb[i * JTP + c] : 0.f;
+          const float pq = x * x, pe = fmaf(x, x, -pq);
+          const float tq = hi + pq;
+          lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
+          hi = tq;
+        }
+        sacc += (double)hi + (double)lo;
+      } else {
+        T nacc = T(0);
+        for (long long e = tid; e < I * JT; e += NT) {
+          const long long i = e / JT;
+          const int c = (int)(e - i * JT);
+          const T x = Tb[i * JTP + c];
+          nacc += (c < ncol) ? x * x : T(0);
+        }
+        sacc += (double)nacc;
       }
-      sacc += (double)nacc;
     }
 
     if (do_w) {

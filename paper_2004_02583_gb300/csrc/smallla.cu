@@ -556,3 +556,77 @@ cudaError_t launch_transpose(int dtype, const void* In, long long rows, long lon
 }
 
 }  // namespace tals
+
+namespace tals {
+
+// ---------------------------------------------------------------------------
+// Exact error of a finished mode, ||B_(n) - Q W^T||^2, from the tensor, the
+// final W (P x R x Q layout) and the FP32 basis Q actually used: for modes
+// whose sweeps could only use ||B||^2 - ||W||^2 (rank split across CTAs), so
+// the reported e_n is free of that cancellation. Columns in tiles of 32, W
+// tile in shared memory, 8 row groups; exact squares in compensated FP32 per
+// thread, FP64 per block.
+// ---------------------------------------------------------------------------
+__global__ void mode_residual_kernel(const float* __restrict__ X, long long P, long long I,
+                                     long long Q, int R, const float* __restrict__ W,
+                                     const float* __restrict__ L, double* __restrict__ part,
+                                     const ModeState* st) {
+  extern __shared__ float Wt[];   // [32][R + 1]
+  __shared__ double red[32];
+  const long long J = P * Q;
+  const int tid = threadIdx.x, c = tid & 31, rg = tid >> 5, nrg = blockDim.x >> 5;
+  float hi = 0.f, lo = 0.f;
+  for (long long t = blockIdx.x; t * 32 < J; t += gridDim.x) {
+    const long long j0 = t * 32;
+    __syncthreads();
+    for (int e = tid; e < 32 * R; e += blockDim.x) {
+      const int cc = e & 31, r = e >> 5;
+      const long long j = j0 + cc;
+      float w = 0.f;
+      if (j < J) {
+        const long long p = j / Q, q = j - p * Q;
+        w = W[(p * R + r) * Q + q];
+      }
+      Wt[cc * (R + 1) + r] = w;
+    }
+    __syncthreads();
+    const long long j = j0 + c;
+    if (j < J) {
+      const long long p = j / Q, q = j - p * Q;
+      const float* xcol = X + p * I * Q + q;
+      const float* wc = Wt + c * (R + 1);
+      for (long long i = rg; i < I; i += nrg) {
+        float y = xcol[i * Q];
+        const float* lrow = L + i * R;
+        for (int r = 0; r < R; ++r) y = fmaf(-lrow[r], wc[r], y);
+        const float pq = y * y, pe = fmaf(y, y, -pq);
+        const float tq = hi + pq;
+        lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
+        hi = tq;
+      }
+    }
+  }
+  const double tot = block_sum((double)hi + (double)lo, red);
+  if (tid == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void mode_residual_finish(const double* __restrict__ part, int n, ModeState* st) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
+  const double tot = block_sum(v, red);
+  if (threadIdx.x == 0 && st->status == 0) st->e_cur = sqrt(tot > 0.0 ? tot : 0.0);
+}
+
+cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
+                                 const float* L, double* part, int nparts, ModeState* st,
+                                 cudaStream_t s) {
+  const long long tiles = (v.J() + 31) / 32;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(nparts, tiles));
+  const size_t sm = (size_t)32 * (R + 1) * sizeof(float);
+  mode_residual_kernel<<<grid, 256, sm, s>>>(X, v.P, v.I, v.Q, R, W, L, part, st);
+  mode_residual_finish<<<1, 256, 0, s>>>(part, grid, st);
+  return cudaGetLastError();
+}
+
+}  // namespace tals
