@@ -187,9 +187,9 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 &&
             mine <= std::max(tot / 4, 16LL << 20);
   // the same tensors with the rank split across CTAs cannot form the residual
-  // inside the pass: take it once, exactly, when the mode is done
-  j.final_resid = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr &&
-                  mine <= std::max(tot / 4, 16LL << 20);
+  // inside the pass: the sweep writes W and a residual kernel takes it
+  j.resid_kernel = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr &&
+                   mine <= std::max(tot / 4, 16LL << 20);
   return TALS_OK;
 }
 
@@ -208,7 +208,8 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   cudaError_t e;
 #define TALS_CK(x)                                   \
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
-  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s, bulk_max));
+  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid || j.resid_kernel, s,
+                            bulk_max));
   // Sec. 4: Y0 = B_(n) S and ||B_(n)||^2 in one pass
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_INIT, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr,
                       sketch_state(c->opts.seed, j.n), j.st, 1 << 30, s));
@@ -247,7 +248,7 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   cudaError_t e;
   // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
-                      j.Wdest, 0, j.st, 1, s, nullptr, j.resid));
+                      j.Wdest, 0, j.st, j.resid_kernel ? 0 : 1, s, nullptr, j.resid));
   return mode_sweep_tail(c, j, j.pc.grid_x, j.pc.grid_x * j.pc.grid_y, 1);
 }
 
@@ -259,6 +260,12 @@ tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int 
   // Y (FP64), X = Q_k^T Y partials, ||W||^2
   TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, gx, I, R, c->Y64, 2, c->L64, c->Gpart,
                              j.rp, c->spart, nsp, 1, j.st, nullptr, s));
+  // e_k^2 = ||B - Q W^T||^2 from this sweep's W (written by the pass) into sW;
+  // the Y partials are consumed, so their buffer holds the residual partials
+  if (j.resid_kernel && test_op == 1)
+    TALS_CK(launch_mode_residual((const float*)j.X, j.v, R, (const float*)j.Wdest,
+                                 (const float*)c->Lt, (double*)c->Ypart, (long long)(c->ypart_elems / 2),
+                                 j.st, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
   // e_k, Eq. 5.01, and chol(X) if the sweep continues
   TALS_CK(launch_small(c->Gfin, 1, R, test_op, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s,
@@ -301,21 +308,11 @@ tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters) {
   return TALS_OK;
 }
 
-tals_status mode_final_resid(tals_ctx* c, const ModeJob& j) {
-  if (!j.final_resid) return TALS_OK;
-  cudaError_t e = launch_mode_residual((const float*)j.X, j.v, j.R, (const float*)j.Wdest,
-                                       (const float*)c->Lt, c->spart, (int)c->spart_n, j.st,
-                                       c->stream);
-  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "mode residual");
-}
-
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   tals_status st = mode_setup(c, j);
   if (st != TALS_OK) return st;
   if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-  if ((st = mode_loop_host(c, j, c->opts.max_sweeps)) != TALS_OK) return st;
-  if ((st = mode_final_resid(c, j)) != TALS_OK) return st;
-  return j.final_resid ? read_states(c) : TALS_OK;
+  return mode_loop_host(c, j, c->opts.max_sweeps);
 }
 
 tals_status mode_status(tals_ctx* c, int n) {

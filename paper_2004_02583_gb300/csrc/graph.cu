@@ -102,7 +102,6 @@ tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) 
     if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
   }
   if ((st = capture_while(c, j, [&] { return mode_sweep_launch(c, j); })) != TALS_OK) return st;
-  if ((st = mode_final_resid(c, j)) != TALS_OK) return st;
   if (U_out) {
     cudaError_t e =
         cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, cudaMemcpyDeviceToDevice, cs);

@@ -21,7 +21,7 @@ struct ModeJob {
   unsigned long long cond = 0;   // CUDA graph conditional handle of the sweep loop
   int has_cond = 0;
   int resid = 0;                 // sweeps measure the error from the explicit residual
-  int final_resid = 0;           // exact ||B - Q W^T|| once the mode is done
+  int resid_kernel = 0;          // rank split across CTAs: e_k from a residual kernel per sweep
 };
 
 struct DriveState {
@@ -43,7 +43,6 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j);
 tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int test_op);
 tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a, int bulk_max);
 uint64_t sketch_state(uint64_t seed, int mode);
-tals_status mode_final_resid(tals_ctx* c, const ModeJob& j);
 tals_status mode_init_tail(tals_ctx* c, const ModeJob& j, bool set_norm_a, int gx, const double* sp,
                            int nsp);
 tals_status read_states(tals_ctx* c);

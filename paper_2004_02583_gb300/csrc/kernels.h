@@ -98,10 +98,15 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
 // views other than Q >= 64 or Q == 1).
 cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,
                              long long sa, long long sb, long long Aout, float* out, cudaStream_t s);
-// e_n = ||B_(n) - Q W^T|| of a finished mode into st->e_cur (FP32 data).
+// st->sW = ||B_(n) - Q W^T||^2 of a sweep (FP32 data); part: scratch for up to
+// cap FP64 partial sums.
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
-                                 const float* L, double* part, int nparts, ModeState* st,
+                                 const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s);
+long long mode_resid_gemm_parts(long long P, long long Aout, long long Q);
+cudaError_t launch_mode_resid_gemm(const float* X, long long P, long long Bin, long long Q,
+                                   const float* M, long long sa, long long sb, long long Aout,
+                                   const float* B, double* part, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s,
                            double* sq = nullptr);
 int to_bf16_blocks(size_t n, int sms);

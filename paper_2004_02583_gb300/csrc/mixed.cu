@@ -106,9 +106,7 @@ tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   if (st != TALS_OK) return st;
   if (!mixed_tc_mode(c, j)) {
     if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-    if ((st = mode_loop_host(c, j, c->opts.max_sweeps)) != TALS_OK) return st;
-    if ((st = mode_final_resid(c, j)) != TALS_OK) return st;
-    return j.final_resid ? read_states(c) : TALS_OK;
+    return mode_loop_host(c, j, c->opts.max_sweeps);
   }
   const int grid = mixed_grid(c, j);
   if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");

@@ -560,12 +560,11 @@ cudaError_t launch_transpose(int dtype, const void* In, long long rows, long lon
 namespace tals {
 
 // ---------------------------------------------------------------------------
-// Exact error of a finished mode, ||B_(n) - Q W^T||^2, from the tensor, the
-// final W (P x R x Q layout) and the FP32 basis Q actually used: for modes
-// whose sweeps could only use ||B||^2 - ||W||^2 (rank split across CTAs), so
-// the reported e_n is free of that cancellation. Columns in tiles of 32, W
-// tile in shared memory, 8 row groups; exact squares in compensated FP32 per
-// thread, FP64 per block.
+// Exact e_k^2 = ||B_(n) - Q W^T||^2 of a sweep from the tensor, the sweep's W
+// (P x R x Q layout) and the FP32 basis Q it used: for modes whose rank is split
+// across CTAs, so the pass cannot form the residual itself and ||B||^2 - ||W||^2
+// would cancel. Generic views: columns in tiles of 32, W tile in shared memory,
+// 8 row groups; exact squares in compensated FP32 per thread, FP64 per block.
 // ---------------------------------------------------------------------------
 __global__ void mode_residual_kernel(const float* __restrict__ X, long long P, long long I,
                                      long long Q, int R, const float* __restrict__ W,
@@ -610,19 +609,30 @@ __global__ void mode_residual_kernel(const float* __restrict__ X, long long P, l
   if (tid == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void mode_residual_finish(const double* __restrict__ part, int n, ModeState* st) {
+// Sum of the n residual partials into the mode state: per sweep into sW (the
+// TEST kernel's e^2 for modes that measure the residual), unless the mode is done.
+__global__ void mode_residual_finish(const double* __restrict__ part, long long n, ModeState* st) {
+  if (st->done) return;
   __shared__ double red[32];
   double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
   const double tot = block_sum(v, red);
-  if (threadIdx.x == 0 && st->status == 0) st->e_cur = sqrt(tot > 0.0 ? tot : 0.0);
+  if (threadIdx.x == 0) st->sW = tot;
 }
 
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
-                                 const float* L, double* part, int nparts, ModeState* st,
+                                 const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s) {
+  // the tiled GEMM form where the view has long rows (Q >= 64)
+  const long long ng = mode_resid_gemm_parts(v.P, v.I, v.Q);
+  if (ng > 0 && ng <= cap) {
+    cudaError_t e = launch_mode_resid_gemm(W, v.P, R, v.Q, L, R, 1, v.I, X, part, s);
+    if (e != cudaSuccess) return e;
+    mode_residual_finish<<<1, 256, 0, s>>>(part, ng, st);
+    return cudaGetLastError();
+  }
   const long long tiles = (v.J() + 31) / 32;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(nparts, tiles));
+  const int grid = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(cap, 1024), tiles));
   const size_t sm = (size_t)32 * (R + 1) * sizeof(float);
   mode_residual_kernel<<<grid, 256, sm, s>>>(X, v.P, v.I, v.Q, R, W, L, part, st);
   mode_residual_finish<<<1, 256, 0, s>>>(part, grid, st);
