@@ -540,12 +540,20 @@ def run_c3(args):
     clocks = Clocks(0)
     clocks.start()
     ctxs = {}
-    for prec in ("mixed_bf16", "native"):
-        ctx = tals.Context(A, cfg.ranks, eta=cfg.eta, seed=1, precision=prec)
+    precs = (args.precision,) if args.no_compare else ("mixed_bf16", "native")
+    for prec in precs:
+        ctx = tals.Context(A, cfg.ranks, eta=cfg.eta, seed=1, precision=prec,
+                           use_graph=not args.no_graph)
         ms, (_, _, st) = _time_gpu(lambda: ctx.st_hosvd(G, Us), args.steps, args.warmup)
         res[prec] = (ms, st)
         ctxs[prec] = ctx
     clk = clocks.stop()
+    if args.no_compare:
+        print(json.dumps({"precision": args.precision, "ms_per_step": res[args.precision][0],
+                          "sweeps": res[args.precision][1]["sweeps"]}))
+        for c in ctxs.values():
+            c.close()
+        return
     roof, roof_tc = _pass_rooflines(ctxs["native"], ctxs["mixed_bf16"], res["native"][1]["order"][0],
                                     clk.get("sm_mhz") or 2070.0, sms, peaks)
     # oracle on a 128^3 x S slab of the same recipe, scaled to the full tensor
