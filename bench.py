@@ -193,6 +193,8 @@ def main():
                     help="skip the other precision path (per-path launch lists under ncu)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="c4: number of tensors (4096 is the workload; fewer for profiling)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default): 512^3 FP32 st-HOSVD, the benchmark line; c1: 64^3 FP64; "
                          "c3: 128^4 FP32 mixed vs plain; c4: 4096 small tensors batched vs "
@@ -593,7 +595,7 @@ def run_c4(args):
     import paper_2004_02583_gb300 as tals
     import workloads as W
     from oracle import tucker_oracle as O
-    count, eta = 4096, 1e-6
+    count, eta = args.batch_count, 1e-6
     items = W.batched(W.SEED_BASE + 3, count)
     As = [torch.from_numpy(a).cuda() for a, _, _ in items]
     ranks = [r for _, _, r in items]
@@ -614,7 +616,7 @@ def run_c4(args):
     peaks, _ = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # per-tensor loop of the plain path on a subset, contexts made beforehand
-    sub = 256
+    sub = min(256, count)
     ctxs = [tals.Context(As[t], ranks[t], eta=eta, seed=1) for t in range(sub)]
     loop_ms, _ = _time_gpu(lambda: [c.st_hosvd() for c in ctxs], 1, 1)
     loop_ms *= count / sub
@@ -622,20 +624,20 @@ def run_c4(args):
         c.close()
     # parity on a few tensors against the oracle
     gaps = []
-    for t in range(8):
+    for t in range(min(8, count)):
         a, dims, rk = items[t]
         ref = O.st_hosvd_als(a.astype(np.float64), rk, eta=eta, seed=1)
         own = O.rel_error(a.astype(np.float64), Gs[t].double().cpu().numpy(),
                           [u.double().cpu().numpy() for u in Us[t]])
         gaps.append(abs(own - O.rel_error(a.astype(np.float64), ref.G, ref.U)))
-    osub = 64
+    osub = min(64, count)
     sec, n = _oracle_time(lambda: [O.st_hosvd_als(items[t][0].astype(np.float64), items[t][2], eta=eta,
                                                   seed=1) for t in range(osub)], 10.0)
-    line = {"metric": "batched st-HOSVD-ALS throughput (4096 uneven small tensors)",
+    line = {"metric": f"batched st-HOSVD-ALS throughput ({count} uneven small tensors)",
             "value": round(count * 1e3 / ms, 1), "unit": "tensors/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3), "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "4096 x st-HOSVD-ALS FP32, I ~ U{16..96}, R ~ U{4..16}, 1e-2 noise, "
+            "config": {"workload": f"{count} x st-HOSVD-ALS FP32, I ~ U{{16..96}}, R ~ U{{4..16}}, 1e-2 noise, "
                                    "eta 1e-6, one persistent graph-captured launch",
                        "total_input_bytes": int(sum(a.nbytes for a, _, _ in items)),
                        "l2": "inputs (GBs) larger than L2",
