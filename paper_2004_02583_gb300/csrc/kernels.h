@@ -95,7 +95,7 @@ cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float
                            double* spart, int* err, int grid, cudaStream_t s, int init = 0,
                            uint64_t sketch = 0);
 // out[p, a, q] = sum_b M[a*sa + b*sb] X[p, b, q] (FP32; cudaErrorNotSupported for
-// views other than Q >= 64 or Q == 1).
+// views other than Q == 1, Q % 4 == 0 with 16-byte aligned X and out, or Q >= 64).
 cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,
                              long long sa, long long sb, long long Aout, float* out, cudaStream_t s);
 // st->sW = ||B_(n) - Q W^T||^2 of a sweep (FP32 data); part: scratch for up to
@@ -103,10 +103,23 @@ cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long lo
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
                                  const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s);
-long long mode_resid_gemm_parts(long long P, long long Aout, long long Q);
+// Partial sums launch_mode_resid_gemm writes for this view (0: not covered).
+long long mode_resid_gemm_parts(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                long long sa, long long sb, long long Aout, const float* B);
 cudaError_t launch_mode_resid_gemm(const float* X, long long P, long long Bin, long long Q,
                                    const float* M, long long sa, long long sb, long long Aout,
                                    const float* B, double* part, cudaStream_t s);
+// Any-view mode product out[p, a, q] = sum_b M[a*sa + b*sb] X[p, b, q]
+// (T = float or double); the fallback of the paths above.
+template <typename T>
+cudaError_t launch_mode_gemm_any(const T* X, long long P, long long Bin, long long Q, const T* M, long long sa,
+                                 long long sb, long long Aout, T* out, cudaStream_t s);
+// Ubar (I x R) = X_(n) V_(n)^T for X viewed P x I x Q and V viewed P x R x Q, in
+// S column splits (part: S * I * R elements of scratch).
+int factor_adjoint_splits(long long P, long long I, long long Q, int R, int sms);
+template <typename T>
+cudaError_t launch_factor_adjoint_any(const T* X, long long P, long long I, long long Q, const T* V, int R,
+                                      int S, T* part, T* Ubar, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s,
                            double* sq = nullptr);
 int to_bf16_blocks(size_t n, int sms);

@@ -8,13 +8,25 @@
 // output tiles once and keeps a 4 x 8 block of outputs per thread in registers
 // (paired FMAs along the contiguous output index).
 //
-// Two layouts cover the views that occur: Q >= 64 (tiles of 64 a x 128 q per
-// p, q contiguous) and Q == 1 (the last mode: tiles of 128 p x 64 a, a
-// contiguous). Other views keep the sweep kernel's PROJECT pass.
+// Two layouts cover the views that occur: Q > 1 (tiles of a x flattened
+// columns p*Q + q, q contiguous) and Q == 1 (the last mode: tiles of p x a,
+// a contiguous). Views the kernels below do not take keep the sweep kernel's
+// PROJECT pass or the any-view kernels at the end of this file.
+//
+// The main kernels (mg_pipe) are persistent: every CTA owns one a-tile for its
+// whole life (the grid is a multiple of the number of a-tiles), walks its
+// share of the column tiles and streams each tile's K chunks through a
+// four-stage cp.async ring, so the HBM stream of X never waits on the FMAs.
+// When the contraction is short (B_in <= 64, every expansion and the residual)
+// the CTA's 64 x B_in slice of M stays in shared memory for the whole launch;
+// longer contractions stage M with X. The first kernels below are the
+// fallback for views the pipelined form does not take (unaligned bases, rows
+// not a multiple of four floats).
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
+#include "pass_impl.cuh"
 
 namespace tals {
 
@@ -217,10 +229,354 @@ __global__ void __launch_bounds__(kGThreads, 2)
   if (tid == 0) part[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent pipelined mode product.
+constexpr int kMgThreads = 128;
+constexpr int kMgBK = 16;        // K chunk per stage
+constexpr int kMgResK = 64;      // longest contraction kept resident
+constexpr int kRowsXS = kMgBK + 4;   // row stride of the rows kernel's X stage (odd count of 16 B)
+
+struct MgArgs {
+  const float* X;       // P x Bin x Q (Q == 1: P x Bin)
+  long long P, Bin, Q;
+  const float* M;       // M[a, b] at M[a * sa + b * sb]
+  long long sa, sb, Aout;
+  float* out;           // P x Aout x Q
+  const float* B;       // residual form: P x Aout x Q
+  double* part;         // residual form: one FP64 partial per CTA
+  long long na;         // a-tiles (the grid is a multiple of na)
+  long long nt;         // tiles per a-tile: cols ceil(P Q / TN), rows ceil(P / TN)
+  int nk;               // K chunks
+  int vec;              // 16-byte output stores
+};
+
+// Tile geometry: TA a (outputs' rank side) x TN (cols: q, rows: p) = 8192
+// outputs per CTA, 8 x 8 per thread.
+template <bool ROWS, int TA>
+struct MgShape {
+  static constexpr int TN = 8192 / TA;
+  static constexpr int STAGES = (ROWS && TA == 32) ? 3 : 4;
+  static constexpr int XS = ROWS ? TN * kRowsXS : kMgBK * TN;   // floats per X stage
+  static constexpr int NTX = ROWS ? TA / 8 : TN / 8;             // threads along the contiguous output index
+};
+
+template <bool ROWS, bool MRES, int TA>
+constexpr size_t mg_smem_floats() {
+  using S = MgShape<ROWS, TA>;
+  const size_t ms = MRES ? 0 : (size_t)kMgBK * TA;
+  return (size_t)S::STAGES * (S::XS + ms) + (MRES ? (size_t)kMgResK * TA : 0) + 64;  // + reduction
+}
+
+// out[p, a, q] (cols) / out[p, a] (rows): ROWS selects the view, MRES the
+// resident M slice, RESID accumulates sum (B - M X)^2 instead of storing.
+template <bool ROWS, bool MRES, bool RESID, int TA>
+__global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
+  using S = MgShape<ROWS, TA>;
+  constexpr int TN = S::TN, XS = S::XS, ST = S::STAGES;
+  constexpr int MS = MRES ? 0 : kMgBK * TA;
+  extern __shared__ __align__(16) float sm[];
+  float* const ring = sm;
+  float* const Mres = sm + ST * (XS + MS);
+  const int tid = threadIdx.x;
+  // cols: ty = a-group (a = ty*8 + u), tx = column group (flattened columns j = p*Q + q:
+  //       tx*4 + {0..3} and TN/2 + tx*4 + {0..3} of the tile; Q % 4 == 0 keeps a group in one p)
+  // rows: ty = p-group (p = ty + NP*u), tx = a-group (a = tx*4 + {0..3}, TA/2 + tx*4 + {0..3})
+  constexpr int NP = TN / 8;   // rows: p-groups
+  const int tx = tid % S::NTX, ty = tid / S::NTX;
+  const long long at = blockIdx.x % a.na;
+  const long long a0 = at * TA;
+  const long long tb = blockIdx.x / a.na, ts = gridDim.x / a.na;
+  const long long ntile = tb < a.nt ? (a.nt - tb + ts - 1) / ts : 0;
+  const long long F = ntile * a.nk;
+
+  if constexpr (MRES) {
+    // the CTA's M slice, as [k][a] (zero beyond Bin and Aout)
+    for (int e = tid; e < kMgResK * TA; e += kMgThreads) {
+      int k, c;
+      if (a.sb == 1) { c = e / kMgResK; k = e % kMgResK; } else { k = e / TA; c = e % TA; }
+      const long long ga = a0 + c;
+      Mres[k * TA + c] = (ga < a.Aout && k < a.Bin) ? a.M[ga * a.sa + k * a.sb] : 0.f;
+    }
+  }
+
+  auto issue = [&](long long f) {
+    if (f < F) {
+      const long long i = f / a.nk;
+      const int kc = (int)(f - i * a.nk);
+      const long long t = tb + i * ts;
+      const long long k0 = (long long)kc * kMgBK;
+      float* xs = ring + (int)(f % ST) * (XS + MS);
+      if constexpr (ROWS) {
+        const long long p0 = t * TN;
+#pragma unroll
+        for (int j = 0; j < (TN * kMgBK / 4) / kMgThreads; ++j) {
+          const int c = tid + j * kMgThreads;
+          const int r = c >> 2, kq = (c & 3) * 4;
+          const long long gp = p0 + r, gk = k0 + kq;
+          const bool ok = gp < a.P && gk < a.Bin;
+          cp_async16(xs + r * kRowsXS + kq, ok ? a.X + gp * a.Bin + gk : a.X, ok ? 16 : 0);
+        }
+      } else {
+        // every chunk of this thread has the same column group (kMgThreads % (TN / 4) == 0)
+        const int qc = (tid % (TN / 4)) * 4;
+        const long long jc = t * TN + qc;
+        const long long p = jc / a.Q, q = jc - p * a.Q;
+        const bool jok = jc < a.P * a.Q;
+        const float* Xp = a.X + p * a.Bin * a.Q + q;
+#pragma unroll
+        for (int j = 0; j < (kMgBK * TN / 4) / kMgThreads; ++j) {
+          const int k = (tid + j * kMgThreads) / (TN / 4);
+          const long long gk = k0 + k;
+          const bool ok = jok && gk < a.Bin;
+          cp_async16(xs + k * TN + qc, ok ? Xp + gk * a.Q : a.X, ok ? 16 : 0);
+        }
+      }
+      if constexpr (!MRES) {
+        float* ms = xs + XS;
+#pragma unroll
+        for (int j = 0; j < (kMgBK * TA / 4 + kMgThreads - 1) / kMgThreads; ++j) {
+          const int c = tid + j * kMgThreads;
+          if (c < kMgBK * TA / 4) {
+            const int k = c / (TA / 4), ac = (c % (TA / 4)) * 4;
+            const long long gk = k0 + k, ga = a0 + ac;
+            const long long left = a.Aout - ga;
+            const int nv = gk < a.Bin && left > 0 ? (left < 4 ? (int)left : 4) : 0;
+            cp_async16(ms + k * TA + ac, nv > 0 ? a.M + gk * a.sb + ga : a.M, nv * 4);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  float2 acc[8][4];
+  float hi = 0.f, lo = 0.f;   // residual form: compensated sum of squares
+#pragma unroll
+  for (int s = 0; s < ST - 1; ++s) issue(s);
+  for (long long f = 0; f < F; ++f) {
+    issue(f + ST - 1);
+    cp_async_wait<ST - 1>();
+    __syncthreads();
+    const long long i = f / a.nk;
+    const int kc = (int)(f - i * a.nk);
+    if (kc == 0) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+    }
+    const float* xs = ring + (int)(f % ST) * (XS + MS);
+    const float* ms = MRES ? Mres + kc * kMgBK * TA : xs + XS;
+    if constexpr (ROWS) {
+#pragma unroll
+      for (int kq = 0; kq < kMgBK; kq += 4) {
+        float4 xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = *reinterpret_cast<const float4*>(xs + (ty + NP * u) * kRowsXS + kq);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const float4 m0 = *reinterpret_cast<const float4*>(ms + (kq + kk) * TA + tx * 4);
+          const float4 m1 = *reinterpret_cast<const float4*>(ms + (kq + kk) * TA + TA / 2 + tx * 4);
+          const float2 mp[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w), make_float2(m1.x, m1.y),
+                                make_float2(m1.z, m1.w)};
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float x = kk == 0 ? xv[u].x : kk == 1 ? xv[u].y : kk == 2 ? xv[u].z : xv[u].w;
+            const float2 x2 = make_float2(x, x);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = __ffma2_rn(x2, mp[v], acc[u][v]);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMgBK; ++k) {
+        const float4 m0 = *reinterpret_cast<const float4*>(ms + k * TA + ty * 8);
+        const float4 m1 = *reinterpret_cast<const float4*>(ms + k * TA + ty * 8 + 4);
+        const float4 x0 = *reinterpret_cast<const float4*>(xs + k * TN + tx * 4);
+        const float4 x1 = *reinterpret_cast<const float4*>(xs + k * TN + TN / 2 + tx * 4);
+        const float2 xp[4] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(x1.x, x1.y),
+                              make_float2(x1.z, x1.w)};
+        const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 m2 = make_float2(mv[u], mv[u]);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = __ffma2_rn(m2, xp[v], acc[u][v]);
+        }
+      }
+    }
+    if (kc == a.nk - 1) {
+      const long long t = tb + i * ts;
+      if constexpr (ROWS) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long gp = t * TN + ty + NP * u;
+          if (gp >= a.P) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const long long ga = a0 + h * (TA / 2) + tx * 4;
+            const float v4[4] = {acc[u][2 * h].x, acc[u][2 * h].y, acc[u][2 * h + 1].x, acc[u][2 * h + 1].y};
+            float* row = a.out + gp * a.Aout + ga;
+            if (a.vec && ga + 4 <= a.Aout) {
+              *reinterpret_cast<float4*>(row) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+            } else {
+              for (int e = 0; e < 4; ++e)
+                if (ga + e < a.Aout) row[e] = v4[e];
+            }
+          }
+        }
+      } else {
+        long long base[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long jc = t * TN + h * (TN / 2) + tx * 4;
+          const long long p = jc / a.Q, q = jc - p * a.Q;
+          base[h] = jc < a.P * a.Q ? p * a.Aout * a.Q + q : -1;   // Q % 4 == 0: whole chunk or none
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long ga = a0 + ty * 8 + u;
+          if (ga >= a.Aout) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (base[h] < 0) continue;
+            const float v4[4] = {acc[u][2 * h].x, acc[u][2 * h].y, acc[u][2 * h + 1].x, acc[u][2 * h + 1].y};
+            const long long off = base[h] + ga * a.Q;
+            if constexpr (RESID) {
+              const float4 b4 = *reinterpret_cast<const float4*>(a.B + off);
+              const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float d = bv[e] - v4[e];
+                const float pq = d * d, pe = fmaf(d, d, -pq), tq = hi + pq;
+                lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
+                hi = tq;
+              }
+            } else {
+              *reinterpret_cast<float4*>(a.out + off) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if constexpr (RESID) {
+    double* red = reinterpret_cast<double*>(Mres + (MRES ? kMgResK * TA : 0));
+    const double tot = block_sum((double)hi + (double)lo, red);
+    if (tid == 0) a.part[blockIdx.x] = tot;
+  }
+}
+
+template <bool ROWS, bool MRES, bool RESID, int TA>
+int mg_blocks_per_sm() {
+  static int occ = -1;
+  if (occ < 0) {
+    const size_t smem = mg_smem_floats<ROWS, MRES, TA>() * sizeof(float);
+    cudaFuncSetAttribute(mg_pipe<ROWS, MRES, RESID, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mg_pipe<ROWS, MRES, RESID, TA>, kMgThreads, smem) !=
+            cudaSuccess ||
+        n < 1)
+      n = 1;
+    occ = n;
+  }
+  return occ;
+}
+
+template <bool ROWS, bool MRES, bool RESID, int TA>
+void mg_run(const MgArgs& a, unsigned grid, cudaStream_t s) {
+  mg_pipe<ROWS, MRES, RESID, TA><<<grid, kMgThreads, mg_smem_floats<ROWS, MRES, TA>() * sizeof(float), s>>>(a);
+}
+
+int mg_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (sms[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 152;
+  }
+  return sms[dev];
+}
+
+// The pipelined form's launch for a view; ok = false where it does not apply
+// (then the first kernels above run).
+struct MgPlan {
+  bool ok = false;
+  bool rows = false, mres = false;
+  int ta = 64;
+  MgArgs a{};
+  long long grid = 0;
+};
+
+template <bool ROWS, bool MRES, bool RESID>
+int mg_occ(int ta) {
+  return ta == 32 ? mg_blocks_per_sm<ROWS, MRES, RESID, 32>() : mg_blocks_per_sm<ROWS, MRES, RESID, 64>();
+}
+
+template <bool RESID>
+MgPlan mg_plan(const float* X, long long P, long long Bin, long long Q, const float* M, long long sa,
+               long long sb, long long Aout, float* out, const float* B = nullptr) {
+  MgPlan pl;
+  if (P < 1 || Bin < 1 || Q < 1 || Aout < 1) return pl;
+  if (RESID && ((uintptr_t)B & 15) != 0) return pl;
+  const bool rows = Q == 1;
+  if (((uintptr_t)X & 15) != 0) return pl;
+  if (rows ? (Bin & 3) != 0 : (Q & 3) != 0) return pl;
+  const bool mres = Bin <= kMgResK;
+  if (!mres && !(sa == 1 && (sb & 3) == 0 && ((uintptr_t)M & 15) == 0)) return pl;
+  if (RESID && rows) return pl;
+  const int ta = Aout <= 32 ? 32 : 64;
+  const long long tn = 8192 / ta;
+  MgArgs& a = pl.a;
+  a.X = X; a.P = P; a.Bin = Bin; a.Q = Q; a.M = M; a.sa = sa; a.sb = sb; a.Aout = Aout; a.out = out;
+  a.B = B;
+  a.na = (Aout + ta - 1) / ta;
+  a.nt = rows ? (P + tn - 1) / tn : (P * Q + tn - 1) / tn;
+  a.nk = (int)((Bin + kMgBK - 1) / kMgBK);
+  a.vec = out != nullptr && ((uintptr_t)out & 15) == 0 && (rows ? (Aout & 3) == 0 : true);
+  if (!rows && !RESID && !a.vec) return pl;   // the cols stores are 16-byte
+  int occ;
+  if (rows) occ = mres ? mg_occ<true, true, false>(ta) : mg_occ<true, false, false>(ta);
+  else occ = mres ? mg_occ<false, true, RESID>(ta) : mg_occ<false, false, RESID>(ta);
+  const long long slots = (long long)mg_sms() * occ;
+  const long long per_a = std::max<long long>(1, std::min<long long>(a.nt, slots / a.na));
+  pl.grid = a.na * per_a;
+  if (pl.grid > 0x7fffffffLL) return pl;
+  pl.ok = true;
+  pl.rows = rows;
+  pl.mres = mres;
+  pl.ta = ta;
+  return pl;
+}
+
+template <bool RESID>
+cudaError_t mg_launch(const MgPlan& pl, cudaStream_t s) {
+  const unsigned g = (unsigned)pl.grid;
+  const bool t32 = pl.ta == 32;
+  if (pl.rows) {
+    if (pl.mres) t32 ? mg_run<true, true, false, 32>(pl.a, g, s) : mg_run<true, true, false, 64>(pl.a, g, s);
+    else t32 ? mg_run<true, false, false, 32>(pl.a, g, s) : mg_run<true, false, false, 64>(pl.a, g, s);
+  } else if (pl.mres) {
+    t32 ? mg_run<false, true, RESID, 32>(pl.a, g, s) : mg_run<false, true, RESID, 64>(pl.a, g, s);
+  } else {
+    t32 ? mg_run<false, false, RESID, 32>(pl.a, g, s) : mg_run<false, false, RESID, 64>(pl.a, g, s);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // Number of partial sums launch_mode_resid_gemm writes (0: view not covered).
-long long mode_resid_gemm_parts(long long P, long long Aout, long long Q) {
+long long mode_resid_gemm_parts(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                long long sa, long long sb, long long Aout, const float* B) {
+  MgPlan pl = mg_plan<true>(X, P, Bin, Q, M, sa, sb, Aout, nullptr, B);
+  if (pl.ok) return pl.grid;
   if (Q < 64 || P > 65535 || (Aout + 63) / 64 > 65535) return 0;
   return ((Q + 127) / 128) * ((Aout + 63) / 64) * P;
 }
@@ -228,7 +584,12 @@ long long mode_resid_gemm_parts(long long P, long long Aout, long long Q) {
 cudaError_t launch_mode_resid_gemm(const float* X, long long P, long long Bin, long long Q,
                                    const float* M, long long sa, long long sb, long long Aout,
                                    const float* B, double* part, cudaStream_t s) {
-  if (mode_resid_gemm_parts(P, Aout, Q) == 0) return cudaErrorNotSupported;
+  MgPlan pl = mg_plan<true>(X, P, Bin, Q, M, sa, sb, Aout, nullptr, B);
+  if (pl.ok) {
+    pl.a.part = part;
+    return mg_launch<true>(pl, s);
+  }
+  if (Q < 64 || P > 65535 || (Aout + 63) / 64 > 65535) return cudaErrorNotSupported;
   const long long gx = (Q + 127) / 128, gy = (Aout + 63) / 64;
   mode_resid_cols<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)P), kGThreads, 0, s>>>(X, Bin, Q, M, sa, sb,
                                                                                    Aout, B, part);
@@ -238,6 +599,10 @@ cudaError_t launch_mode_resid_gemm(const float* X, long long P, long long Bin, l
 cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,
                              long long sa, long long sb, long long Aout, float* out, cudaStream_t s) {
   if (P < 1 || Bin < 1 || Q < 1 || Aout < 1) return cudaErrorInvalidValue;
+  {
+    MgPlan pl = mg_plan<false>(X, P, Bin, Q, M, sa, sb, Aout, out);
+    if (pl.ok) return mg_launch<false>(pl, s);
+  }
   const int vec = ((uintptr_t)out & 15) == 0;   // 16-byte stores only from an aligned base
   if (Q >= 64) {
     const long long gx = (Q + 127) / 128, gy = (Aout + 63) / 64;
@@ -254,5 +619,146 @@ cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long lo
   }
   return cudaErrorNotSupported;
 }
+
+// ---------------------------------------------------------------------------
+// Any-view forms (FP32 and FP64): the fallback where the views above and the
+// sweep kernel's PROJECT / GIVEN passes do not apply (long modes in FP64,
+// unaligned FP32 views). Plain 32 x 32 shared-memory tiles; the column index
+// c = p * Q + q runs over the flattened P x Q positions.
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mode_gemm_any(const T* __restrict__ X, long long P, long long Bin, long long Q, const T* __restrict__ M,
+                  long long sa, long long sb, long long Aout, T* __restrict__ out) {
+  __shared__ T Ms[32][33];   // [k][a]
+  __shared__ T Xs[32][33];   // [k][c]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long c = (long long)blockIdx.x * 32 + tx, a0 = (long long)blockIdx.y * 32;
+  const bool cok = c < P * Q;
+  const long long p = cok ? c / Q : 0, q = cok ? c - p * Q : 0;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (long long k0 = 0; k0 < Bin; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const long long gk = k0 + r, ga = a0 + tx;
+      Xs[r][tx] = (cok && gk < Bin) ? X[(p * Bin + gk) * Q + q] : T(0);
+      Ms[r][tx] = (ga < Aout && gk < Bin) ? M[ga * sa + gk * sb] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const T x = Xs[k][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fma(Ms[k][ty + 8 * i], x, acc[i]);
+    }
+    __syncthreads();
+  }
+  if (!cok) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long ga = a0 + ty + 8 * i;
+    if (ga < Aout) out[(p * Aout + ga) * Q + q] = acc[i];
+  }
+}
+
+// part[s][i][r] = sum over columns j of split s of X[p, i, q] V[p, r, q]
+// (j = p * Q + q): the factor adjoint X_(n) V_(n)^T in column splits.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    factor_adjoint_any(const T* __restrict__ X, long long P, long long I, long long Q, const T* __restrict__ V,
+                       int R, long long jper, T* __restrict__ part) {
+  __shared__ T Xs[32][33];   // [j][i]
+  __shared__ T Vs[32][33];   // [j][r]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long i0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32;
+  const long long J = P * Q;
+  const long long jb = (long long)blockIdx.z * jper;
+  const long long je = jb + jper < J ? jb + jper : J;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (long long j0 = jb; j0 < je; j0 += 32) {
+    const long long j = j0 + tx;
+    const bool jok = j < je;
+    const long long p = jok ? j / Q : 0, q = jok ? j - p * Q : 0;
+    for (int rr = ty; rr < 32; rr += 8) {
+      const long long gi = i0 + rr, gr = r0 + rr;
+      Xs[tx][rr] = (jok && gi < I) ? X[(p * I + gi) * Q + q] : T(0);
+      Vs[tx][rr] = (jok && gr < R) ? V[(p * R + gr) * Q + q] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const T x = Xs[jj][tx];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[m] = fma(x, Vs[jj][ty + 8 * m], acc[m]);
+    }
+    __syncthreads();
+  }
+  const long long gi = i0 + tx;
+  if (gi >= I) return;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const long long gr = r0 + ty + 8 * m;
+    if (gr < R) part[((long long)blockIdx.z * I + gi) * R + gr] = acc[m];
+  }
+}
+
+// out[e] = sum_s part[s * n + e], s in order (deterministic).
+template <typename T>
+__global__ void sum_splits(const T* __restrict__ part, int S, long long n, T* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    T v = part[e];
+    for (int s = 1; s < S; ++s) v += part[(long long)s * n + e];
+    out[e] = v;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_mode_gemm_any(const T* X, long long P, long long Bin, long long Q, const T* M, long long sa,
+                                 long long sb, long long Aout, T* out, cudaStream_t s) {
+  if (P < 1 || Bin < 1 || Q < 1 || Aout < 1) return cudaErrorInvalidValue;
+  const long long gx = (P * Q + 31) / 32, gy = (Aout + 31) / 32;
+  if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorNotSupported;
+  mode_gemm_any<T><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(X, P, Bin, Q, M, sa, sb, Aout, out);
+  return cudaGetLastError();
+}
+
+int factor_adjoint_splits(long long P, long long I, long long Q, int R, int sms) {
+  const long long tiles = ((I + 31) / 32) * ((R + 31) / 32);
+  long long S = (4LL * sms + tiles - 1) / tiles;
+  const long long maxs = (P * Q + 1023) / 1024;   // at least 1024 columns per split
+  if (S > maxs) S = maxs;
+  if (S > 1024) S = 1024;
+  return (int)(S < 1 ? 1 : S);
+}
+
+template <typename T>
+cudaError_t launch_factor_adjoint_any(const T* X, long long P, long long I, long long Q, const T* V, int R,
+                                      int S, T* part, T* Ubar, cudaStream_t s) {
+  if (P < 1 || I < 1 || Q < 1 || R < 1 || S < 1) return cudaErrorInvalidValue;
+  const long long J = P * Q;
+  long long jper = (J + S - 1) / S;
+  jper = (jper + 31) / 32 * 32;
+  const long long gx = (I + 31) / 32, gy = (R + 31) / 32;
+  if (gx > 0x7fffffffLL || gy > 65535 || S > 65535) return cudaErrorNotSupported;
+  factor_adjoint_any<T><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)S), 256, 0, s>>>(X, P, I, Q, V, R, jper,
+                                                                                    part);
+  const long long n = I * R;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  sum_splits<T><<<(unsigned)blocks, 256, 0, s>>>(part, S, n, Ubar);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_mode_gemm_any<float>(const float*, long long, long long, long long, const float*,
+                                                 long long, long long, long long, float*, cudaStream_t);
+template cudaError_t launch_mode_gemm_any<double>(const double*, long long, long long, long long,
+                                                  const double*, long long, long long, long long, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_factor_adjoint_any<float>(const float*, long long, long long, long long,
+                                                      const float*, int, int, float*, float*, cudaStream_t);
+template cudaError_t launch_factor_adjoint_any<double>(const double*, long long, long long, long long,
+                                                       const double*, int, int, double*, double*,
+                                                       cudaStream_t);
 
 }  // namespace tals

@@ -624,7 +624,7 @@ cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const
                                  const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s) {
   // the tiled GEMM form where the view has long rows (Q >= 64)
-  const long long ng = mode_resid_gemm_parts(v.P, v.I, v.Q);
+  const long long ng = mode_resid_gemm_parts(W, v.P, R, v.Q, L, R, 1, v.I, X);
   if (ng > 0 && ng <= cap) {
     cudaError_t e = launch_mode_resid_gemm(W, v.P, R, v.Q, L, R, 1, v.I, X, part, s);
     if (e != cudaSuccess) return e;

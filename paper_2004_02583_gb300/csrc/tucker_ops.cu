@@ -65,7 +65,7 @@ size_t numel(const long long* d, int N) {
 tals_status apply_mode(OpCtx& o, const void* X, const long long* d, int n, const void* L,
                        int R_out, void* out) {
   ModeView v = view_of(d, o.N, n);
-  if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1)) {
+  if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1 || v.Q % 4 == 0)) {
     // register-tiled mode product: M = L^T, element (a, b) = L[b * R_out + a]
     cudaError_t e = launch_mode_gemm((const float*)X, v.P, v.I, v.Q, (const float*)L, 1, R_out, R_out,
                                      (float*)out, o.s);
@@ -73,8 +73,17 @@ tals_status apply_mode(OpCtx& o, const void* X, const long long* d, int n, const
     if (e != cudaErrorNotSupported) return cuda_fail(e, "mode product");
   }
   PassConfig pc = pass_config(o.dtype, v, R_out, o.sms);
-  if (!pc.ok) return fail(TALS_ENOTSUP, "mode product of mode %d (size %lld -> %d) exceeds the "
-                          "kernel limits", n, v.I, R_out);
+  if (!pc.ok) {
+    // any-view tiled product: M = L^T
+    cudaError_t e = o.dtype == TALS_F32
+                        ? launch_mode_gemm_any((const float*)X, v.P, v.I, v.Q, (const float*)L, 1, R_out, R_out,
+                                               (float*)out, o.s)
+                        : launch_mode_gemm_any((const double*)X, v.P, v.I, v.Q, (const double*)L, 1, R_out,
+                                               R_out, (double*)out, o.s);
+    if (e != cudaSuccess) return fail(TALS_ENOTSUP, "mode product of mode %d (size %lld -> %d): %s", n, v.I,
+                                      R_out, cudaGetErrorString(e));
+    return TALS_OK;
+  }
   cudaError_t e;
   double* sp = (double*)o.sc->get((size_t)pc.grid_x * pc.grid_y * sizeof(double), &e);
   if (e != cudaSuccess) return cuda_fail(e, "scratch");
@@ -113,7 +122,21 @@ tals_status factor_adjoint(OpCtx& o, const void* P, const long long* d, int n, c
   ModeView v = view_of(d, o.N, n);
   const int R = o.ranks[n];
   PassConfig pc = pass_config(o.dtype, v, R, o.sms);
-  if (!pc.ok) return fail(TALS_ENOTSUP, "factor adjoint of mode %d exceeds the kernel limits", n);
+  if (!pc.ok) {
+    // any-view form in column splits
+    const int S = factor_adjoint_splits(v.P, v.I, v.Q, R, o.sms);
+    cudaError_t e;
+    void* part = o.sc->get((size_t)S * v.I * R * o.esz, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    e = o.dtype == TALS_F32
+            ? launch_factor_adjoint_any((const float*)P, v.P, v.I, v.Q, (const float*)V, R, S, (float*)part,
+                                        (float*)Ubar, o.s)
+            : launch_factor_adjoint_any((const double*)P, v.P, v.I, v.Q, (const double*)V, R, S, (double*)part,
+                                        (double*)Ubar, o.s);
+    if (e != cudaSuccess) return fail(TALS_ENOTSUP, "factor adjoint of mode %d: %s", n, cudaGetErrorString(e));
+    o.sc->release(part);
+    return TALS_OK;
+  }
   RowPlan rp = row_plan(v.I, R, o.sms);
   cudaError_t e;
   void* yp = o.sc->get((size_t)pc.grid_x * v.I * R * o.esz, &e);
@@ -204,13 +227,45 @@ OpCtx make_ctx(int dtype, int ndim, const int64_t* dims, const int* ranks, void*
 }
 
 // Order in which a chain of mode products keeps intermediates smallest.
+// Order of the mode products of a projection (expand = false: I_m -> R_m from
+// the full tensor) or a reconstruction (expand = true: R_m -> I_m from the
+// core) with the fewest multiply-adds: a mode product costs (elements of the
+// larger of its input and output) x (the smaller of I_m, R_m), and the
+// minimum over all orders is found exactly by dynamic programming over the
+// subsets of modes already applied (N <= 8: at most 256 subsets). Ties keep
+// the lower mode first.
 std::vector<int> shrink_order(const OpCtx& o, bool expand) {
-  std::vector<int> ord(o.N);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-    const double ra = (double)o.ranks[a] / o.dims[a], rb = (double)o.ranks[b] / o.dims[b];
-    return expand ? ra > rb : ra < rb;
-  });
+  const int N = o.N;
+  const int full = (1 << N) - 1;
+  // elements of the tensor once the modes in `done` are applied
+  auto size_of = [&](int done) {
+    double v = 1.0;
+    for (int m = 0; m < N; ++m) {
+      const bool applied = (done >> m) & 1;
+      const double at_rank = (double)o.ranks[m], at_full = (double)o.dims[m];
+      v *= expand ? (applied ? at_full : at_rank) : (applied ? at_rank : at_full);
+    }
+    return v;
+  };
+  std::vector<double> best(full + 1, 1e300);
+  std::vector<int> last(full + 1, -1);
+  best[0] = 0.0;
+  for (int done = 1; done <= full; ++done)
+    for (int m = 0; m < N; ++m) {
+      if (!((done >> m) & 1)) continue;
+      const int prev = done & ~(1 << m);
+      const double big = expand ? size_of(done) : size_of(prev);
+      const double c = best[prev] + big * (double)std::min<long long>(o.ranks[m], o.dims[m]);
+      if (c < best[done] * (1.0 - 1e-12)) {
+        best[done] = c;
+        last[done] = m;
+      }
+    }
+  std::vector<int> ord(N);
+  for (int done = full, k = N - 1; k >= 0; --k) {
+    ord[k] = last[done];
+    done &= ~(1 << last[done]);
+  }
   return ord;
 }
 
@@ -254,7 +309,7 @@ tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
     {
       // register-tiled expansion with M = U_m (element (i, r) = U[i * R + r])
       ModeView v = view_of(d, o.N, m);
-      if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1)) {
+      if (o.dtype == TALS_F32 && (v.Q >= 64 || v.Q == 1 || v.Q % 4 == 0)) {
         void* dst = B_out;
         if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
         if (e != cudaSuccess) return cuda_fail(e, "scratch");

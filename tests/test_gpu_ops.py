@@ -33,7 +33,12 @@ def _t(x):
 
 
 CASES = [((23, 17, 40), (5, 4, 7)), ((12, 9, 8, 10), (3, 2, 4, 5)), ((64, 33, 70), (16, 8, 9)),
-         ((130, 20, 6), (40, 5, 6))]
+         ((130, 20, 6), (40, 5, 6)),
+         # pipelined mode products: staged contractions (B_in > 64) in both views,
+         # ragged a/p/q tails, resident expansions to a Q == 1 view with 100 columns
+         ((70, 36, 100), (12, 20, 8)),
+         # more tiles than CTAs: the persistent loop wraps (mode-1 view: 512 q-tiles)
+         ((100, 64, 1024), (12, 16, 8))]
 
 
 @pytest.mark.parametrize("dims,ranks", CASES)
