@@ -234,6 +234,16 @@ struct LaSmem {
   int* flag;
 };
 
+// Bytes of the small algebra's scratch (aliasing the pass buffers) and of the
+// buffers that live across passes.
+__host__ __device__ constexpr size_t la_scratch_bytes() {
+  return ((2 * (size_t)kBatchMaxI * kBatchMaxR + 4 * kBatchMaxR * kBatchMaxR + kBatchMaxR) * sizeof(double) + 16 +
+          15) / 16 * 16;
+}
+__host__ __device__ constexpr size_t la_live_bytes() {
+  return (size_t)kBatchMaxI * kBatchMaxR * (sizeof(double) + 2 * sizeof(float));
+}
+
 // Q = orthonormal basis of In by CholeskyQR (one round): L = In F^-T; the
 // FP32 copy Lt and the Gram of its stored values GL. Returns failure.
 __device__ int cta_cholqr(const double* In, LaSmem& m, int I, int R, double* Out) {
@@ -258,19 +268,22 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
         order[a] = order[c];
         order[c] = x;
       }
+  // The pass's buffers and the FP64 scratch of the small algebra (Y, Z, X, GL,
+  // work) are never live together: both start at offset 0. L, Lt and Yf cross
+  // the passes and sit above the larger of the two.
   LaSmem m;
-  unsigned char* la = smem + pass_bytes;
   const int IR = kBatchMaxI * kBatchMaxR;
-  m.Y = reinterpret_cast<double*>(la);
-  m.L = m.Y + IR;
-  m.Z = m.L + IR;
+  m.Y = reinterpret_cast<double*>(smem);
+  m.Z = m.Y + IR;
   m.X = m.Z + IR;
   m.GL = m.X + kBatchMaxR * kBatchMaxR;
-  m.Yf = reinterpret_cast<float*>(m.GL + kBatchMaxR * kBatchMaxR);
-  m.Lt = m.Yf + IR;
-  m.work = reinterpret_cast<double*>(m.Lt + IR);
+  m.work = m.GL + kBatchMaxR * kBatchMaxR;
   m.flag = reinterpret_cast<int*>(m.work + 2 * kBatchMaxR * kBatchMaxR + kBatchMaxR);
-  __shared__ double s_norm, s_sum;
+  unsigned char* live = smem + (pass_bytes > la_scratch_bytes() ? pass_bytes : la_scratch_bytes());
+  m.L = reinterpret_cast<double*>(live);
+  m.Yf = reinterpret_cast<float*>(m.L + IR);
+  m.Lt = m.Yf + IR;
+  __shared__ double s_norm;
   __shared__ int s_stop;
 
   float* scr = b.scratch + (size_t)blockIdx.x * 2 * b.scratch_elems;
@@ -303,6 +316,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
     a.mode = PASS_INIT;
     a.sketch_state = b.seed ^ ((uint64_t)n << 56);
     double nrm = pass_cta<float, RC, RPT, RW, kThreads, JT>(a, 0, 1, 0, smem, m.Yf);
+    __syncthreads();   // the scratch below overlays the pass's tiles
     if (threadIdx.x == 0) s_norm = nrm;
     __syncthreads();
     const double normM2 = s_norm;
@@ -322,6 +336,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
       a.L = m.Lt;
       a.Wout = (k >= 1 || k + 1 >= b.max_sweeps) ? dest : nullptr;
       const double rs = pass_cta<float, RC, RPT, RW, kThreads, JT>(a, 0, 1, 0, smem, m.Yf);
+      __syncthreads();   // the scratch below overlays the pass's tiles
       for (int e = threadIdx.x; e < I * Rn; e += blockDim.x) m.Y[e] = (double)m.Yf[e];
       // e_k and the Eq. 5.01 stop rule
       if (threadIdx.x == 0) {
@@ -370,7 +385,7 @@ __device__ void run_tensor(const BatchArgs& b, int t, unsigned char* smem, size_
 }
 
 template <int RC, int RPT, int RW, int JT>
-__global__ void __launch_bounds__(kThreads, 1) batched_kernel(BatchArgs b, size_t pass_bytes) {
+__global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchArgs b, size_t pass_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_t;
   while (true) {
@@ -408,10 +423,9 @@ size_t pass_region(const Variant& v) {
   return (b + 15) / 16 * 16;
 }
 
-size_t la_region() {
-  const size_t IR = (size_t)kBatchMaxI * kBatchMaxR;
-  return 3 * IR * sizeof(double) + 2 * kBatchMaxR * kBatchMaxR * sizeof(double) +
-         2 * IR * sizeof(float) + (2 * kBatchMaxR * kBatchMaxR + kBatchMaxR) * sizeof(double) + 16;
+// Dynamic shared memory of a variant: max(pass buffers, small-algebra scratch) + live buffers.
+size_t batch_smem(size_t pass_bytes) {
+  return std::max(pass_bytes, la_scratch_bytes()) + la_live_bytes();
 }
 
 struct Plan {
@@ -545,7 +559,7 @@ extern "C" tals_status tals_batched_st_hosvd(int count, void* const* A_ptrs, con
   auto launch = [&](int vi, int per_sm, cudaStream_t st) -> cudaError_t {
     const Variant& v = vs[vi];
     const size_t pr = pass_region(v);
-    const size_t smem = pr + la_region();
+    const size_t smem = batch_smem(pr);
     cudaError_t err = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int occ = 0;
