@@ -268,8 +268,12 @@ tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int 
                                  j.st, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
   // e_k, Eq. 5.01, and chol(X) if the sweep continues
+  // FP32 data: chol(X) in FP32 -- X^-1 only preconditions Z = Y X^-1 (span(Z) =
+  // span(Y) for any invertible factor, applied exactly in FP64 by the row
+  // solves); the factor of Z^T Z, which sets the orthonormality of Q, stays FP64
+  const int f32 = c->dtype == TALS_F32;
   TALS_CK(launch_small(c->Gfin, 1, R, test_op, c->F, j.st, c->norm_a2, j.cond, j.has_cond, s,
-                       c->GfinL));
+                       c->GfinL, f32));
   // L_{k+1} = Y X^{-1} (Alg. 3 L-update in the Q_k basis), then its Q factor
   TALS_CK(launch_row_solve(c->dtype, c->Y64, I, R, c->F, 1, c->Z64, nullptr, c->Gpart, j.rp, j.st, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));

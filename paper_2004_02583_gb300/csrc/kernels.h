@@ -72,9 +72,10 @@ cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
 //                sweep continues, F = chol(Gram).
 // When has_cond, thread 0 sets the CUDA graph conditional `cond` to 0 once the
 // mode is done (stop rule, sweep budget or failure), ending the device-side loop.
+// f32: factor in FP32 (a preconditioning factor; any pivot failure falls back to FP64).
 cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F,
                          ModeState* st, const double* norm_a2, unsigned long long cond,
-                         int has_cond, cudaStream_t s, const double* GL = nullptr);
+                         int has_cond, cudaStream_t s, const double* GL = nullptr, int f32 = 0);
 
 // Row-wise solves against the R x R lower factor F (FP64):
 //   op 0 (LT):  Out = In F^-T          (Q factor of CholeskyQR)

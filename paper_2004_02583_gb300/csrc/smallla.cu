@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
                                                               const double* norm_a2,
                                                               cudaGraphConditionalHandle cond,
                                                               int has_cond,
-                                                              const double* __restrict__ GL) {
+                                                              const double* __restrict__ GL,
+                                                              int f32) {
   if (st->done) {
     if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
@@ -248,6 +249,91 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     while (ip * (ip + 1) / 2 > a) --ip;
     while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
     tri[a] = (ip << 16) | (a - ip * (ip + 1) / 2);
+  }
+  if (f32) {
+    // The same LDL^T in FP32 (4-cycle latency instead of 64), for factors that
+    // only have to be invertible and well scaled -- chol(X) of the L-update on
+    // FP32 data: the row solves apply it exactly in FP64, so Y X^-1 keeps the
+    // span of Y, and the basis rotates by O(eps32 cond(X)) at most. A pivot
+    // that fails in FP32 falls back to the FP64 factorization below.
+    float* S32 = reinterpret_cast<float*>(S);   // the FP64 array's storage
+    __shared__ float Lc32[2][kMaxR];
+    __shared__ float rs32[kMaxR];
+    __shared__ int tiny32, fail32;
+    for (int o = tid; o < R * R; o += kSmallThreads) {
+      const int r = o / R, c = o % R;
+      if (c <= r) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nb; ++q) {
+          a += Gpart[(size_t)q * R * R + r * R + c];
+          b += Gpart[(size_t)q * R * R + c * R + r];
+        }
+        S32[r * R + c] = (float)(0.5 * (a + b));
+      }
+    }
+    if (tid == 0) fail32 = 0;
+    __syncthreads();
+    if (tid < 32) {
+      float dmax = 0.f;
+      for (int r = tid; r < R; r += 32) dmax = fmaxf(dmax, S32[r * R + r]);
+      for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      if (tid == 0) tiny32 = __float_as_int(64.f * 1.1920929e-7f * dmax);
+    }
+    __syncthreads();
+    const int lane32 = tid & 31, warp32 = tid >> 5;
+    auto ok32 = [&](float d) {
+      const int b = __float_as_int(d);
+      return b > tiny32 && ((b >> 23) & 0xff) != 0xff;
+    };
+    if (warp32 == 0) {
+      const float d = S32[0];
+      if (lane32 == 0 && !ok32(d)) fail32 = 1;
+      const float dinv = __frcp_rn(d);
+      for (int j = 1 + lane32; j < R; j += 32) Lc32[0][j] = S32[j * R] * dinv;
+    }
+    __syncthreads();
+    for (int k = 0; k + 1 < R; ++k) {
+      const int cb = k & 1, c1 = k + 1;
+      if (warp32 == 0) {
+        const float lk = Lc32[cb][c1];
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = c1 + lane32 + 32 * h;
+          v[h] = i < R ? fmaf(-S32[i * R + k], lk, S32[i * R + c1]) : 0.f;
+        }
+        const float d = __shfl_sync(0xffffffffu, v[0], 0);
+        if (lane32 == 0 && !ok32(d)) fail32 = 1;
+        const float dinv = __frcp_rn(d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = c1 + lane32 + 32 * h;
+          if (i < R) {
+            S32[i * R + c1] = v[h];
+            if (i > c1) Lc32[cb ^ 1][i] = v[h] * dinv;
+          }
+        }
+      } else {
+        const int m = R - 2 - k;
+        const int na = m * (m + 1) / 2;
+        for (int a = tid - 32; a < na; a += kSmallThreads - 32) {
+          const int ij = tri[a];
+          const int i = k + 2 + (ij >> 16), j = k + 2 + (ij & 0xffff);
+          S32[i * R + j] = fmaf(-S32[i * R + k], Lc32[cb][j], S32[i * R + j]);
+        }
+      }
+      __syncthreads();
+    }
+    if (!fail32) {
+      for (int r = tid; r < R; r += kSmallThreads) rs32[r] = rsqrtf(S32[r * R + r]);
+      __syncthreads();
+      for (int o = tid; o < R * R; o += kSmallThreads) {
+        const int r = o / R, c = o % R;
+        F[o] = c <= r ? (double)(S32[o] * rs32[c]) : 0.0;
+      }
+      return;
+    }
+    __syncthreads();   // every thread is past its last read of S32 before the FP64 reload
   }
   for (int o = tid; o < R * R; o += kSmallThreads) {
     const int r = o / R, c = o % R;
@@ -346,10 +432,10 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
 
 cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F, ModeState* st,
                          const double* norm_a2, unsigned long long cond, int has_cond,
-                         cudaStream_t s, const double* GL) {
+                         cudaStream_t s, const double* GL, int f32) {
   if (R > kMaxR) return cudaErrorInvalidValue;
   small_kernel<<<1, kSmallThreads, 0, s>>>(Gpart, nb, R, op, F, st, norm_a2,
-                                            (cudaGraphConditionalHandle)cond, has_cond, GL);
+                                            (cudaGraphConditionalHandle)cond, has_cond, GL, f32);
   return cudaGetLastError();
 }
 
