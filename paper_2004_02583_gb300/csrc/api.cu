@@ -145,8 +145,8 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
   TALS_AL(c->GpartL, need.gpart * sizeof(double));
   int rmax = 1;
   for (int m = 0; m < N; ++m) rmax = std::max(rmax, c->ranks[m]);
-  TALS_AL(c->Gfin, (size_t)rmax * rmax * sizeof(double));
-  TALS_AL(c->F, (size_t)rmax * rmax * sizeof(double));
+  TALS_AL(c->Gfin, (size_t)rmax * rmax * (sizeof(double) + sizeof(float)));   // + FP32 copy
+  TALS_AL(c->F, ((size_t)3 * rmax * rmax + rmax) * sizeof(double));   // [C | Ff | Fb | dinv]
   TALS_AL(c->GfinL, (size_t)rmax * rmax * sizeof(double));
   TALS_AL(c->Y64, need.ir * sizeof(double));
   TALS_AL(c->L64, need.ir * sizeof(double));
@@ -266,7 +266,7 @@ tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int 
     TALS_CK(launch_mode_residual((const float*)j.X, j.v, R, (const float*)j.Wdest,
                                  (const float*)c->Lt, (double*)c->Ypart, (long long)(c->ypart_elems / 2),
                                  j.st, s));
-  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
+  TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s, c->dtype == TALS_F32));
   // e_k, Eq. 5.01, and chol(X) if the sweep continues
   // FP32 data: chol(X) in FP32 -- X^-1 only preconditions Z = Y X^-1 (span(Z) =
   // span(Y) for any invertible factor, applied exactly in FP64 by the row

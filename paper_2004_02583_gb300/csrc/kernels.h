@@ -63,8 +63,9 @@ cudaError_t launch_transpose(int dtype, const void* In, long long rows, long lon
                              cudaStream_t s);
 
 // Gfin[o] = sum_b Gpart[b][o] over nb partials of R x R (deterministic order).
+// write32: also an FP32 copy of the R x R result right after it (Gfin + R*R, as floats).
 cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
-                            const ModeState* st, cudaStream_t s);
+                            const ModeState* st, cudaStream_t s, int write32 = 0);
 
 // Single-CTA FP64 kernel: sums nb Gram partials, then
 //   op 0 (QR):   lower Cholesky factor F of the Gram (fails -> ESINGULAR)
@@ -77,6 +78,9 @@ cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F,
                          ModeState* st, const double* norm_a2, unsigned long long cond,
                          int has_cond, cudaStream_t s, const double* GL = nullptr, int f32 = 0);
 
+// F (small kernel output, 3 R^2 + R doubles): the lower Cholesky factor C, then
+// its copies with rows scaled by 1 / C[r][r] and with columns scaled by
+// 1 / C[c][c], then the R values 1 / C[r][r]. The row solves read the last three.
 // Row-wise solves against the R x R lower factor F (FP64):
 //   op 0 (LT):  Out = In F^-T          (Q factor of CholeskyQR)
 //   op 1 (SPD): Out = In (F F^T)^-1

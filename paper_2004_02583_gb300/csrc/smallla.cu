@@ -163,12 +163,26 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
                                                               int has_cond,
                                                               const double* __restrict__ GL,
                                                               int f32) {
+  const int tid = threadIdx.x;
+  // R <= 32, FP32 factor: warp 0 factors in registers (row `lane` of the
+  // symmetrised Gram per lane, identity beyond R). Its row is loaded here, in
+  // the same round trip as the done flag.
+  const bool reg32 = f32 && R <= 32 && nb == 1;
+  float srow[32];
+  if (reg32 && tid < 32) {
+    const float* G32 = reinterpret_cast<const float*>(Gpart + R * R);   // FP32 copy (gram_sum)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const bool in = tid < R && j < R;
+      const float a = in ? G32[tid * R + j] : 0.f, b = in ? G32[j * R + tid] : 0.f;
+      srow[j] = in ? 0.5f * (a + b) : (tid == j ? 1.f : 0.f);
+    }
+  }
   if (st->done) {
     if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
   __shared__ int fail;
-  const int tid = threadIdx.x;
 
   if (op == 1 || op == 2) {
     // Eq. 5.01 on e_k^2 = ||B_(n)||^2 - ||W||^2 (W = B^T Q_k is the LS optimum for Q_k),
@@ -250,7 +264,66 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     while ((ip + 1) * (ip + 2) / 2 <= a) ++ip;
     tri[a] = (ip << 16) | (a - ip * (ip + 1) / 2);
   }
-  if (f32) {
+  if (reg32) {
+    // LDL^T in FP32 registers, one warp, no block barriers: at step k lane i
+    // holds row i of S_k; the pivot d_k comes from lane k and every S_k[j][k]
+    // from lane j by shuffle. The full symmetric matrix is carried (each lane
+    // updates its whole row), so no transposes are needed.
+    __shared__ int bad_r;
+    if (tid < 32) {
+      const int lane = tid;
+      float dl = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) dl = j == lane ? srow[j] : dl;
+      float dmax = lane < R ? dl : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      const int tiny = __float_as_int(64.f * 1.1920929e-7f * dmax);
+      int bad = 0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float d = __shfl_sync(0xffffffffu, srow[k], k);
+        const int b = __float_as_int(d);
+        bad |= (k < R) && !(b > tiny && ((b >> 23) & 0xff) != 0xff);
+        const float l = srow[k] * __frcp_rn(d);
+#pragma unroll
+        for (int j = k + 1; j < 32; ++j) srow[j] = fmaf(-l, __shfl_sync(0xffffffffu, srow[k], j), srow[j]);
+      }
+      if (!bad) {
+        // C = L D^{1/2}: C[i][j] = S_j[i][j] / sqrt(d_j), staged in FP32
+        float* C32 = reinterpret_cast<float*>(S);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dl = j == lane ? srow[j] : dl;
+        const float rsl = rsqrtf(dl);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float rsj = __shfl_sync(0xffffffffu, rsl, j);
+          const float c = j < lane ? srow[j] * rsj : (j == lane ? dl * rsl : 0.f);
+          if (lane < R && j < R) C32[lane * R + j] = c;
+        }
+      }
+      if (lane == 0) bad_r = bad;
+    }
+    __syncthreads();
+    if (!bad_r) {
+      // the FP64 factor block, spread over all warps (each FP64 warp instruction
+      // holds an SMSP's FP64 pipe ~76 cycles: one warp alone would take ~4x longer)
+      const float* C32 = reinterpret_cast<const float*>(S);
+      __shared__ double dinv_r[32];
+      if (tid < R) dinv_r[tid] = 1.0 / (double)C32[tid * R + tid];
+      __syncthreads();
+      for (int o = tid; o < R * R; o += kSmallThreads) {
+        const int r = o / R, c = o % R;
+        const double cv = (double)C32[o];
+        F[o] = cv;
+        F[R * R + o] = cv * dinv_r[r];
+        F[2 * R * R + o] = cv * dinv_r[c];
+      }
+      if (tid < R) F[3 * R * R + tid] = dinv_r[tid];
+      return;
+    }
+    // a pivot failed in FP32: the FP64 factorization below
+  } else if (f32) {
     // The same LDL^T in FP32 (4-cycle latency instead of 64), for factors that
     // only have to be invertible and well scaled -- chol(X) of the L-update on
     // FP32 data: the row solves apply it exactly in FP64, so Y X^-1 keeps the
@@ -325,12 +398,20 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       __syncthreads();
     }
     if (!fail32) {
-      for (int r = tid; r < R; r += kSmallThreads) rs32[r] = rsqrtf(S32[r * R + r]);
+      __shared__ double dinv32[kMaxR];
+      for (int r = tid; r < R; r += kSmallThreads) {
+        rs32[r] = rsqrtf(S32[r * R + r]);
+        dinv32[r] = 1.0 / (double)(S32[r * R + r] * rs32[r]);
+      }
       __syncthreads();
       for (int o = tid; o < R * R; o += kSmallThreads) {
         const int r = o / R, c = o % R;
-        F[o] = c <= r ? (double)(S32[o] * rs32[c]) : 0.0;
+        const double cv = c <= r ? (double)(S32[o] * rs32[c]) : 0.0;
+        F[o] = cv;
+        F[R * R + o] = cv * dinv32[r];
+        F[2 * R * R + o] = cv * dinv32[c];
       }
+      for (int r = tid; r < R; r += kSmallThreads) F[3 * R * R + r] = dinv32[r];
       return;
     }
     __syncthreads();   // every thread is past its last read of S32 before the FP64 reload
@@ -416,12 +497,20 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     }
     __syncthreads();
   }
-  for (int r = tid; r < R; r += kSmallThreads) rs[r] = rsqrt(S[r * R + r]);
+  __shared__ double dinv64[kMaxR];
+  for (int r = tid; r < R; r += kSmallThreads) {
+    rs[r] = rsqrt(S[r * R + r]);
+    dinv64[r] = 1.0 / (S[r * R + r] * rs[r]);
+  }
   __syncthreads();
   for (int o = tid; o < R * R; o += kSmallThreads) {
     const int r = o / R, c = o % R;
-    F[o] = c <= r ? S[o] * rs[c] : 0.0;   // C[r][c]; sqrt(d_c) on the diagonal
+    const double cv = c <= r ? S[o] * rs[c] : 0.0;   // C[r][c]; sqrt(d_c) on the diagonal
+    F[o] = cv;
+    F[R * R + o] = cv * dinv64[r];       // forward-solve copy, rows scaled by 1 / C[r][r]
+    F[2 * R * R + o] = cv * dinv64[c];   // backward-solve copy, columns scaled by 1 / C[c][c]
   }
+  for (int r = tid; r < R; r += kSmallThreads) F[3 * R * R + r] = dinv64[r];
   if (tid == 0 && fail) {
     st->status = 4;   // TALS_ESINGULAR: Gram not numerically SPD (Remark 3)
     st->fail_stage = op == 1 ? 1 : 2;
@@ -451,21 +540,30 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
                                  const double* __restrict__ F, int op, double* __restrict__ Out,
                                  T* __restrict__ OutT, double* __restrict__ Gpart,
                                  int rows_per_block, const ModeState* st, int gram_rounded) {
-  if (st != nullptr && st->done) return;
+  const int done = st != nullptr ? st->done : 0;   // read in the same round trip as the factor
   extern __shared__ double sh[];
   double* Ff = sh;                                   // [R][R] F[j][c] / F[j][j]  (forward)
   double* Fb = Ff + (size_t)R * R;                   // [R][R] F[c][j] / F[j][j]  (backward)
   double* dinv = Fb + (size_t)R * R;                 // [R]
   double* Os = dinv + R;                             // [rows_per_block][R]
-  for (int r = threadIdx.x; r < R; r += blockDim.x) dinv[r] = 1.0 / F[r * R + r];
-  __syncthreads();
-  for (int o = threadIdx.x; o < R * R; o += blockDim.x) {
-    const int r = o / R, c = o % R;
-    const double f = F[o];
-    Ff[o] = f * dinv[r];
-    Fb[o] = f * dinv[c];
+  // the factor block [C | Ff | Fb | dinv] written by the small kernel: Ff, Fb
+  // and dinv are contiguous, copied as one array
+  {
+    const double* src = F + (size_t)R * R;
+    const int n = 2 * R * R + R;
+    int o = threadIdx.x;
+    for (; o + 3 * (int)blockDim.x < n; o += 4 * blockDim.x) {
+      const double v0 = src[o], v1 = src[o + blockDim.x], v2 = src[o + 2 * blockDim.x],
+                   v3 = src[o + 3 * blockDim.x];
+      sh[o] = v0;
+      sh[o + blockDim.x] = v1;
+      sh[o + 2 * blockDim.x] = v2;
+      sh[o + 3 * blockDim.x] = v3;
+    }
+    for (; o < n; o += blockDim.x) sh[o] = src[o];
   }
   __syncthreads();
+  if (done) return;
   const long long row0 = (long long)blockIdx.x * rows_per_block;
   const int nrows = (int)min((long long)rows_per_block, I - row0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -569,7 +667,7 @@ cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, co
 // Deterministic multi-CTA sum of Gram partials: Gfin[o] = sum_b Gpart[b][o].
 // ---------------------------------------------------------------------------
 __global__ void gram_sum_kernel(const double* __restrict__ Gpart, int nb, int RR,
-                                double* __restrict__ Gfin, const ModeState* st) {
+                                double* __restrict__ Gfin, const ModeState* st, int write32) {
   if (st != nullptr && st->done) return;
   __shared__ double part[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;   // 8 groups x 32 entries
@@ -584,13 +682,14 @@ __global__ void gram_sum_kernel(const double* __restrict__ Gpart, int nb, int RR
 #pragma unroll
     for (int g = 0; g < 8; ++g) t += part[g][lane];
     Gfin[o] = t;
+    if (write32) reinterpret_cast<float*>(Gfin + RR)[o] = (float)t;   // FP32 copy after the matrix
   }
 }
 
 cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
-                            const ModeState* st, cudaStream_t s) {
+                            const ModeState* st, cudaStream_t s, int write32) {
   const int RR = R * R;
-  gram_sum_kernel<<<(RR + 31) / 32, 256, 0, s>>>(Gpart, nb, RR, Gfin, st);
+  gram_sum_kernel<<<(RR + 31) / 32, 256, 0, s>>>(Gpart, nb, RR, Gfin, st, write32);
   return cudaGetLastError();
 }
 
