@@ -77,6 +77,21 @@ __device__ __forceinline__ double fast_rcp64(double d) {
   return fma(x0, e2, x0);
 }
 
+// As fast_rcp64 with one Newton step instead of the third-order one: relative
+// error below 2^-46 from the 24-bit seed, one dependent FP64 instruction less.
+__device__ __forceinline__ double fast_rcp64_newton(double d) {
+  const int hi = __double2hiint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  if (ex < -120 || ex > 120) return 1.0 / d;   // callers pass d > 0
+  const unsigned lo = (unsigned)__double2loint(d);
+  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
+  const float rf = __frcp_rn(f);
+  const int rb = __float_as_int(rf);
+  const int rex = ((rb >> 23) & 0xff) - 127;
+  const double x0 = __hiloint2double(((rex + 1023) << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+  return fma(x0, fma(-d, x0, 1.0), x0);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

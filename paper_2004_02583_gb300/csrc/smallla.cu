@@ -457,11 +457,14 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     if (warp == 0) {
       // column k+1: S[i][k+1] -= S[i][k] L_{k+1}, i >= k+1
       const double lk = Lc[cb][c1];
+      // the second row of each lane only exists for R > 32 (a uniform branch:
+      // a predicated-off FP64 instruction would still hold the pipe)
       double v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = c1 + lane + 32 * h;
-        v[h] = i < R ? fma(-S[i * R + k], lk, S[i * R + c1]) : 0.0;
+      v[0] = c1 + lane < R ? fma(-S[(c1 + lane) * R + k], lk, S[(c1 + lane) * R + c1]) : 0.0;
+      v[1] = 0.0;
+      if (R > 32) {
+        const int i = c1 + lane + 32;
+        v[1] = i < R ? fma(-S[i * R + k], lk, S[i * R + c1]) : 0.0;
       }
       // every lane takes the pivot's reciprocal (one warp instruction either
       // way; no divergent branch and no shuffle after it)
@@ -473,9 +476,10 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
           fail = 1;
         }
       }
-      const double dinv = fast_rcp64(d);
+      const double dinv = fast_rcp64_newton(d);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
+        if (h == 1 && R <= 32) break;
         const int i = c1 + lane + 32 * h;
         if (i < R) {
           S[i * R + c1] = v[h];
