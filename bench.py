@@ -667,8 +667,24 @@ def run_c5(args):
     import workloads as W
     from oracle import tucker_oracle as O
     cfg = W.CONFIGS["d1024_f32"]
-    p = W.make(cfg)
+    if args.dims:   # profiling: the same recipe at other sizes
+        p = W.planted(cfg.seed, tuple(int(x) for x in args.dims.split(",")), cfg.ranks, cfg.core,
+                      cfg.noise_rel, dtype=np.float32)
+    else:
+        p = W.make(cfg)
     A = torch.from_numpy(p.A).cuda()
+    if args.profile_pass:
+        # only the Tucker mode products (two projections, two reconstructions), for an ncu capture
+        rng = np.random.default_rng(0)
+        Uq = [torch.from_numpy(np.linalg.qr(rng.standard_normal((d, r)))[0].astype(np.float32)).cuda()
+              for d, r in zip(p.A.shape, cfg.ranks)]
+        G = tals.project(A, Uq)
+        tals.project(A, Uq)
+        tals.reconstruct(G, Uq)
+        tals.reconstruct(G, Uq)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_mode_products": list(p.A.shape)}))
+        return
     peaks, _ = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     clocks = Clocks(0)
