@@ -144,6 +144,23 @@ tals_status t_hosvd(tals_ctx* ctx, void* G_out, void* const* U_out, tals_stats* 
 tals_status st_hosvd_host(tals_ctx* ctx, const void* A_host, void* G_host,
                           void* const* U_host, tals_stats* st);
 
+/* st_hosvd_host over `count` tensors, pipelined: while tensor t is decomposed on
+ * the context's stream, tensor t+1 is copied to a second device buffer on an
+ * upload stream, so the host-to-device copies overlap the decompositions. Every
+ * tensor is copied in full and every result copied back, in order.
+ * A_host[t]: host tensor t (dims of the context; pinned memory for the copy to
+ * run asynchronously); G_host[t]: host core; U_host: NULL or count*N host
+ * factor pointers (U_host[t*N + n], I_n x R_n, any entry may be NULL); stats:
+ * NULL or `count` entries. The caller owns every host buffer and keeps them
+ * alive until the call returns (it returns after the last result is on the
+ * host). Context: from tucker_als_init_owned; the first call allocates a second
+ * tensor buffer and per-slot outputs (freed by tals_destroy). Without CUDA
+ * graphs (opts.use_graph = 0) the tensors run one after another as
+ * st_hosvd_host. Errors: TALS_EINVAL for NULL arguments or count < 1; the
+ * first failing tensor's status otherwise (later tensors are not run). */
+tals_status st_hosvd_host_many(tals_ctx* ctx, int count, const void* const* A_host,
+                               void* const* G_host, void* const* U_host, tals_stats* stats);
+
 /* Like tucker_als_init but the context allocates and owns a device buffer for A
  * (to be filled by st_hosvd_host or by copying into tals_ctx_tensor()). */
 tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int64_t* dims,

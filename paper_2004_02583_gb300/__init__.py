@@ -72,6 +72,8 @@ SIGNATURES = {
     "st_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
     "t_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
     "st_hosvd_host": (ctypes.c_int, [_VP, _VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
+    "st_hosvd_host_many": (ctypes.c_int, [_VP, ctypes.c_int, _VPP, _VPP, _VPP,
+                                          ctypes.POINTER(tals_stats)]),
     "reconstruct": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
     "project": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
     "reconstruct_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P,
@@ -302,6 +304,22 @@ class HostContext:
         _check(lib().st_hosvd_host(self._h, A_host.data_ptr(), G_host.data_ptr(),
                                    _ptrs(U_host), ctypes.byref(st)))
         return st.to_dict(self.ndim)
+
+    def st_hosvd_many(self, A_hosts, G_hosts, U_hosts=None):
+        """Pipelined st_hosvd over lists of host tensors: the upload of tensor t+1
+        overlaps the decomposition of tensor t. U_hosts: None or one list of N
+        factor tensors per input. Returns the per-tensor statistics."""
+        n = len(A_hosts)
+        if len(G_hosts) != n or (U_hosts is not None and len(U_hosts) != n):
+            raise ValueError("one core (and factor list) per input tensor")
+        A = (ctypes.c_void_p * n)(*[a.data_ptr() for a in A_hosts])
+        G = (ctypes.c_void_p * n)(*[g.data_ptr() for g in G_hosts])
+        U = None
+        if U_hosts is not None:
+            U = (ctypes.c_void_p * (n * self.ndim))(*[u.data_ptr() for us in U_hosts for u in us])
+        st = (tals_stats * n)()
+        _check(lib().st_hosvd_host_many(self._h, n, A, G, U, st))
+        return [st[i].to_dict(self.ndim) for i in range(n)]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

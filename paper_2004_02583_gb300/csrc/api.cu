@@ -455,11 +455,21 @@ void tals_destroy(tals_ctx* c) {
   cudaStream_t s = c->stream;
   graphs_destroy(c);
   mixed_free(c);
+  if (c->upload) cudaStreamSynchronize(c->upload);
   void* bufs[] = {c->GpartL, c->GfinL, c->tbuf[0], c->tbuf[1], c->Ypart, c->spart, c->Gpart, c->Gfin, c->F,
-                  c->Y64,     c->L64,     c->Z64,   c->Lt,    c->st,    c->norm_a2, c->A_owned};
+                  c->Y64,     c->L64,     c->Z64,   c->Lt,    c->st,    c->norm_a2, c->A_owned,
+                  c->A_owned2, c->hostio_G, c->pipe_G[0], c->pipe_G[1]};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, s);
+  for (int m = 0; m < TALS_MAX_NDIM; ++m)
+    for (void* p : {c->hostio_U[m], c->pipe_U[0][m], c->pipe_U[1][m]})
+      if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_loaded[i]) cudaEventDestroy(c->ev_loaded[i]);
+    if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+  }
+  if (c->upload) cudaStreamDestroy(c->upload);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->host_d) cudaFreeHost(c->host_d);
   delete c;
@@ -618,6 +628,93 @@ tals_status st_hosvd_host(tals_ctx* c, const void* A_host, void* G_host, void* c
                           cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? TALS_OK : cuda_fail(e, "result download");
+}
+
+tals_status st_hosvd_host_many(tals_ctx* c, int count, const void* const* A_host,
+                               void* const* G_host, void* const* U_host, tals_stats* stats) {
+  if (!c || count < 1 || !A_host || !G_host) return fail(TALS_EINVAL, "NULL argument or count < 1");
+  if (!c->A_owned) return fail(TALS_EINVAL, "st_hosvd_host_many needs a context from tucker_als_init_owned");
+  const int N = c->N;
+  for (int t = 0; t < count; ++t)
+    if (!A_host[t] || !G_host[t]) return fail(TALS_EINVAL, "NULL host buffer for tensor %d", t);
+  if (!c->opts.use_graph) {
+    // the host-driven loop waits inside every decomposition: nothing to overlap
+    for (int t = 0; t < count; ++t) {
+      tals_status st = st_hosvd_host(c, A_host[t], G_host[t], U_host ? U_host + (size_t)t * N : nullptr,
+                                     stats ? stats + t : nullptr);
+      if (st != TALS_OK) return st;
+    }
+    return TALS_OK;
+  }
+  size_t nA = 1, nG = 1;
+  for (int m = 0; m < N; ++m) {
+    nA *= (size_t)c->dims[m];
+    nG *= (size_t)c->ranks[m];
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->A_owned2 && (e = cudaMallocAsync(&c->A_owned2, nA * c->esz, c->stream)) != cudaSuccess)
+    return cuda_fail(e, "second tensor buffer");
+  if (!c->upload) {
+    if ((e = cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "upload stream");
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&c->ev_loaded[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline events");
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!c->pipe_G[i]) {
+      if ((e = cudaMallocAsync(&c->pipe_G[i], nG * c->esz, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "core buffer");
+      for (int m = 0; m < N; ++m)
+        if ((e = cudaMallocAsync(&c->pipe_U[i][m], (size_t)c->dims[m] * c->ranks[m] * c->esz,
+                                 c->stream)) != cudaSuccess)
+          return cuda_fail(e, "factor buffer");
+    }
+  void* bufs[2] = {c->A_owned, c->A_owned2};
+  // uploads wait for everything already queued on the context's stream
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(c->ev_free[i], c->stream);
+  auto upload = [&](int t, int slot) {
+    cudaError_t u = cudaStreamWaitEvent(c->upload, c->ev_free[slot], 0);
+    if (u == cudaSuccess)
+      u = cudaMemcpyAsync(bufs[slot], A_host[t], nA * c->esz, cudaMemcpyHostToDevice, c->upload);
+    if (u == cudaSuccess) u = cudaEventRecord(c->ev_loaded[slot], c->upload);
+    return u;
+  };
+  if (e == cudaSuccess) e = upload(0, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor upload");
+  tals_status result = TALS_OK;
+  for (int t = 0; t < count && result == TALS_OK; ++t) {
+    const int slot = t & 1;
+    // tensor t+1 crosses the link while tensor t is decomposed
+    if (t + 1 < count && (e = upload(t + 1, slot ^ 1)) != cudaSuccess) {
+      result = cuda_fail(e, "tensor upload");
+      break;
+    }
+    if ((e = cudaStreamWaitEvent(c->stream, c->ev_loaded[slot], 0)) != cudaSuccess) {
+      result = cuda_fail(e, "upload wait");
+      break;
+    }
+    c->A = bufs[slot];
+    if ((result = st_hosvd_graph_launch(c, c->pipe_G[slot], c->pipe_U[slot])) != TALS_OK) break;
+    e = cudaEventRecord(c->ev_free[slot], c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(G_host[t], c->pipe_G[slot], nG * c->esz, cudaMemcpyDeviceToHost, c->stream);
+    for (int m = 0; m < N && e == cudaSuccess; ++m)
+      if (U_host && U_host[(size_t)t * N + m])
+        e = cudaMemcpyAsync(U_host[(size_t)t * N + m], c->pipe_U[slot][m],
+                            (size_t)c->dims[m] * c->ranks[m] * c->esz, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      result = cuda_fail(e, "result download");
+      break;
+    }
+    result = st_hosvd_graph_collect(c, c->pipe_G[slot], c->pipe_U[slot], stats ? stats + t : nullptr);
+  }
+  c->A = c->A_owned;
+  cudaStreamSynchronize(c->upload);   // no upload left in flight into a buffer reused later
+  return result;
 }
 
 tals_status als_mode_sweep(tals_ctx* c, int mode, int max_iters, double* err_out,

@@ -18,6 +18,7 @@ namespace tals {
 
 struct GraphEntry {
   int kind = 0;                       // 0 st-HOSVD, 1 t-HOSVD
+  const void* A = nullptr;            // the input tensor the graph reads
   void* G = nullptr;
   void* U[TALS_MAX_NDIM] = {};
   cudaGraphExec_t exec = nullptr;
@@ -112,7 +113,7 @@ tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) 
 
 GraphEntry* find(tals_ctx* c, int kind, void* G, void* const* U) {
   for (auto& en : c->graphs->entries) {
-    if (en.kind != kind || en.G != G) continue;
+    if (en.kind != kind || en.G != G || en.A != c->A) continue;
     bool same = true;
     for (int n = 0; n < c->N; ++n)
       if (en.U[n] != (U ? U[n] : nullptr)) same = false;
@@ -193,11 +194,13 @@ tals_status build(tals_ctx* c, int kind, void* G_out, void* const* U_out, GraphE
   if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
   out->kind = kind;
   out->G = G_out;
+  out->A = c->A;
   for (int n = 0; n < N; ++n) out->U[n] = U_out ? U_out[n] : nullptr;
   return TALS_OK;
 }
 
-tals_status run(tals_ctx* c, int kind, void* G_out, void* const* U_out, tals_stats* stats) {
+// The cached graph for (kind, c->A, G, U), built on first use.
+tals_status entry(tals_ctx* c, int kind, void* G_out, void* const* U_out, GraphEntry** out) {
   tals_status st = ensure_streams(c);
   if (st != TALS_OK) return st;
   GraphEntry* en = find(c, kind, G_out, U_out);
@@ -207,9 +210,15 @@ tals_status run(tals_ctx* c, int kind, void* G_out, void* const* U_out, tals_sta
     c->graphs->entries.push_back(fresh);
     en = &c->graphs->entries.back();
   }
-  cudaError_t e = cudaGraphLaunch(en->exec, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  *out = en;
+  return TALS_OK;
+}
+
+// Status and statistics of the last decomposition launched on c->stream, once
+// the stream has been synchronized (the graph's last nodes copy them to pinned
+// host memory).
+tals_status collect(tals_ctx* c, int kind, const GraphEntry* en, tals_stats* stats) {
+  tals_status st;
   if ((st = mixed_check(c)) != TALS_OK) return st;
   // statistics from the pinned copies written by the graph's last nodes
   tals_stats local;
@@ -245,7 +254,31 @@ tals_status run(tals_ctx* c, int kind, void* G_out, void* const* U_out, tals_sta
   return TALS_OK;
 }
 
+tals_status run(tals_ctx* c, int kind, void* G_out, void* const* U_out, tals_stats* stats) {
+  GraphEntry* en = nullptr;
+  tals_status st = entry(c, kind, G_out, U_out, &en);
+  if (st != TALS_OK) return st;
+  cudaError_t e = cudaGraphLaunch(en->exec, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return collect(c, kind, en, stats);
+}
+
 }  // namespace
+
+tals_status st_hosvd_graph_launch(tals_ctx* c, void* G_out, void* const* U_out) {
+  GraphEntry* en = nullptr;
+  tals_status st = entry(c, 0, G_out, U_out, &en);
+  if (st != TALS_OK) return st;
+  cudaError_t e = cudaGraphLaunch(en->exec, c->stream);
+  return e == cudaSuccess ? TALS_OK : cuda_fail(e, "graph launch");
+}
+
+tals_status st_hosvd_graph_collect(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* stats) {
+  GraphEntry* en = find(c, 0, G_out, U_out);
+  if (!en) return fail(TALS_EINVAL, "no st-HOSVD graph launched for these buffers");
+  return collect(c, 0, en, stats);
+}
 
 tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st) {
   return run(c, 0, G_out, U_out, st);

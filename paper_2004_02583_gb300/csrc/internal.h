@@ -51,6 +51,10 @@ tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters);
 
 // graph.cu: whole decompositions as one CUDA graph per context and output set
 tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
+// The cached st-HOSVD graph for (c->A, G_out, U_out), launched on c->stream without
+// waiting; collect reads its status and statistics once the stream is synchronized.
+tals_status st_hosvd_graph_launch(tals_ctx* c, void* G_out, void* const* U_out);
+tals_status st_hosvd_graph_collect(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* stats);
 tals_status t_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
 void graphs_destroy(tals_ctx* c);
 
@@ -111,6 +115,14 @@ struct tals_ctx {
   // st_hosvd_host device buffers
   void* hostio_G = nullptr;
   void* hostio_U[TALS_MAX_NDIM] = {};
+  // st_hosvd_host_many: a second input buffer, the upload stream, and per slot
+  // the upload / release events and the device outputs
+  void* A_owned2 = nullptr;
+  cudaStream_t upload = nullptr;
+  cudaEvent_t ev_loaded[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  void* pipe_G[2] = {nullptr, nullptr};
+  void* pipe_U[2][TALS_MAX_NDIM] = {};
   tals::GraphCache* graphs = nullptr;
   tals::MixedState* mixed = nullptr;
 };
