@@ -720,6 +720,22 @@ def run_c5(args):
     clk = clocks.stop()
     rec_bytes = A.numel() * 4 + Gd.numel() * 4 + sum(u.numel() * 4 for u in Us)
     gbs = rec_bytes / (rec_ms * 1e-3) / 1e9
+    # algorithmic flops of the reconstruction in the library's mode order (the flop minimum over
+    # all orders: each mode product costs 2 min(I_n, R_n) flops per element of its larger side)
+    import itertools
+    dims, rks = list(A.shape), list(cfg.ranks)
+
+    def _order_flops(order):
+        cur, fl = list(rks), 0
+        for m in order:
+            cur[m] = dims[m]
+            fl += 2 * min(dims[m], rks[m]) * int(np.prod(cur))
+        return fl
+    rec_flops = min(_order_flops(o) for o in itertools.permutations(range(len(dims))))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    c5_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * c5_mhz * 1e6 / 1e12
+    rec_tflops = rec_flops / (rec_ms * 1e-3) / 1e12
     # oracle: the loss gradient on a 1024 x 1024 x S slab, scaled
     S = 8
     a_s = p.A[:, :, :S].astype(np.float64)
@@ -734,11 +750,18 @@ def run_c5(args):
                        "forward_ms": round(fwd_ms, 3), "backward_ms": round(bwd_ms, 3),
                        "sweeps": st["sweeps"], "rel_err": st["rel_err"],
                        "l2": "inputs (2 GiB) larger than L2"},
-            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(gbs / hbm, 4), "traffic": None,
-                         "kernel": "reconstruct (B = G x1 U1 x2 U2 x3 U3, the 2 GiB write of the "
-                                   "backward's largest pass)", "pass_ms": round(rec_ms, 3),
-                         "algorithmic_bytes": rec_bytes},
+            "roofline": {"bound": "alu", "achieved": round(rec_tflops, 2), "peak": round(alu_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(rec_tflops / alu_peak, 4),
+                         # ncu DRAM bytes of the three mode products on the 1024x1024x256 case
+                         # (profiles/mg_pipe_mode_products_1024x1024x256.md), x2 for the full size
+                         "traffic": 2 * (823040 + 8734720 + 73020000 + 134466304 + 1012872000),
+                         "kernel": "reconstruct: three mg_pipe mode products (B = G x1 U1 x2 U2 x3 U3, "
+                                   "2 GiB written; 64 flops per written element, above the SIMT ridge)",
+                         "pass_ms": round(rec_ms, 3), "algorithmic_flops": rec_flops,
+                         "algorithmic_bytes": rec_bytes, "hbm_gbs_achieved": round(gbs, 1),
+                         "hbm_frac": round(gbs / hbm, 4),
+                         "peak_source": f"FP32 FMA peak from {sms} SMs x 128 lanes x 2 flops x "
+                                        f"{c5_mhz} MHz (derived); HBM {hbm} GB/s (measured)"},
             "clocks": _clock_line(clk),
             "cpu_baseline": {"value": round((S / 512.0) / sec, 4), "unit": "loss-gradients/s",
                              "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
