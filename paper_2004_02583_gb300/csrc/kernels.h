@@ -27,6 +27,7 @@ struct PassConfig {
   int nbuf = 2;      // tile buffers (2: cp.async double buffering)
   int nt = 256;      // threads per CTA
   int jt = 16;       // unfolding columns per tile
+  bool tr = false;   // transposed tile (Q = 1 views, FP32)
   bool ok = false;
 };
 

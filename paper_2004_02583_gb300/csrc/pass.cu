@@ -5,13 +5,13 @@
 
 namespace tals {
 
-template <typename T, int RC, int RPT, int RW, int NT, int JT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT, bool TR>
 __global__ void __launch_bounds__(NT, 1) pass_kernel(PassArgs<T> a) {
   if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* yp = a.Ypart != nullptr ? a.Ypart + (size_t)blockIdx.x * a.I * a.R : nullptr;
   const double tot =
-      pass_cta<T, RC, RPT, RW, NT, JT>(a, blockIdx.x, gridDim.x, blockIdx.y, smem_raw, yp);
+      pass_cta<T, RC, RPT, RW, NT, JT, TR>(a, blockIdx.x, gridDim.x, blockIdx.y, smem_raw, yp);
   if (threadIdx.x == 0) a.spart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -39,17 +39,32 @@ const Inst kInstF32[] = {{32, 1, 16, 512, 16}, {32, 2, 16, 512, 16}, {32, 4, 16,
 const Inst kInstF64[] = {{16, 1, 8, 256, 16}, {16, 2, 8, 256, 16}, {16, 4, 8, 256, 16},
                          {8, 1, 8, 256, 16},  {8, 2, 8, 256, 16},  {8, 4, 8, 256, 16}};
 
-template <typename T, int RC, int RPT, int RW, int NT, int JT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT, bool TR = false>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&pass_kernel<T, RC, RPT, RW, NT, JT>);
+  return reinterpret_cast<void*>(&pass_kernel<T, RC, RPT, RW, NT, JT, TR>);
 }
 
+// Instantiations with the transposed tile (views with Q = 1, FP32; an even
+// number of ranks per step-1 lane).
+const Inst kInstF32Tr[] = {{32, 4, 16, 256, 16}, {32, 2, 16, 512, 16}, {16, 1, 16, 512, 16},
+                           {16, 4, 16, 256, 16}, {16, 2, 8, 128, 64},  {8, 2, 4, 128, 64},
+                           {16, 2, 8, 256, 32},  {32, 2, 16, 256, 32}};
+
 template <typename T>
-void* lookup(const Inst& in) {
+void* lookup(const Inst& in, bool tr) {
 #define TALS_CASE(RC, RPT, RW, NT, JT)                                               \
   if (in.rc == RC && in.rpt == RPT && in.rw == RW && in.nt == NT && in.jt == JT)     \
     return kernel_ptr<T, RC, RPT, RW, NT, JT>();
+#define TALS_CASE_TR(RC, RPT, RW, NT, JT)                                            \
+  if (in.rc == RC && in.rpt == RPT && in.rw == RW && in.nt == NT && in.jt == JT)     \
+    return kernel_ptr<T, RC, RPT, RW, NT, JT, true>();
   if constexpr (sizeof(T) == 4) {
+    if (tr) {
+      TALS_CASE_TR(32, 4, 16, 256, 16) TALS_CASE_TR(32, 2, 16, 512, 16) TALS_CASE_TR(16, 1, 16, 512, 16)
+      TALS_CASE_TR(16, 4, 16, 256, 16) TALS_CASE_TR(16, 2, 8, 128, 64) TALS_CASE_TR(8, 2, 4, 128, 64)
+      TALS_CASE_TR(16, 2, 8, 256, 32) TALS_CASE_TR(32, 2, 16, 256, 32)
+      return nullptr;
+    }
     TALS_CASE(32, 1, 16, 512, 16) TALS_CASE(32, 2, 16, 512, 16) TALS_CASE(32, 4, 16, 256, 16)
     TALS_CASE(16, 1, 16, 512, 16) TALS_CASE(16, 2, 16, 512, 16) TALS_CASE(16, 4, 16, 256, 16)
     TALS_CASE(8, 1, 8, 512, 16) TALS_CASE(8, 2, 8, 512, 16) TALS_CASE(8, 4, 8, 512, 16)
@@ -61,6 +76,7 @@ void* lookup(const Inst& in) {
     TALS_CASE(8, 1, 8, 256, 16) TALS_CASE(8, 2, 8, 256, 16) TALS_CASE(8, 4, 8, 256, 16)
   }
 #undef TALS_CASE
+#undef TALS_CASE_TR
   return nullptr;
 }
 
@@ -69,8 +85,12 @@ void* lookup(const Inst& in) {
 PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
   PassConfig cfg;
   const bool f32 = dtype == 1;
-  const Inst* tab = f32 ? kInstF32 : kInstF64;
-  const int ntab = f32 ? (int)(sizeof(kInstF32) / sizeof(Inst)) : (int)(sizeof(kInstF64) / sizeof(Inst));
+  // views with Q = 1 (the last mode): columns are contiguous rows, staged as a
+  // transposed tile with 16-byte copies (FP32, I a multiple of 4)
+  const bool tr = f32 && v.Q == 1 && v.I % 4 == 0;
+  const Inst* tab = tr ? kInstF32Tr : (f32 ? kInstF32 : kInstF64);
+  const int ntab = tr ? (int)(sizeof(kInstF32Tr) / sizeof(Inst))
+                      : (f32 ? (int)(sizeof(kInstF32) / sizeof(Inst)) : (int)(sizeof(kInstF64) / sizeof(Inst)));
   const size_t smem_max = 227 * 1024;
   // Score every fitting (instantiation, buffering): rank chunks re-read the
   // tensor (mostly from L2) and a single buffer exposes load latency; prefer
@@ -82,7 +102,7 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
       const int nrg = in.rc / in.rw;
       const int rowt = in.nt / nrg;
       if ((long long)rowt * in.rpt < v.I) continue;
-      size_t sm = f32 ? pass_smem_bytes<float>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt, in.jt)
+      size_t sm = f32 ? pass_smem_bytes<float>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt, in.jt, tr)
                       : pass_smem_bytes<double>(v.I, in.rc, rowt * in.rpt, nbuf, in.nt, in.jt);
       if (sm > smem_max) continue;
       const int chunks = (R + in.rc - 1) / in.rc;
@@ -106,6 +126,7 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
         cfg.jt = in.jt;
         cfg.smem = sm;
         cfg.nbuf = nbuf;
+        cfg.tr = tr;
         cfg.ok = true;
       }
     }
@@ -128,7 +149,8 @@ cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* 
   if (!cfg.ok) return cudaErrorInvalidConfiguration;
   if (resid && cfg.grid_y != 1) return cudaErrorInvalidValue;
   const Inst in{cfg.rc, cfg.rpt, cfg.rw, cfg.nt, cfg.jt};
-  void* fn = dtype == 1 ? lookup<float>(in) : lookup<double>(in);
+  if (cfg.tr && (dtype != 1 || v.Q != 1 || v.I % 4 != 0)) return cudaErrorInvalidValue;
+  void* fn = dtype == 1 ? lookup<float>(in, cfg.tr) : lookup<double>(in, false);
   if (fn == nullptr) return cudaErrorInvalidDeviceFunction;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfg.smem);
@@ -136,7 +158,8 @@ cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* 
   dim3 grid(cfg.grid_x, cfg.grid_y);
   const long long ntiles = (v.J() + cfg.jt - 1) / cfg.jt;
   const size_t esz = dtype == 1 ? 4 : 8;
-  const int vec_ok = ((uintptr_t)X % 16 == 0) && ((v.Q * esz) % 16 == 0);
+  // 16-byte tile copies: rows of Q elements (of I elements for the transposed tile) stay aligned
+  const int vec_ok = ((uintptr_t)X % 16 == 0) && (((cfg.tr ? v.I : v.Q) * esz) % 16 == 0);
   if (dtype == 1) {
     PassArgs<float> a{(const float*)X, v.P, v.I, v.Q, v.J(), R, mode, (const float*)Lq,
                       (const float*)Win, (float*)Ypart, spart, (float*)Wout, sketch_state, st,

@@ -73,11 +73,22 @@ __host__ __device__ inline long long slack_rows(long long I, int rowspan) {
   return rowspan > I ? rowspan - I : 0;
 }
 
+// Transposed tile (views with Q = 1, FP32): column c of the tile -- row p = j0 + c
+// of the P x I view, contiguous in memory -- is row c of a JT x tr_pitch(I)
+// array, copied with 16-byte chunks; step 2's reads past row I - 1 of the last
+// column need tr_slack elements after the last buffer.
+__host__ __device__ inline long long tr_pitch(long long I) { return I + 4; }
+__host__ __device__ inline long long tr_slack(long long I, int rowspan) {
+  const long long s = rowspan - tr_pitch(I);
+  return s > 0 ? (s + 3) / 4 * 4 : 0;
+}
+
 template <typename T>
 __host__ __device__ inline size_t pass_smem_bytes(long long I, int RC, int rowspan, int nbuf,
-                                                  int nt = kThreads, int jt = kJT) {
+                                                  int nt = kThreads, int jt = kJT, bool tr = false) {
   const size_t jtp = (size_t)jt + 4;
-  size_t ts = (size_t)nbuf * ((size_t)I * jtp) + (size_t)slack_rows(I, rowspan) * jtp;
+  size_t ts = tr ? (size_t)nbuf * jt * tr_pitch(I) + (size_t)tr_slack(I, rowspan)
+                 : (size_t)nbuf * ((size_t)I * jtp) + (size_t)slack_rows(I, rowspan) * jtp;
   size_t ls = (size_t)I * RC;
   size_t wr = (size_t)(nt / 32) * jt * (RC + 4);
   size_t ws = (size_t)jt * (RC + 4);
@@ -107,11 +118,34 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Issue the copies of tile t (JT columns) into Tb (I x (JT + 4)). Columns beyond J are zero-filled.
 // Column c of the tile is B[p, :, q] with (p, q) stepped from the tile's first
 // column: one division per tile, none per element.
-template <typename T, int JT = kJT>
+template <typename T, int JT = kJT, bool TR = false>
 __device__ __forceinline__ void issue_tile(const PassArgs<T>& a, long long t, T* Tb) {
   const long long I = a.I, Q = a.Q;
   const long long j0 = t * JT;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if constexpr (TR) {
+    // Q = 1: tile column c is the contiguous row j0 + c of the P x I view
+    const long long IP = tr_pitch(I);
+    if (a.vec_ok) {   // X 16-byte aligned and I % 4 == 0
+      constexpr int EPV = 16 / sizeof(T);
+      const long long cpr = I / EPV;
+      for (long long e = tid; e < JT * cpr; e += nt) {
+        const int c = (int)(e / cpr);
+        const long long k = e - c * cpr;
+        const bool ok = j0 + c < a.J;
+        cp_async16(Tb + c * IP + k * EPV, a.X + (ok ? (j0 + c) * I + k * EPV : 0), ok ? 16 : 0);
+      }
+    } else {
+      for (long long e = tid; e < JT * I; e += nt) {
+        const int c = (int)(e / I);
+        const long long i = e - c * I;
+        const bool ok = j0 + c < a.J;
+        cp_async_elem<sizeof(T)>(Tb + c * IP + i, a.X + (ok ? (j0 + c) * I + i : 0),
+                                 ok ? (int)sizeof(T) : 0);
+      }
+    }
+    return;
+  }
   const long long p0 = j0 / Q, q0 = j0 - p0 * Q;
   constexpr int EPV = 16 / sizeof(T);   // elements per 16-byte chunk
   if (a.vec_ok && q0 + JT <= Q && j0 + JT <= a.J) {
@@ -170,15 +204,20 @@ __device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
 // One CTA's share of a pass: tiles t_begin, t_begin + t_step, ... of rank chunk
 // `rchunk`. Y (this chunk's columns) is written to Yout (I x R, row stride R);
 // returns the CTA's FP64 sum (||B||^2, ||W||^2 or ||B - Qb W^T||^2) in thread 0.
-template <typename T, int RC, int RPT, int RW, int NT, int JT = kJT>
+template <typename T, int RC, int RPT, int RW, int NT, int JT = kJT, bool TR = false>
 __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_begin, long long t_step,
                                            int rchunk, unsigned char* smem_raw, T* Yout) {
   using S = PassShape<T, RC, RPT, RW, NT, JT>;
+  static_assert(!TR || (sizeof(T) == 4 && S::RL % 2 == 0), "transposed tiles: FP32, even RL");
   constexpr int JTP = JT + 4;
   constexpr int WSP = S::WSP;
   const long long I = a.I;
-  T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][I][JTP]
-  T* Ls = Tbuf + (size_t)a.nbuf * I * JTP + (size_t)slack_rows(I, S::ROWT * RPT) * JTP;  // [I][RC]
+  const long long IP = tr_pitch(I);   // TR: row pitch of the transposed tile
+  // elements per tile buffer: [I][JTP], or [JT][IP] for TR
+  const size_t TBS = TR ? (size_t)JT * IP : (size_t)I * JTP;
+  T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][tile]
+  T* Ls = Tbuf + (size_t)a.nbuf * TBS +
+          (TR ? (size_t)tr_slack(I, S::ROWT * RPT) : (size_t)slack_rows(I, S::ROWT * RPT) * JTP);  // [I][RC]
   T* Wred = Ls + (size_t)I * RC;                                           // [NW][JT][WSP]
   T* Ws = Wred + (size_t)S::NW * JT * WSP;                                // [JT][WSP]
   double* red = reinterpret_cast<double*>(Ws + (size_t)JT * WSP);
@@ -195,7 +234,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 
   // first tile in flight before anything else
   long long t = t_begin;
-  if (t < a.ntiles) issue_tile<T, JT>(a, t, Tbuf);
+  if (t < a.ntiles) issue_tile<T, JT, TR>(a, t, Tbuf);
   cp_async_commit();
 
   // Qb columns r0 .. r0+RC-1 (zero beyond R) into shared memory.
@@ -222,17 +261,18 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 
   const int rgrp = tid / S::ROWT;            // step-2 r-group (warp-uniform)
   const int ti = tid - rgrp * S::ROWT;       // step-2 row-thread index
-  const long long IW = (I + S::NW - 1) / S::NW;
+  // step-1 row slice of this warp (TR: a multiple of 4 rows, for float4 reads along i)
+  const long long IW = TR ? ((I + S::NW - 1) / S::NW + 3) / 4 * 4 : (I + S::NW - 1) / S::NW;
   const long long ilo = min(I, warp * IW), ihi = min(I, ilo + IW);
   const int cg = lane % S::CG, rg = lane / S::CG;   // step-1 lane layout: CG col groups x RG r groups
 
   int buf = 0;
   for (; t < a.ntiles; t += t_step) {
     const long long tn = t + t_step;
-    T* Tb = Tbuf + (size_t)buf * I * JTP;
+    T* Tb = Tbuf + (size_t)buf * TBS;
     if (a.nbuf > 1) {
       // stream the next tile into the other buffer while this one is used
-      if (tn < a.ntiles) issue_tile<T, JT>(a, tn, Tbuf + (size_t)(buf ^ 1) * I * JTP);
+      if (tn < a.ntiles) issue_tile<T, JT, TR>(a, tn, Tbuf + (size_t)(buf ^ 1) * TBS);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
@@ -250,7 +290,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         for (long long e = tid; e < I * JT; e += NT) {
           const long long i = e / JT;
           const int c = (int)(e - i * JT);
-          const float x = (c < ncol) ? Tb[i * JTP + c] : 0.f;
+          const float x = (c < ncol) ? Tb[TR ? c * IP + i : i * JTP + c] : 0.f;
           const float pq = x * x, pe = fmaf(x, x, -pq);
           const float tq = hi + pq;
           lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
@@ -275,7 +315,52 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       const T* trow = Tb + cg * 4;
       const T* lrow = Ls + rg * S::RL;
       const int nrow = (int)(ihi - ilo);
-      if constexpr (sizeof(T) == 4 && S::RL % 2 == 0) {
+      if constexpr (TR) {
+        // transposed tile: this lane's columns are cg + CG u (u = 0..3), so the
+        // four column groups of a warp read different bank groups; rows in
+        // fours, one float4 along i per column
+        float2 acc2[4][S::RL / 2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < S::RL / 2; ++v) acc2[u][v] = make_float2(0.f, 0.f);
+        const float* tc = reinterpret_cast<const float*>(Tb) + (long long)cg * IP + ilo;
+        const float* lp = reinterpret_cast<const float*>(lrow) + (int)ilo * RC;
+#pragma unroll 2
+        for (int ii = 0; ii < nrow; ii += 4) {
+          float4 bv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) bv[u] = *reinterpret_cast<const float4*>(tc + (long long)u * S::CG * IP + ii);
+#pragma unroll
+          for (int r4 = 0; r4 < 4; ++r4) {
+            float2 l2[S::RL / 2];
+            if constexpr (S::RL % 4 == 0) {
+#pragma unroll
+              for (int v = 0; v < S::RL; v += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(lp + (ii + r4) * RC + v);
+                l2[v / 2] = make_float2(q4.x, q4.y);
+                l2[v / 2 + 1] = make_float2(q4.z, q4.w);
+              }
+            } else {
+              l2[0] = *reinterpret_cast<const float2*>(lp + (ii + r4) * RC);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float x = r4 == 0 ? bv[u].x : r4 == 1 ? bv[u].y : r4 == 2 ? bv[u].z : bv[u].w;
+              const float2 t2 = make_float2(x, x);
+#pragma unroll
+              for (int v = 0; v < S::RL / 2; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < S::RL / 2; ++v) {
+            acc[u][2 * v] = acc2[u][v].x;
+            acc[u][2 * v + 1] = acc2[u][v].y;
+          }
+      } else if constexpr (sizeof(T) == 4 && S::RL % 2 == 0) {
         // FP32: paired FMAs (two lanes of r per instruction), same rounding as fmaf
         float2 acc2[4][S::RL / 2];
 #pragma unroll
@@ -356,7 +441,8 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < S::RL; ++v) wr[(cg * 4 + u) * WSP + rg * S::RL + v] = acc[u][v];
+        for (int v = 0; v < S::RL; ++v)
+          wr[(TR ? cg + S::CG * u : cg * 4 + u) * WSP + rg * S::RL + v] = acc[u][v];
       __syncthreads();
       // final W: consecutive threads -> consecutive q (cfast) or consecutive r
       T wsq = T(0);
@@ -393,7 +479,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 #pragma unroll
             for (int q = 0; q < 4; ++q) dot = fma(l4[q], w4[q], dot);
           }
-          const T rsd = Tb[i * JTP + c] - dot;
+          const T rsd = Tb[TR ? c * IP + i : i * JTP + c] - dot;
           racc += (c < ncol) ? rsd * rsd : T(0);
         }
         sacc += (double)racc;
@@ -434,10 +520,19 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
 #pragma unroll
         for (int c4 = 0; c4 < JT; c4 += 4) {
           float tv[RPT][4];
+          if constexpr (TR) {
+            // transposed tile: consecutive threads read consecutive rows of a column
+            const float* tcol = reinterpret_cast<const float*>(Tb) + ti;
 #pragma unroll
-          for (int k = 0; k < RPT; ++k) {
-            const float4 x = *reinterpret_cast<const float4*>(tp + k * S::ROWT * JTP + c4);
-            tv[k][0] = x.x; tv[k][1] = x.y; tv[k][2] = x.z; tv[k][3] = x.w;
+            for (int k = 0; k < RPT; ++k)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) tv[k][u] = tcol[(long long)(c4 + u) * IP + k * S::ROWT];
+          } else {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+              const float4 x = *reinterpret_cast<const float4*>(tp + k * S::ROWT * JTP + c4);
+              tv[k][0] = x.x; tv[k][1] = x.y; tv[k][2] = x.z; tv[k][3] = x.w;
+            }
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -484,7 +579,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
     if (a.nbuf > 1) {
       buf ^= 1;
     } else if (tn < a.ntiles) {
-      issue_tile<T, JT>(a, tn, Tbuf);
+      issue_tile<T, JT, TR>(a, tn, Tbuf);
       cp_async_commit();
     }
   }

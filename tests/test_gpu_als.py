@@ -81,6 +81,8 @@ SHAPES = [
     ((20, 18, 16, 14), (3, 4, 2, 5)),   # 4th order
     ((130, 70, 9), (12, 9, 9)),         # last mode small: Q = 9 and Q = 1 layouts
     ((7, 300, 12), (7, 16, 12)),        # R = I (full rank mode)
+    ((37, 29, 64), (5, 6, 8)),          # last mode I % 4 == 0: transposed tiles, J = 1073 ragged
+    ((24, 20, 200), (4, 5, 12)),        # transposed tiles with I = 200, J = 480
 ]
 
 
