@@ -2,7 +2,8 @@
 //
 // One CTA walks tiles of kTileCols consecutive unfolding columns j = p*Q + q,
 // reading B[p, 0:I, q] in place (never forming a permuted unfolding, Sec. 3
-// "row-wise update"). Per tile, with Qb the orthonormal basis of L_k in shared
+// "row-wise update"). A tile is held as I x (JT + 4); for views with Q = 1,
+// whose columns are contiguous rows of the tensor, as JT x (I + 4) (TR). Per tile, with Qb the orthonormal basis of L_k in shared
 // memory:
 //   step 1  W_t = B_t^T Qb                (kTileCols x RC, K = I)     Alg. 3 R-update
 //   step 2  Y  += B_t W_t                 (I x RC, K = kTileCols)     Alg. 3 L-update
