@@ -47,23 +47,17 @@ __global__ void reduce_rows_kernel(const T* __restrict__ Ypart, int gx, long lon
       // FP32 partials: Neumaier-compensated FP32 sum (the running sum and its
       // exact rounding error), FP64-level accuracy at FP32 arithmetic rates
       float hi = 0.f, lo = 0.f;
-      int b = 0;
-      for (; b + 8 <= nb; b += 8) {
+      // batches of 8 loads in flight, the last one predicated (adding 0 is exact)
+      for (int b = 0; b < nb; b += 8) {
         float x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(b + u) * sstride];
+        for (int u = 0; u < 8; ++u) x[u] = b + u < nb ? src[(size_t)(b + u) * sstride] : 0.f;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float t = hi + x[u];
           lo += fabsf(hi) >= fabsf(x[u]) ? (hi - t) + x[u] : (x[u] - t) + hi;
           hi = t;
         }
-      }
-      for (; b < nb; ++b) {
-        const float xv = src[(size_t)b * sstride];
-        const float t = hi + xv;
-        lo += fabsf(hi) >= fabsf(xv) ? (hi - t) + xv : (xv - t) + hi;
-        hi = t;
       }
       s = (double)hi + (double)lo;
     } else {
