@@ -35,7 +35,7 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # from ncu captures of the 512x512x256 case scaled by 2 (traffic grows with the
 # columns processed): profiles/pass_kernel_sweep_512x512x256.md and
 # profiles/tc_pass_512x512x256.md.
-PASS_TRAFFIC = 2 * (268605952 + 14885120)   # bytes per launch
+PASS_TRAFFIC = 2 * (268594432 + 14928640)   # bytes per launch (ncu, 512x512x256 view, x2)
 TC_TRAFFIC = 2 * (134336000 + 3278080)
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
