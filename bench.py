@@ -113,6 +113,25 @@ def _dist():
     return world, rank, local
 
 
+def _job_ms(ms, dist, device="cuda"):
+    """Time of one weak-scaled step of the whole job: every rank times its own
+    replica, and the step lasts as long as the slowest rank (max over ranks),
+    followed by a barrier. Single process: the rank's own time."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def _job_value(world, ms, units_per_rank=1.0):
+    """Whole-job throughput: the units every rank processed in one step, per second
+    of the slowest rank's step time."""
+    return world * units_per_rank * 1e3 / ms
+
+
 def _cpu_oracle_run(a64, ranks, eta):
     from oracle import tucker_oracle as O
     t0 = time.perf_counter()
@@ -255,12 +274,7 @@ def main():
         sweeps_total += sum(st["sweeps"])
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = _job_ms(ev0.elapsed_time(ev1) / args.steps, dist)
     clk = clocks.stop() if rank == 0 else {}
 
     # the other precision path on the same input, for the equal-error comparison
@@ -373,7 +387,7 @@ def main():
     plain_st = st if args.precision == "native" else ost
     mixed_ms = ms if args.precision == "mixed_bf16" else o_ms
     plain_ms = ms if args.precision == "native" else o_ms
-    value = world * 1e3 / ms
+    value = _job_value(world, ms)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "st-HOSVD/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4),
