@@ -161,6 +161,15 @@ tals_status st_hosvd_host(tals_ctx* ctx, const void* A_host, void* G_host,
 tals_status st_hosvd_host_many(tals_ctx* ctx, int count, const void* const* A_host,
                                void* const* G_host, void* const* U_host, tals_stats* stats);
 
+/* Self-test of the failure path of the bounded device waits (failure detection
+ * without a fault): one CTA waits on an mbarrier that nothing arrives at, using
+ * the tensor-core pass's own bounded-wait helper with a limit of `seconds`
+ * (0 < seconds <= 10) of SM clock cycles; the wait gives up, the kernel records
+ * the timeout and returns, and the device stays usable. Returns TALS_ETIMEOUT
+ * when the failure path works (TALS_OK would mean the wait completed), TALS_EINVAL
+ * for a bad limit, TALS_ECUDA on a CUDA error. stream: a cudaStream_t or NULL. */
+tals_status tals_selftest_wait_timeout(double seconds, void* stream);
+
 /* Like tucker_als_init but the context allocates and owns a device buffer for A
  * (to be filled by st_hosvd_host or by copying into tals_ctx_tensor()). */
 tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int64_t* dims,

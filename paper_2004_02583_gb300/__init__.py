@@ -72,6 +72,7 @@ SIGNATURES = {
     "st_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
     "t_hosvd": (ctypes.c_int, [_VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
     "st_hosvd_host": (ctypes.c_int, [_VP, _VP, _VP, _VPP, ctypes.POINTER(tals_stats)]),
+    "tals_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_double, _VP]),
     "st_hosvd_host_many": (ctypes.c_int, [_VP, ctypes.c_int, _VPP, _VPP, _VPP,
                                           ctypes.POINTER(tals_stats)]),
     "reconstruct": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
@@ -122,6 +123,13 @@ def _check(status: int):
     if status != TALS_OK:
         msg = lib().tals_last_error()
         raise TalsError(status, msg.decode() if msg else "")
+
+
+def selftest_wait_timeout(seconds=0.01, stream=None) -> int:
+    """Run the failure path of the bounded device waits once (a wait on a barrier
+    nothing arrives at, giving up after `seconds`); returns the status code,
+    TALS_ETIMEOUT when the failure path works."""
+    return int(lib().tals_selftest_wait_timeout(float(seconds), _stream_ptr(stream)))
 
 
 def default_opts(**kw) -> tals_opts:

@@ -352,6 +352,26 @@ const char* tals_last_error(void) { return g_err.c_str(); }
 
 const char* tals_version(void) { return "tals 0.1 (sm_103a)"; }
 
+tals_status tals_selftest_wait_timeout(double seconds, void* stream) {
+  if (!(seconds > 0.0) || seconds > 10.0) return fail(TALS_EINVAL, "seconds must be in (0, 10]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device clock");
+  int* err = nullptr;
+  if ((e = cudaMallocAsync(&err, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "status buffer");
+  int host = -1;
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_wait_timeout_probe(err, (long long)(seconds * khz * 1e3), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(err, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  if (host == TALS_ETIMEOUT) return fail(TALS_ETIMEOUT, "bounded wait gave up as intended");
+  return TALS_OK;
+}
+
 static tals_status validate(int dtype, int ndim, const int64_t* dims, const int* ranks) {
   if (dtype != TALS_F32 && dtype != TALS_F64) return fail(TALS_EINVAL, "unsupported dtype %d", dtype);
   if (ndim < 2 || ndim > TALS_MAX_NDIM) return fail(TALS_EINVAL, "ndim %d outside [2, 8]", ndim);

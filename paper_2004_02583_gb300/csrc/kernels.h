@@ -126,6 +126,9 @@ int factor_adjoint_splits(long long P, long long I, long long Q, int R, int sms)
 template <typename T>
 cudaError_t launch_factor_adjoint_any(const T* X, long long P, long long I, long long Q, const T* V, int R,
                                       int S, T* part, T* Ubar, cudaStream_t s);
+// One CTA whose bounded mbarrier wait runs out after limit_cycles; *err = 5
+// (TALS_ETIMEOUT) afterwards. Exercises the failure path without a fault.
+cudaError_t launch_wait_timeout_probe(int* err, long long limit_cycles, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, void* y, size_t n, int sms, cudaStream_t s,
                            double* sq = nullptr);
 int to_bf16_blocks(size_t n, int sms);

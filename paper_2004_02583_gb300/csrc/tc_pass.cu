@@ -153,18 +153,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-// Clock-bounded wait (about two seconds); gives up early when another role of
-// the CTA has already failed.
-__device__ __forceinline__ bool mbar_wait_b(uint32_t mbar, uint32_t parity, volatile int* fail) {
+// Clock-bounded wait: gives up after `limit` cycles (setting *fail), or early
+// when another role of the CTA has already failed.
+__device__ __forceinline__ bool mbar_wait_limit(uint32_t mbar, uint32_t parity, volatile int* fail,
+                                                long long limit) {
   const long long t0 = clock64();
   while (true) {
     if (mbar_try(mbar, parity)) return true;
     if (*fail) return false;
-    if (clock64() - t0 > (4ll << 30)) {
+    if (clock64() - t0 > limit) {
       *fail = 1;
       return false;
     }
   }
+}
+
+// The pass's waits: about two seconds.
+__device__ __forceinline__ bool mbar_wait_b(uint32_t mbar, uint32_t parity, volatile int* fail) {
+  return mbar_wait_limit(mbar, parity, fail, 4ll << 30);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -686,6 +692,30 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __res
     const double t = block_sum((double)hi + (double)lo, red);
     if (threadIdx.x == 0) sq[blockIdx.x] = t;
   }
+}
+
+// Failure path of the bounded waits, exercised on purpose: one thread waits on
+// an initialised mbarrier that nothing arrives at (phase 0 never completes),
+// gives up after `limit` cycles through the same helper as the pass, records
+// TALS_ETIMEOUT and the kernel returns normally.
+__global__ void wait_timeout_probe(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) {
+    mbar_init(su32(&bar), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* vf = &s_fail;
+    if (!mbar_wait_limit(su32(&bar), 0u, vf, limit)) atomicExch(err, 5);   // TALS_ETIMEOUT
+  }
+}
+
+cudaError_t launch_wait_timeout_probe(int* err, long long limit_cycles, cudaStream_t s) {
+  wait_timeout_probe<<<1, 32, 0, s>>>(err, limit_cycles);
+  return cudaGetLastError();
 }
 
 int to_bf16_blocks(size_t n, int sms) {

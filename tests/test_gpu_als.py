@@ -207,3 +207,15 @@ def test_exact_recovery_f32(tals):
     G, Us, st = tals.st_hosvd(_gpu(p.A), ranks, eta=1e-4, seed=0)
     assert all(st["converged"]) and max(st["sweeps"]) <= 3
     assert st["rel_err"] < 1e-3   # FP32 noise floor of an exact tensor
+
+
+def test_bounded_wait_failure_path_and_recovery(tals):
+    # failure detection without a fault: a device wait that can never complete gives
+    # up after its limit, the status reaches the host, and the device stays usable
+    assert tals.selftest_wait_timeout(0.01) == tals.TALS_ETIMEOUT
+    assert tals.selftest_wait_timeout(0.002) == tals.TALS_ETIMEOUT
+    dims, ranks = (40, 37, 29), (5, 6, 7)
+    p = W.planted(W.SEED_BASE + 11, dims, ranks, "inv_k", 1e-2, dtype=np.float32)
+    ref = O.st_hosvd_als(p.A.astype(np.float64), ranks, eta=-1.0, seed=5, max_sweeps=3)
+    _cmp(tals.st_hosvd(_gpu(p.A), ranks, eta=-1.0, seed=5, max_sweeps=3), ref,
+         p.A.astype(np.float64), np.float32, fixed=True)
