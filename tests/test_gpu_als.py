@@ -219,3 +219,31 @@ def test_bounded_wait_failure_path_and_recovery(tals):
     ref = O.st_hosvd_als(p.A.astype(np.float64), ranks, eta=-1.0, seed=5, max_sweeps=3)
     _cmp(tals.st_hosvd(_gpu(p.A), ranks, eta=-1.0, seed=5, max_sweeps=3), ref,
          p.A.astype(np.float64), np.float32, fixed=True)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sweep_by_sweep_errors_match_oracle(tals, dtype):
+    # the user-drivable unit, one sweep at a time: e_0, e_1, ... of every mode equal the
+    # oracle's literal Alg. 3 sequence and never increase (each half-step is an exact LS
+    # minimiser; invariant (iv))
+    dims, ranks = (40, 36, 30), (6, 5, 4)
+    p = W.planted(W.SEED_BASE + 18, dims, ranks, "inv_k", 1e-2, dtype=dtype)
+    a64 = p.A.astype(np.float64)
+    K = 5
+    ref = O.st_hosvd_als(a64, ranks, eta=-1.0, seed=6, max_sweeps=K)
+    ctx = tals.Context(_gpu(p.A), ranks, eta=-1.0, max_sweeps=K, seed=6)
+    norm_a = np.sqrt(O.frob2(a64))
+    tol_e2 = (1e-12 if dtype == np.float64 else 2e-7) * norm_a ** 2
+    for n in ref.order:
+        seq = []
+        for _ in range(K):
+            e, _ = ctx.mode_sweep(n, 1)
+            seq.append(e)
+        want = ref.als[n].errs
+        assert len(want) == K
+        for k in range(K):
+            assert abs(seq[k] ** 2 - want[k] ** 2) <= tol_e2, (n, k, seq[k], want[k])
+            if k:
+                assert seq[k] ** 2 <= seq[k - 1] ** 2 + tol_e2
+        ctx.mode_finish(n, truncate=True)
+    ctx.close()
