@@ -412,12 +412,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // counter-based generator (entry (j, r) from output j R + r)
         if (lt >= 2) ok = mbar_wait_b(su32(&opfree[wb]), (use - 1) & 1u, vfail);
         if (!ok) break;
-        if (wrow) {
+        {
+          // lanes l and l + 16 share row m of W_t, half of its ranks each: the
+          // generator is integer-heavy, and every tile of the pass waits for it
           const long long j = (blockIdx.x + lt * gridDim.x) * kTcCols + m;
           unsigned char* wrowp = wop + (size_t)wb * RP * 128 + (m & 7) * 2;
           const int c8 = m >> 3;
+          const int rbeg = (lane >> 4) * (RP / 2);
 #pragma unroll 4
-          for (int r = 0; r < RP; ++r) {
+          for (int rr = 0; rr < RP / 2; ++rr) {
+            const int r = rbeg + rr;
             const float w = r < a.R ? sketch_entry(a.sketch, (uint64_t)j, a.R, r) : 0.f;
             *reinterpret_cast<__nv_bfloat16*>(wrowp + r * 128 + ((c8 ^ (r & 7)) << 4)) =
                 __float2bfloat16_rn(w);
