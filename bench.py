@@ -36,7 +36,7 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # columns processed): profiles/pass_kernel_sweep_512x512x256.md and
 # profiles/tc_pass_512x512x256.md.
 PASS_TRAFFIC = 2 * (268594432 + 14928640)   # bytes per launch (ncu, 512x512x256 view, x2)
-TC_TRAFFIC = 2 * (134336000 + 3278080)
+TC_TRAFFIC = 2 * (134338048 + 3646208)   # ncu, 512x512x256 view, x2
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
