@@ -387,6 +387,9 @@ static tals_status validate(int dtype, int ndim, const int64_t* dims, const int*
     if (ranks[n] > other)
       return fail(TALS_EINVAL, "ranks[%d] = %d exceeds the product of the other ranks (%lld)", n,
                   ranks[n], other);
+    if (ranks[n] > 64)
+      return fail(TALS_ENOTSUP, "ranks[%d] = %d: the R x R factorizations run in one CTA, R <= 64", n,
+                  ranks[n]);
   }
   return TALS_OK;
 }

@@ -61,3 +61,23 @@ def test_product_path_does_not_touch_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "oracle" not in txt.replace("the oracle", ""), f
+
+
+def test_host_validation_without_a_gpu(lib):
+    # tucker_als_init_owned validates on the host before any CUDA call
+    import ctypes
+    import paper_2004_02583_gb300 as pkg
+
+    def init(dtype, dims, ranks):
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        r = (ctypes.c_int * len(ranks))(*ranks)
+        o = pkg.default_opts()
+        return lib.tucker_als_init_owned(ctypes.byref(h), dtype, len(dims), d, r, ctypes.byref(o), None)
+
+    assert init(pkg.TALS_F32, (10, 9, 8), (11, 2, 2)) == pkg.TALS_EINVAL     # R > I
+    assert init(pkg.TALS_F32, (10, 9, 8), (5, 2, 2)) == pkg.TALS_EINVAL      # R_0 > R_1 R_2
+    assert init(pkg.TALS_F32, (10,), (2,)) == pkg.TALS_EINVAL                # ndim < 2
+    assert init(7, (10, 9, 8), (2, 2, 2)) == pkg.TALS_EINVAL                 # dtype
+    assert init(pkg.TALS_F32, (100, 90, 80), (65, 65, 65)) == pkg.TALS_ENOTSUP   # R > 64
+    assert b"R <= 64" in lib.tals_last_error()
