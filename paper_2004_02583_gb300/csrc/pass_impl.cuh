@@ -84,6 +84,15 @@ __host__ __device__ inline long long tr_slack(long long I, int rowspan) {
   return s > 0 ? (s + 3) / 4 * 4 : 0;
 }
 
+// Step 1 with half-warp row split (FP32, untransposed 16-column tiles, rank
+// chunk 32, 256 threads): a lane holds 4 columns x 8 ranks instead of 4 x 4, so
+// each column value it broadcasts feeds four paired FMAs instead of two; the two
+// half-warps take alternate rows and leave separate partials, doubling the
+// cross-warp reduction buffer.
+__host__ __device__ constexpr bool pass_split_rows(bool f32, bool tr, int rc, int nt, int jt) {
+  return f32 && !tr && rc == 32 && nt == 256 && jt == 16;
+}
+
 template <typename T>
 __host__ __device__ inline size_t pass_smem_bytes(long long I, int RC, int rowspan, int nbuf,
                                                   int nt = kThreads, int jt = kJT, bool tr = false) {
@@ -91,7 +100,8 @@ __host__ __device__ inline size_t pass_smem_bytes(long long I, int RC, int rowsp
   size_t ts = tr ? (size_t)nbuf * jt * tr_pitch(I) + (size_t)tr_slack(I, rowspan)
                  : (size_t)nbuf * ((size_t)I * jtp) + (size_t)slack_rows(I, rowspan) * jtp;
   size_t ls = (size_t)I * RC;
-  size_t wr = (size_t)(nt / 32) * jt * (RC + 4);
+  size_t wr = (size_t)(nt / 32) * jt * (RC + 4) *
+              (pass_split_rows(sizeof(T) == 4, tr, RC, nt, jt) ? 2 : 1);
   size_t ws = (size_t)jt * (RC + 4);
   return (ts + ls + wr + ws) * sizeof(T) + 32 * sizeof(double);
 }
@@ -219,8 +229,10 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
   T* Tbuf = reinterpret_cast<T*>(smem_raw);                                // [nbuf][tile]
   T* Ls = Tbuf + (size_t)a.nbuf * TBS +
           (TR ? (size_t)tr_slack(I, S::ROWT * RPT) : (size_t)slack_rows(I, S::ROWT * RPT) * JTP);  // [I][RC]
-  T* Wred = Ls + (size_t)I * RC;                                           // [NW][JT][WSP]
-  T* Ws = Wred + (size_t)S::NW * JT * WSP;                                // [JT][WSP]
+  constexpr bool SPLIT = pass_split_rows(sizeof(T) == 4, TR, RC, NT, JT);
+  constexpr int NPART = SPLIT ? 2 * S::NW : S::NW;                        // step-1 partial sets
+  T* Wred = Ls + (size_t)I * RC;                                           // [NPART][JT][WSP]
+  T* Ws = Wred + (size_t)NPART * JT * WSP;                                 // [JT][WSP]
   double* red = reinterpret_cast<double*>(Ws + (size_t)JT * WSP);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -316,7 +328,42 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       const T* trow = Tb + cg * 4;
       const T* lrow = Ls + rg * S::RL;
       const int nrow = (int)(ihi - ilo);
-      if constexpr (TR) {
+      if constexpr (SPLIT) {
+        // half-warp h takes rows ilo + h, ilo + h + 2, ...; lane (c4, r8) of the
+        // half holds columns 4 c4 .. 4 c4 + 3 x ranks 8 r8 .. 8 r8 + 7
+        const int half = lane >> 4, c4 = lane & 3, r8 = (lane >> 2) & 3;
+        float2 acc2[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc2[u][v] = make_float2(0.f, 0.f);
+        const float* tp = reinterpret_cast<const float*>(Tb) + ((int)ilo + half) * JTP + c4 * 4;
+        const float* lp = reinterpret_cast<const float*>(Ls) + ((int)ilo + half) * RC + r8 * 8;
+        const int nh = (nrow - half + 1) / 2;
+#pragma unroll 4
+        for (int ii = 0; ii < nh; ++ii) {
+          const float4 t4 = *reinterpret_cast<const float4*>(tp + 2 * ii * JTP);
+          const float4 qa = *reinterpret_cast<const float4*>(lp + 2 * ii * RC);
+          const float4 qb = *reinterpret_cast<const float4*>(lp + 2 * ii * RC + 4);
+          const float2 l2[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w),
+                                make_float2(qb.x, qb.y), make_float2(qb.z, qb.w)};
+          const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 t2 = make_float2(tv[u], tv[u]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+          }
+        }
+        float* wr = reinterpret_cast<float*>(Wred) + (size_t)(2 * warp + half) * JT * WSP;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float* d = wr + (c4 * 4 + u) * WSP + r8 * 8;
+          *reinterpret_cast<float4*>(d) = make_float4(acc2[u][0].x, acc2[u][0].y, acc2[u][1].x, acc2[u][1].y);
+          *reinterpret_cast<float4*>(d + 4) =
+              make_float4(acc2[u][2].x, acc2[u][2].y, acc2[u][3].x, acc2[u][3].y);
+        }
+      } else if constexpr (TR) {
         // transposed tile: this lane's columns are cg + CG u (u = 0..3), so the
         // four column groups of a warp read different bank groups; rows in
         // fours, one float4 along i per column
@@ -438,12 +485,14 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
           }
         }
       }
-      T* wr = Wred + (size_t)warp * JT * WSP;
+      if constexpr (!SPLIT) {
+        T* wr = Wred + (size_t)warp * JT * WSP;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < S::RL; ++v)
-          wr[(TR ? cg + S::CG * u : cg * 4 + u) * WSP + rg * S::RL + v] = acc[u][v];
+          for (int v = 0; v < S::RL; ++v)
+            wr[(TR ? cg + S::CG * u : cg * 4 + u) * WSP + rg * S::RL + v] = acc[u][v];
+      }
       __syncthreads();
       // final W: consecutive threads -> consecutive q (cfast) or consecutive r
       T wsq = T(0);
@@ -452,7 +501,7 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         const int rl = cfast ? (o / JT) : (o % RC);
         T w = T(0);
 #pragma unroll
-        for (int g = 0; g < S::NW; ++g) w += Wred[((size_t)g * JT + c) * WSP + rl];
+        for (int g = 0; g < NPART; ++g) w += Wred[((size_t)g * JT + c) * WSP + rl];
         const int r = r0 + rl;
         const bool valid = (c < ncol) && (r < a.R);
         w = valid ? w : T(0);
