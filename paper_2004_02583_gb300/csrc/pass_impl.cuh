@@ -84,13 +84,13 @@ __host__ __device__ inline long long tr_slack(long long I, int rowspan) {
   return s > 0 ? (s + 3) / 4 * 4 : 0;
 }
 
-// Step 1 with half-warp row split (FP32, untransposed 16-column tiles, rank
-// chunk 32, 256 threads): a lane holds 4 columns x 8 ranks instead of 4 x 4, so
-// each column value it broadcasts feeds four paired FMAs instead of two; the two
-// half-warps take alternate rows and leave separate partials, doubling the
-// cross-warp reduction buffer.
+// Step 1 with half-warp row split (FP32, 16-column tiles, rank chunk 32, 256
+// threads): a lane holds 4 columns x 8 ranks instead of 4 x 4, so each column
+// value it broadcasts feeds four paired FMAs instead of two; the two half-warps
+// take alternate rows (alternate groups of four rows for transposed tiles) and
+// leave separate partials, doubling the cross-warp reduction buffer.
 __host__ __device__ constexpr bool pass_split_rows(bool f32, bool tr, int rc, int nt, int jt) {
-  return f32 && !tr && rc == 32 && nt == 256 && jt == 16;
+  return f32 && rc == 32 && nt == 256 && jt == 16;
 }
 
 template <typename T>
@@ -283,15 +283,15 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
   for (; t < a.ntiles; t += t_step) {
     const long long tn = t + t_step;
     T* Tb = Tbuf + (size_t)buf * TBS;
+    cp_async_wait<0>();
+    // tile t has landed for every thread, and every thread is done with the
+    // previous tile: the other buffer, Wred and Ws are free
+    __syncthreads();
     if (a.nbuf > 1) {
       // stream the next tile into the other buffer while this one is used
       if (tn < a.ntiles) issue_tile<T, JT, TR>(a, tn, Tbuf + (size_t)(buf ^ 1) * TBS);
       cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
     }
-    __syncthreads();
     const long long j0 = t * JT;
     const int ncol = (int)min((long long)JT, a.J - j0);
 
@@ -329,36 +329,66 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
       const T* lrow = Ls + rg * S::RL;
       const int nrow = (int)(ihi - ilo);
       if constexpr (SPLIT) {
-        // half-warp h takes rows ilo + h, ilo + h + 2, ...; lane (c4, r8) of the
-        // half holds columns 4 c4 .. 4 c4 + 3 x ranks 8 r8 .. 8 r8 + 7
+        // half-warp h takes rows ilo + h, ilo + h + 2, ... (transposed tiles:
+        // groups of four rows); lane (c4, r8) of the half holds four columns x
+        // ranks 8 r8 .. 8 r8 + 7
         const int half = lane >> 4, c4 = lane & 3, r8 = (lane >> 2) & 3;
         float2 acc2[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc2[u][v] = make_float2(0.f, 0.f);
-        const float* tp = reinterpret_cast<const float*>(Tb) + ((int)ilo + half) * JTP + c4 * 4;
-        const float* lp = reinterpret_cast<const float*>(Ls) + ((int)ilo + half) * RC + r8 * 8;
-        const int nh = (nrow - half + 1) / 2;
+        if constexpr (TR) {
+          // columns c4 + 4 u, as in the unsplit transposed path
+          const int g0 = (int)ilo + 4 * half;
+          const float* tc = reinterpret_cast<const float*>(Tb) + (long long)c4 * IP + g0;
+          const float* lp = reinterpret_cast<const float*>(Ls) + g0 * RC + r8 * 8;
+          const int nh = (nrow / 4 - half + 1) / 2;
+#pragma unroll 2
+          for (int gg = 0; gg < nh; ++gg) {
+            float4 bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              bv[u] = *reinterpret_cast<const float4*>(tc + (long long)u * 4 * IP + 8 * gg);
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+              const float4 qa = *reinterpret_cast<const float4*>(lp + (8 * gg + r4) * RC);
+              const float4 qb = *reinterpret_cast<const float4*>(lp + (8 * gg + r4) * RC + 4);
+              const float2 l2[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w),
+                                    make_float2(qb.x, qb.y), make_float2(qb.z, qb.w)};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float x = r4 == 0 ? bv[u].x : r4 == 1 ? bv[u].y : r4 == 2 ? bv[u].z : bv[u].w;
+                const float2 t2 = make_float2(x, x);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+              }
+            }
+          }
+        } else {
+          const float* tp = reinterpret_cast<const float*>(Tb) + ((int)ilo + half) * JTP + c4 * 4;
+          const float* lp = reinterpret_cast<const float*>(Ls) + ((int)ilo + half) * RC + r8 * 8;
+          const int nh = (nrow - half + 1) / 2;
 #pragma unroll 4
-        for (int ii = 0; ii < nh; ++ii) {
-          const float4 t4 = *reinterpret_cast<const float4*>(tp + 2 * ii * JTP);
-          const float4 qa = *reinterpret_cast<const float4*>(lp + 2 * ii * RC);
-          const float4 qb = *reinterpret_cast<const float4*>(lp + 2 * ii * RC + 4);
-          const float2 l2[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w),
-                                make_float2(qb.x, qb.y), make_float2(qb.z, qb.w)};
-          const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+          for (int ii = 0; ii < nh; ++ii) {
+            const float4 t4 = *reinterpret_cast<const float4*>(tp + 2 * ii * JTP);
+            const float4 qa = *reinterpret_cast<const float4*>(lp + 2 * ii * RC);
+            const float4 qb = *reinterpret_cast<const float4*>(lp + 2 * ii * RC + 4);
+            const float2 l2[4] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w),
+                                  make_float2(qb.x, qb.y), make_float2(qb.z, qb.w)};
+            const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float2 t2 = make_float2(tv[u], tv[u]);
+            for (int u = 0; u < 4; ++u) {
+              const float2 t2 = make_float2(tv[u], tv[u]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+              for (int v = 0; v < 4; ++v) acc2[u][v] = __ffma2_rn(t2, l2[v], acc2[u][v]);
+            }
           }
         }
         float* wr = reinterpret_cast<float*>(Wred) + (size_t)(2 * warp + half) * JT * WSP;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          float* d = wr + (c4 * 4 + u) * WSP + r8 * 8;
+          float* d = wr + (TR ? c4 + 4 * u : c4 * 4 + u) * WSP + r8 * 8;
           *reinterpret_cast<float4*>(d) = make_float4(acc2[u][0].x, acc2[u][0].y, acc2[u][1].x, acc2[u][1].y);
           *reinterpret_cast<float4*>(d + 4) =
               make_float4(acc2[u][2].x, acc2[u][2].y, acc2[u][3].x, acc2[u][3].y);
@@ -625,12 +655,14 @@ __device__ __forceinline__ double pass_cta(const PassArgs<T>& a, long long t_beg
         }
       }
     }
-    __syncthreads();   // buffer `buf` and Ws fully consumed before they are refilled
     if (a.nbuf > 1) {
       buf ^= 1;
-    } else if (tn < a.ntiles) {
-      issue_tile<T, JT, TR>(a, tn, Tbuf);
-      cp_async_commit();
+    } else {
+      __syncthreads();   // the single buffer fully consumed before it is refilled
+      if (tn < a.ntiles) {
+        issue_tile<T, JT, TR>(a, tn, Tbuf);
+        cp_async_commit();
+      }
     }
   }
   cp_async_wait<0>();

@@ -117,6 +117,22 @@ def test_tolerance_run_f32(tals):
     _cmp((G, Us, st), ref, a64, np.float32, fixed=False)
 
 
+# Rank chunk 32 at I = 300 / 301 selects the 256-thread pass whose step 1 splits
+# each warp's rows between its half-warps: mode 1 (I = 301, untransposed, warp
+# slices of 38 and 35 rows, odd halves) and mode 3 (I = 300, Q = 1: transposed
+# tiles, groups of four rows, the last warp's five groups split 3 / 2)
+@pytest.mark.parametrize("driver", ["st", "t"])
+def test_fixed_sweeps_f32_half_warp_rows(tals, driver):
+    dims, ranks = (301, 20, 300), (24, 6, 20)
+    p = W.planted(W.SEED_BASE + 12, dims, ranks, "gauss", 1e-2, dtype=np.float32)
+    a64 = p.A.astype(np.float64)
+    f = O.st_hosvd_als if driver == "st" else O.t_hosvd_als
+    ref = f(a64, ranks, eta=-1.0, seed=5, max_sweeps=3)
+    g = tals.st_hosvd if driver == "st" else tals.t_hosvd
+    res = g(_gpu(p.A), ranks, eta=-1.0, seed=5, max_sweeps=3)
+    _cmp(res, ref, a64, np.float32, fixed=True)
+
+
 def test_rank_chunked_large_mode(tals):
     # I = 1024 with R = 48: the pass splits the rank into chunks across CTAs.
     # A Gaussian core keeps the subspace well conditioned for an FP32 angle check
