@@ -35,7 +35,7 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # from ncu captures of the 512x512x256 case scaled by 2 (traffic grows with the
 # columns processed): profiles/pass_kernel_sweep_512x512x256.md and
 # profiles/tc_pass_512x512x256.md.
-PASS_TRAFFIC = 2 * (268594432 + 14928640)   # bytes per launch (ncu, 512x512x256 view, x2)
+PASS_TRAFFIC = 2 * (268599552 + 14900480)   # bytes per launch (ncu, 512x512x256 view, x2)
 TC_TRAFFIC = 2 * (134338048 + 3646208)   # ncu, 512x512x256 view, x2
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
@@ -380,9 +380,9 @@ def main():
         "tensor_frac": round(tc_tflops / bf16_peak, 4),
         "peak_source": f"HBM {hbm} GB/s ({peak_kind}); dense BF16 burst {bf16_peak} TFLOP/s ({peak_kind})",
     }
-    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep, plus the
-    # BF16 conversion of each mode that runs tensor-core sweeps
-    launches = sum(10 + 9 * s for s in st["sweeps"]) + sum(1 for b in st["bulk_sweeps"] if b > 0)
+    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep + the factor
+    # copy, plus the BF16 conversion of each mode that runs tensor-core sweeps
+    launches = sum(11 + 9 * s for s in st["sweeps"]) + sum(1 for b in st["bulk_sweeps"] if b > 0)
     mixed_st = st if args.precision == "mixed_bf16" else ost
     plain_st = st if args.precision == "native" else ost
     mixed_ms = ms if args.precision == "mixed_bf16" else o_ms

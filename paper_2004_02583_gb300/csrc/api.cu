@@ -501,8 +501,7 @@ void tals_destroy(tals_ctx* c) {
 // Copy the current orthonormal factor Q (dtype) of a finished mode to U_out.
 static tals_status emit_factor(tals_ctx* c, const ModeJob& j, void* U_out) {
   if (!U_out) return TALS_OK;
-  cudaError_t e = cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz,
-                                  cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = launch_copy(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, c->stream);
   return e == cudaSuccess ? TALS_OK : cuda_fail(e, "factor copy");
 }
 

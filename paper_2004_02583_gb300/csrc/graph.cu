@@ -104,8 +104,7 @@ tals_status capture_mode(tals_ctx* c, ModeJob& j, bool set_norm_a, void* U_out) 
   }
   if ((st = capture_while(c, j, [&] { return mode_sweep_launch(c, j); })) != TALS_OK) return st;
   if (U_out) {
-    cudaError_t e =
-        cudaMemcpyAsync(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, cudaMemcpyDeviceToDevice, cs);
+    cudaError_t e = launch_copy(U_out, c->Lt, (size_t)j.v.I * j.R * c->esz, cs);
     if (e != cudaSuccess) return cuda_fail(e, "factor copy");
   }
   return TALS_OK;

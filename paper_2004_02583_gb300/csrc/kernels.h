@@ -90,6 +90,10 @@ cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, co
                              int op, double* Out, void* OutT, double* Gpart, const RowPlan& rp,
                              const ModeState* st, cudaStream_t s, int gram_rounded = 0);
 
+// Copy `bytes` (a multiple of 4; both pointers 4-byte aligned, else
+// cudaErrorInvalidValue) from src to dst, both in device memory, by a kernel.
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 // Initialise a ModeState (k = 0, flags cleared) on the device. resid: the
 // sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,

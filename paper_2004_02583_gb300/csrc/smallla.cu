@@ -728,6 +728,24 @@ __global__ void transpose_kernel(const T* __restrict__ In, long long rows, long 
   }
 }
 
+// Device-to-device copy by the SMs: keeps the decomposition's graph free of
+// copy-engine work, so that no step of it waits behind a host upload that
+// another stream has queued on a copy engine.
+__global__ void copy_words_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                  size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 3) != 0) return cudaErrorInvalidValue;
+  const size_t n = bytes / 4;
+  const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 1024);
+  copy_words_kernel<<<blocks, 256, 0, s>>>((const uint32_t*)src, (uint32_t*)dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transpose(int dtype, const void* In, long long rows, long long cols, void* Out,
                              cudaStream_t s) {
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
