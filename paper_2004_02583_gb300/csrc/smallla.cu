@@ -531,9 +531,11 @@ cudaError_t launch_small(const double* Gpart, int nb, int R, int op, double* F, 
 // (R <= 64). The factor's rows (forward) and columns (backward) are scaled by
 // the pivot reciprocals once per block; each solved entry is broadcast with a
 // shuffle and every lane updates its own scaled running value, so the
-// dependent chain per row is R steps of one shuffle and one FMA.
+// dependent chain per row is R steps of one shuffle and one FMA. WIDE (R > 32)
+// adds the second column per lane; below that it is not issued at all (a
+// predicated-off FP64 instruction still holds the FP64 pipe).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int R,
                                  const double* __restrict__ F, int op, double* __restrict__ Out,
                                  T* __restrict__ OutT, double* __restrict__ Gpart,
@@ -572,30 +574,32 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
     // as each x_c is broadcast; e_r is final when step r begins, so x_r = e_r and
     // each step's serial chain is one shuffle and one FMA.
     double e0 = j0 < R ? In[i * R + j0] * dinv[j0] : 0.0;
-    double e1 = j1 < R ? In[i * R + j1] * dinv[j1] : 0.0;
+    double e1 = (WIDE && j1 < R) ? In[i * R + j1] * dinv[j1] : 0.0;
     double x0 = 0.0, x1 = 0.0;   // solved entries owned by this lane
     // forward: F x^T = b^T
     for (int r = 0; r < R; ++r) {
       const int owner = r & 31;
-      const double v = __shfl_sync(0xffffffffu, r < 32 ? e0 : e1, owner);
+      const double v = __shfl_sync(0xffffffffu, (!WIDE || r < 32) ? e0 : e1, owner);
       if (lane == owner) {
-        if (r < 32) x0 = v; else x1 = v;
+        if (!WIDE || r < 32) x0 = v; else x1 = v;
       }
       if (j0 > r && j0 < R) e0 = fma(-Ff[j0 * R + r], v, e0);
-      if (j1 > r && j1 < R) e1 = fma(-Ff[j1 * R + r], v, e1);
+      if constexpr (WIDE)
+        if (j1 > r && j1 < R) e1 = fma(-Ff[j1 * R + r], v, e1);
     }
     if (op == 1) {
       // backward: F^T z^T = x^T, z_r = (x_r - sum_{c>r} F[c][r] z_c) / F[r][r]
       e0 = j0 < R ? x0 * dinv[j0] : 0.0;
-      e1 = j1 < R ? x1 * dinv[j1] : 0.0;
+      e1 = (WIDE && j1 < R) ? x1 * dinv[j1] : 0.0;
       for (int r = R - 1; r >= 0; --r) {
         const int owner = r & 31;
-        const double v = __shfl_sync(0xffffffffu, r < 32 ? e0 : e1, owner);
+        const double v = __shfl_sync(0xffffffffu, (!WIDE || r < 32) ? e0 : e1, owner);
         if (lane == owner) {
-          if (r < 32) x0 = v; else x1 = v;
+          if (!WIDE || r < 32) x0 = v; else x1 = v;
         }
         if (j0 < r) e0 = fma(-Fb[r * R + j0], v, e0);
-        if (j1 < r && j1 < R) e1 = fma(-Fb[r * R + j1], v, e1);
+        if constexpr (WIDE)
+          if (j1 < r && j1 < R) e1 = fma(-Fb[r * R + j1], v, e1);
       }
     }
     double* xs = Os + (size_t)lr * R;
@@ -609,7 +613,7 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
       }
       xs[j0] = g;
     }
-    if (j1 < R) {
+    if (WIDE && j1 < R) {
       Out[i * R + j1] = x1;
       double g = x1;
       if (OutT != nullptr) {
@@ -643,42 +647,60 @@ cudaError_t launch_row_solve(int dtype, const double* In, long long I, int R, co
   if (R > 64) return cudaErrorInvalidValue;
   const size_t sm = ((size_t)2 * R * R + R + (size_t)rp.rows_per_block * R) * sizeof(double);
   const int threads = 32 * std::max(1, std::min(8, rp.rows_per_block));
-  if (dtype == 1) {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(row_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm);
-    row_solve_kernel<float><<<rp.blocks, threads, sm, s>>>(In, I, R, F, op, Out, (float*)OutT,
-                                                           Gpart, rp.rows_per_block, st,
-                                                           gram_rounded);
-  } else {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(row_solve_kernel<double>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    row_solve_kernel<double><<<rp.blocks, threads, sm, s>>>(In, I, R, F, op, Out, (double*)OutT,
-                                                            Gpart, rp.rows_per_block, st,
-                                                            gram_rounded);
-  }
-  return cudaGetLastError();
+  auto go = [&](auto kern, auto* outT) {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<rp.blocks, threads, sm, s>>>(In, I, R, F, op, Out, outT, Gpart, rp.rows_per_block, st,
+                                        gram_rounded);
+    return cudaGetLastError();
+  };
+  if (dtype == 1)
+    return R > 32 ? go(row_solve_kernel<float, true>, (float*)OutT)
+                  : go(row_solve_kernel<float, false>, (float*)OutT);
+  return R > 32 ? go(row_solve_kernel<double, true>, (double*)OutT)
+                : go(row_solve_kernel<double, false>, (double*)OutT);
 }
 
 // ---------------------------------------------------------------------------
 // Deterministic multi-CTA sum of Gram partials: Gfin[o] = sum_b Gpart[b][o].
 // ---------------------------------------------------------------------------
+constexpr int kGramSumThreads = 1024;   // 32 groups x 32 entries per block
+
 __global__ void gram_sum_kernel(const double* __restrict__ Gpart, int nb, int RR,
                                 double* __restrict__ Gfin, const ModeState* st, int write32) {
   if (st != nullptr && st->done) return;
-  __shared__ double part[8][33];
-  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;   // 8 groups x 32 entries
+  __shared__ double part[32][33];
+  __shared__ double red[4][33];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int o = blockIdx.x * 32 + lane;
   double s = 0.0;
-  if (o < RR)
-    for (int b = grp; b < nb; b += 8) s += Gpart[(size_t)b * RR + o];
+  if (o < RR) {
+    int b = grp;
+    // four loads in flight, then their sum in order
+    for (; b + 96 < nb; b += 128) {
+      const double v0 = Gpart[(size_t)b * RR + o], v1 = Gpart[(size_t)(b + 32) * RR + o],
+                   v2 = Gpart[(size_t)(b + 64) * RR + o], v3 = Gpart[(size_t)(b + 96) * RR + o];
+      s += v0;
+      s += v1;
+      s += v2;
+      s += v3;
+    }
+    for (; b < nb; b += 32) s += Gpart[(size_t)b * RR + o];
+  }
   part[grp][lane] = s;
   __syncthreads();
-  if (grp == 0 && o < RR) {
+  // fixed-order tree over the 32 groups: four sums of eight, then their sum
+  if (grp < 4) {
     double t = 0.0;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) t += part[g][lane];
+    for (int g = 0; g < 8; ++g) t += part[grp * 8 + g][lane];
+    red[grp][lane] = t;
+  }
+  __syncthreads();
+  if (grp == 0 && o < RR) {
+    const double t = (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]);
     Gfin[o] = t;
     if (write32) reinterpret_cast<float*>(Gfin + RR)[o] = (float)t;   // FP32 copy after the matrix
   }
@@ -687,7 +709,7 @@ __global__ void gram_sum_kernel(const double* __restrict__ Gpart, int nb, int RR
 cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
                             const ModeState* st, cudaStream_t s, int write32) {
   const int RR = R * R;
-  gram_sum_kernel<<<(RR + 31) / 32, 256, 0, s>>>(Gpart, nb, RR, Gfin, st, write32);
+  gram_sum_kernel<<<(RR + 31) / 32, kGramSumThreads, 0, s>>>(Gpart, nb, RR, Gfin, st, write32);
   return cudaGetLastError();
 }
 
