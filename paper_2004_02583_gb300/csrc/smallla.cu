@@ -547,20 +547,16 @@ __global__ void row_solve_kernel(const double* __restrict__ In, long long I, int
   double* dinv = Fb + (size_t)R * R;                 // [R]
   double* Os = dinv + R;                             // [rows_per_block][R]
   // the factor block [C | Ff | Fb | dinv] written by the small kernel: Ff, Fb
-  // and dinv are contiguous, copied as one array
+  // and dinv are contiguous, staged as one array by asynchronous 8-byte copies,
+  // all in flight at once (one round trip to L2 instead of one per batch of loads)
   {
     const double* src = F + (size_t)R * R;
     const int n = 2 * R * R + R;
-    int o = threadIdx.x;
-    for (; o + 3 * (int)blockDim.x < n; o += 4 * blockDim.x) {
-      const double v0 = src[o], v1 = src[o + blockDim.x], v2 = src[o + 2 * blockDim.x],
-                   v3 = src[o + 3 * blockDim.x];
-      sh[o] = v0;
-      sh[o + blockDim.x] = v1;
-      sh[o + 2 * blockDim.x] = v2;
-      sh[o + 3 * blockDim.x] = v3;
-    }
-    for (; o < n; o += blockDim.x) sh[o] = src[o];
+    for (int o = threadIdx.x; o < n; o += blockDim.x)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(sh + o)), "l"(src + o));
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
   }
   __syncthreads();
   if (done) return;
