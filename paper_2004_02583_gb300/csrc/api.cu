@@ -709,11 +709,6 @@ tals_status st_hosvd_host_many(tals_ctx* c, int count, const void* const* A_host
   tals_status result = TALS_OK;
   for (int t = 0; t < count && result == TALS_OK; ++t) {
     const int slot = t & 1;
-    // tensor t+1 crosses the link while tensor t is decomposed
-    if (t + 1 < count && (e = upload(t + 1, slot ^ 1)) != cudaSuccess) {
-      result = cuda_fail(e, "tensor upload");
-      break;
-    }
     if ((e = cudaStreamWaitEvent(c->stream, c->ev_loaded[slot], 0)) != cudaSuccess) {
       result = cuda_fail(e, "upload wait");
       break;
@@ -727,6 +722,13 @@ tals_status st_hosvd_host_many(tals_ctx* c, int count, const void* const* A_host
       if (U_host && U_host[(size_t)t * N + m])
         e = cudaMemcpyAsync(U_host[(size_t)t * N + m], c->pipe_U[slot][m],
                             (size_t)c->dims[m] * c->ranks[m] * c->esz, cudaMemcpyDeviceToHost, c->stream);
+    // tensor t+1 crosses the link while tensor t is decomposed; queued after the
+    // decomposition's launch, so that a host thread held inside a large copy call
+    // still finds the decomposition already running
+    if (e == cudaSuccess && t + 1 < count && (e = upload(t + 1, slot ^ 1)) != cudaSuccess) {
+      result = cuda_fail(e, "tensor upload");
+      break;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       result = cuda_fail(e, "result download");

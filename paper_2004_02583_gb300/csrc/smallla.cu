@@ -186,11 +186,26 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     __shared__ double red[32];
     if (tid == 0) phase_end = 0;
     double c = 0.0;
-    if (GL != nullptr)
-      for (int o = tid; o < R * R; o += kSmallThreads) {
+    if (GL != nullptr) {
+      // a thread's first four entries: their loads issued together, then summed in
+      // the order of the plain loop
+      double g[4], x[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int o = tid + m * kSmallThreads;
+        g[m] = o < R * R ? GL[o] : 0.0;
+        x[m] = o < R * R ? Gpart[o] : 0.0;
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int o = tid + m * kSmallThreads;
+        if (o < R * R) c += (g[m] - (o / R == o % R ? 1.0 : 0.0)) * x[m];
+      }
+      for (int o = tid + 4 * kSmallThreads; o < R * R; o += kSmallThreads) {
         const int r = o / R, q = o % R;
         c += (GL[o] - (r == q ? 1.0 : 0.0)) * Gpart[o];
       }
+    }
     const double corr = block_sum(c, red);
     if (tid == 0) {
       const bool rs = st->resid && op == 1;
@@ -410,16 +425,37 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     }
     __syncthreads();   // every thread is past its last read of S32 before the FP64 reload
   }
-  for (int o = tid; o < R * R; o += kSmallThreads) {
-    const int r = o / R, c = o % R;
-    if (c <= r) {
-      double a = 0.0, b = 0.0;
-      for (int q = 0; q < nb; ++q) {   // nb = 1 after gram_sum
-        a += Gpart[(size_t)q * R * R + r * R + c];
-        b += Gpart[(size_t)q * R * R + c * R + r];
+  if (nb == 1) {
+    // the summed Gram: four entries' loads in flight per thread and round
+    for (int m0 = 0; m0 < R * R; m0 += 4 * kSmallThreads) {
+      double a[4], b[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int o = m0 + tid + m * kSmallThreads;
+        const int r = o / R, c = o % R;
+        const bool in = o < R * R && c <= r;
+        a[m] = in ? Gpart[r * R + c] : 0.0;
+        b[m] = in ? Gpart[c * R + r] : 0.0;
       }
-      // symmetrise (the cross Gram Q^T B B^T Q is symmetric in exact arithmetic)
-      S[r * R + c] = 0.5 * (a + b);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int o = m0 + tid + m * kSmallThreads;
+        const int r = o / R, c = o % R;
+        // symmetrise (the cross Gram Q^T B B^T Q is symmetric in exact arithmetic)
+        if (o < R * R && c <= r) S[r * R + c] = 0.5 * (a[m] + b[m]);
+      }
+    }
+  } else {
+    for (int o = tid; o < R * R; o += kSmallThreads) {
+      const int r = o / R, c = o % R;
+      if (c <= r) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nb; ++q) {
+          a += Gpart[(size_t)q * R * R + r * R + c];
+          b += Gpart[(size_t)q * R * R + c * R + r];
+        }
+        S[r * R + c] = 0.5 * (a + b);
+      }
     }
   }
   if (tid == 0) fail = 0;
