@@ -207,6 +207,19 @@ tals_status project_backward(const void* A, void* const* U, const void* G_bar, i
                              int ndim, const int64_t* dims, const int* ranks, void* A_bar,
                              void* const* U_bar, void* stream);
 
+/* Host only, no CUDA call: the order in which project (expand = 0) or
+ * reconstruct (expand = 1) apply their ndim mode products. A mode product costs
+ * min(I_n, R_n) multiply-adds per element of its larger side (the input of a
+ * contraction, the output of an expansion); the order written to order_out
+ * (host, ndim entries: the modes in the order applied) is the exact minimum of
+ * the summed cost over all ndim! orders, found by dynamic programming over the
+ * subsets of applied modes (ties keep the lower mode first), and *madds_out
+ * (host, may be NULL) receives that minimum. dims and ranks: host, ndim entries.
+ * TALS_EINVAL for ndim outside 1..TALS_MAX_NDIM, a NULL dims, ranks or
+ * order_out, or a size or rank below 1. */
+tals_status tals_mode_product_order(int ndim, const int64_t* dims, const int* ranks, int expand,
+                                    int* order_out, double* madds_out);
+
 /* Batched st-HOSVD-ALS over `count` independent third-order FP32 tensors of
  * uneven sizes. A_ptrs/G_ptrs/U_ptrs are HOST arrays of DEVICE pointers
  * (U_ptrs has 3*count entries: tensor t's factors at 3t, 3t+1, 3t+2); dims and

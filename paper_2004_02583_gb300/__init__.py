@@ -81,6 +81,8 @@ SIGNATURES = {
                                             _IP, _VP, _VPP, _VP]),
     "project_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P, _IP,
                                         _VP, _VPP, _VP]),
+    "tals_mode_product_order": (ctypes.c_int, [ctypes.c_int, _I64P, _IP, ctypes.c_int, _IP,
+                                               ctypes.POINTER(ctypes.c_double)]),
     "tals_batched_st_hosvd": (ctypes.c_int, [ctypes.c_int, _VPP, _I64P, _IP,
                                              ctypes.POINTER(tals_opts), _VPP, _VPP,
                                              ctypes.POINTER(tals_stats), _VP]),
@@ -130,6 +132,18 @@ def selftest_wait_timeout(seconds=0.01, stream=None) -> int:
     nothing arrives at, giving up after `seconds`); returns the status code,
     TALS_ETIMEOUT when the failure path works."""
     return int(lib().tals_selftest_wait_timeout(float(seconds), _stream_ptr(stream)))
+
+
+def mode_product_order(dims, ranks, expand=False):
+    """Order (and multiply-add count) in which project (expand=False) or
+    reconstruct (expand=True) apply their mode products: host only, no GPU."""
+    n = len(dims)
+    d = (ctypes.c_int64 * n)(*[int(x) for x in dims])
+    r = (ctypes.c_int * n)(*[int(x) for x in ranks])
+    out = (ctypes.c_int * n)()
+    madds = ctypes.c_double()
+    _check(lib().tals_mode_product_order(n, d, r, int(bool(expand)), out, ctypes.byref(madds)))
+    return list(out), madds.value
 
 
 def default_opts(**kw) -> tals_opts:

@@ -234,15 +234,15 @@ OpCtx make_ctx(int dtype, int ndim, const int64_t* dims, const int* ranks, void*
 // minimum over all orders is found exactly by dynamic programming over the
 // subsets of modes already applied (N <= 8: at most 256 subsets). Ties keep
 // the lower mode first.
-std::vector<int> shrink_order(const OpCtx& o, bool expand) {
-  const int N = o.N;
+std::vector<int> product_order(int N, const long long* dims, const int* ranks, bool expand,
+                               double* cost) {
   const int full = (1 << N) - 1;
   // elements of the tensor once the modes in `done` are applied
   auto size_of = [&](int done) {
     double v = 1.0;
     for (int m = 0; m < N; ++m) {
       const bool applied = (done >> m) & 1;
-      const double at_rank = (double)o.ranks[m], at_full = (double)o.dims[m];
+      const double at_rank = (double)ranks[m], at_full = (double)dims[m];
       v *= expand ? (applied ? at_full : at_rank) : (applied ? at_rank : at_full);
     }
     return v;
@@ -255,7 +255,7 @@ std::vector<int> shrink_order(const OpCtx& o, bool expand) {
       if (!((done >> m) & 1)) continue;
       const int prev = done & ~(1 << m);
       const double big = expand ? size_of(done) : size_of(prev);
-      const double c = best[prev] + big * (double)std::min<long long>(o.ranks[m], o.dims[m]);
+      const double c = best[prev] + big * (double)std::min<long long>(ranks[m], dims[m]);
       if (c < best[done] * (1.0 - 1e-12)) {
         best[done] = c;
         last[done] = m;
@@ -266,7 +266,12 @@ std::vector<int> shrink_order(const OpCtx& o, bool expand) {
     ord[k] = last[done];
     done &= ~(1 << last[done]);
   }
+  if (cost) *cost = best[full];
   return ord;
+}
+
+std::vector<int> shrink_order(const OpCtx& o, bool expand) {
+  return product_order(o.N, o.dims, o.ranks, expand, nullptr);
 }
 
 tals_status do_project(OpCtx& o, const void* A, void* G_out) {
@@ -357,6 +362,20 @@ tals_status finish(cudaStream_t s) {
 using namespace tals;
 
 extern "C" {
+
+tals_status tals_mode_product_order(int ndim, const int64_t* dims, const int* ranks, int expand,
+                                    int* order_out, double* madds_out) {
+  if (ndim < 1 || ndim > TALS_MAX_NDIM) return fail(TALS_EINVAL, "ndim must be in 1..%d", TALS_MAX_NDIM);
+  if (!dims || !ranks || !order_out) return fail(TALS_EINVAL, "NULL argument");
+  long long d[TALS_MAX_NDIM];
+  for (int m = 0; m < ndim; ++m) {
+    if (dims[m] < 1 || ranks[m] < 1) return fail(TALS_EINVAL, "sizes and ranks must be >= 1");
+    d[m] = dims[m];
+  }
+  const std::vector<int> ord = product_order(ndim, d, ranks, expand != 0, madds_out);
+  std::copy(ord.begin(), ord.end(), order_out);
+  return TALS_OK;
+}
 
 tals_status project(const void* A, void* const* U, int dtype, int ndim, const int64_t* dims,
                     const int* ranks, void* G_out, void* stream) {
