@@ -782,9 +782,10 @@ __global__ void transpose_kernel(const T* __restrict__ In, long long rows, long 
   }
 }
 
-// Device-to-device copy by the SMs: keeps the decomposition's graph free of
-// copy-engine work, so that no step of it waits behind a host upload that
-// another stream has queued on a copy engine.
+// Device-to-device copy by the SMs: leaves the decomposition's graph no
+// copy-engine work before its final small downloads, so that no step in the
+// middle of it can wait behind a host upload queued on a copy engine by
+// another stream.
 __global__ void copy_words_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                   size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
