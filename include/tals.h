@@ -240,6 +240,17 @@ tals_status tals_batched_st_hosvd(int count, void* const* A_ptrs, const int64_t*
 tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, double* bytes,
                            double* flops);
 
+/* Host only, no CUDA call (diagnostics): the configuration of the fused sweep pass
+ * for a mode view P x I x Q (I the mode's size, P and Q the products of the sizes
+ * before and after it) at rank R on a GPU with num_sms SMs. plan_out (host, 10
+ * ints): rank chunk, rows per thread, ranks per thread, threads per CTA, columns
+ * per tile, tile buffers, transposed tile (0/1), dynamic shared memory in bytes,
+ * CTAs along the tiles, rank chunks. TALS_EINVAL for a bad dtype, a size, rank
+ * or SM count below 1 or a NULL plan_out; TALS_ENOTSUP when no configuration
+ * fits in shared memory (above the limits of I_n stated with the error codes). */
+tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, int num_sms,
+                           int* plan_out);
+
 /* Diagnostics (one fused sweep, Eq. 2.2): for the FP32 tensor A (device, dims[ndim])
  * viewed as its mode-`mode` unfolding B and the FP32 basis Q (device, I_mode x R,
  * row-major), write Y = B B^T Q (device, FP64, I_mode x R) and *wnorm2 = ||B^T Q||^2.

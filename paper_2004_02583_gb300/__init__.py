@@ -81,6 +81,8 @@ SIGNATURES = {
                                             _IP, _VP, _VPP, _VP]),
     "project_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P, _IP,
                                         _VP, _VPP, _VP]),
+    "tals_pass_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_int, ctypes.c_int, _IP]),
     "tals_mode_product_order": (ctypes.c_int, [ctypes.c_int, _I64P, _IP, ctypes.c_int, _IP,
                                                ctypes.POINTER(ctypes.c_double)]),
     "tals_batched_st_hosvd": (ctypes.c_int, [ctypes.c_int, _VPP, _I64P, _IP,
@@ -144,6 +146,19 @@ def mode_product_order(dims, ranks, expand=False):
     madds = ctypes.c_double()
     _check(lib().tals_mode_product_order(n, d, r, int(bool(expand)), out, ctypes.byref(madds)))
     return list(out), madds.value
+
+
+def pass_plan(dtype, P, I, Q, R, num_sms=152):
+    """Configuration of the fused sweep pass for a P x I x Q mode view at rank R
+    (host only, no GPU): a dict, or None when no configuration fits."""
+    code = TALS_F32 if dtype in ("f32", "float32", TALS_F32) else TALS_F64
+    out = (ctypes.c_int * 10)()
+    st = lib().tals_pass_plan(code, int(P), int(I), int(Q), int(R), int(num_sms), out)
+    if st == TALS_ENOTSUP:
+        return None
+    _check(st)
+    keys = ("rc", "rpt", "rw", "nt", "jt", "nbuf", "tr", "smem", "grid_x", "grid_y")
+    return dict(zip(keys, list(out)))
 
 
 def default_opts(**kw) -> tals_opts:

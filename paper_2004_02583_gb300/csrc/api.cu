@@ -804,6 +804,19 @@ tals_status als_mode_finish(tals_ctx* c, int mode, void* U_out, int truncate) {
   return e == cudaSuccess ? TALS_OK : cuda_fail(e, "synchronize");
 }
 
+tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, int num_sms,
+                           int* plan_out) {
+  if (dtype != TALS_F32 && dtype != TALS_F64) return fail(TALS_EINVAL, "unsupported dtype %d", dtype);
+  if (P < 1 || I < 1 || Q < 1 || R < 1 || num_sms < 1 || !plan_out)
+    return fail(TALS_EINVAL, "P, I, Q, R and num_sms must be >= 1, plan_out not NULL");
+  const PassConfig pc = pass_config(dtype, ModeView{P, I, Q}, R, num_sms);
+  if (!pc.ok) return fail(TALS_ENOTSUP, "no pass configuration fits I = %lld, R = %d", (long long)I, R);
+  const int plan[10] = {pc.rc, pc.rpt, pc.rw, pc.nt, pc.jt, pc.nbuf, pc.tr ? 1 : 0, (int)pc.smem,
+                        pc.grid_x, pc.grid_y};
+  std::copy(plan, plan + 10, plan_out);
+  return TALS_OK;
+}
+
 tals_status tals_time_pass(tals_ctx* c, int mode, int iters, double* ms, double* bytes,
                            double* flops) {
   if (!c || mode < 0 || mode >= c->N || iters < 1) return fail(TALS_EINVAL, "bad arguments");

@@ -82,12 +82,11 @@ void* lookup(const Inst& in, bool tr) {
 
 }  // namespace
 
-PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
+namespace {
+
+PassConfig pass_config_from(int dtype, const ModeView& v, int R, int num_sms, bool tr) {
   PassConfig cfg;
   const bool f32 = dtype == 1;
-  // views with Q = 1 (the last mode): columns are contiguous rows, staged as a
-  // transposed tile with 16-byte copies (FP32, I a multiple of 4)
-  const bool tr = f32 && v.Q == 1 && v.I % 4 == 0;
   const Inst* tab = tr ? kInstF32Tr : (f32 ? kInstF32 : kInstF64);
   const int ntab = tr ? (int)(sizeof(kInstF32Tr) / sizeof(Inst))
                       : (f32 ? (int)(sizeof(kInstF32) / sizeof(Inst)) : (int)(sizeof(kInstF64) / sizeof(Inst)));
@@ -140,6 +139,20 @@ PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
   gx = std::min(gx, ntiles);
   cfg.grid_x = (int)gx;
   return cfg;
+}
+
+}  // namespace
+
+PassConfig pass_config(int dtype, const ModeView& v, int R, int num_sms) {
+  // views with Q = 1 (the last mode): columns are contiguous rows, staged as a
+  // transposed tile with 16-byte copies (FP32, I a multiple of 4); where no
+  // transposed instantiation fits (I above 1024), the untransposed tile, whose
+  // columns are then copied element by element
+  if (dtype == 1 && v.Q == 1 && v.I % 4 == 0) {
+    const PassConfig cfg = pass_config_from(dtype, v, R, num_sms, true);
+    if (cfg.ok) return cfg;
+  }
+  return pass_config_from(dtype, v, R, num_sms, false);
 }
 
 cudaError_t launch_pass(int dtype, const PassConfig& cfg, int mode, const void* X,

@@ -61,3 +61,35 @@ def test_order_rejects_bad_arguments(pkg):
         pkg.mode_product_order([4, 0, 3], [2, 1, 1])
     with pytest.raises(pkg.TalsError):
         pkg.mode_product_order([2] * 9, [1] * 9)
+
+
+# The fused pass's configuration (host logic, no GPU): every mode size up to the
+# limits the header states (1920 in FP32, 852 in FP64, R <= 64) has a
+# configuration that fits in shared memory, in any view -- including Q = 1
+# views above 1024, where no transposed-tile instantiation fits and the
+# untransposed one takes over -- and the next size up has none.
+@pytest.mark.parametrize("dtype,limit", [("f32", 1920), ("f64", 852)])
+def test_pass_plan_covers_the_stated_limits(pkg, dtype, limit):
+    for R in (1, 5, 8, 16, 17, 32, 33, 64):
+        for Q in (1, 2, 3, 64):
+            for I in sorted({max(R, 1), 100, 512, 1024, 1028, 1280, limit - 1, limit}):
+                if I < R or I > limit:
+                    continue
+                plan = pkg.pass_plan(dtype, 7, I, Q, R)
+                assert plan is not None, (dtype, I, Q, R)
+                assert plan["smem"] <= 227 * 1024
+                assert plan["rc"] * plan["grid_y"] >= R
+                if plan["tr"]:
+                    assert dtype == "f32" and Q == 1 and I % 4 == 0
+            assert pkg.pass_plan(dtype, 7, limit + 1, Q, min(R, 8)) is None
+
+
+def test_pass_plan_of_the_512cube_views(pkg):
+    # the 512^3 st-HOSVD's first view (1 x 512 x 262144) and its last (1024 x 512 x 1)
+    p = pkg.pass_plan("f32", 1, 512, 512 * 512, 32)
+    assert (p["rc"], p["rpt"], p["rw"], p["nt"], p["jt"], p["nbuf"], p["tr"]) == (32, 4, 16, 256, 16, 2, 0)
+    assert p["grid_x"] == 152 and p["grid_y"] == 1
+    p = pkg.pass_plan("f32", 1024, 512, 1, 32)
+    assert p["tr"] == 1 and p["rc"] == 32
+    with pytest.raises(pkg.TalsError):
+        pkg.pass_plan("f32", 0, 512, 1, 32)
