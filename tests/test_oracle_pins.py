@@ -178,6 +178,29 @@ def test_als_one_step_matches_closed_form_E22():
     assert np.allclose(r2.L, l1, rtol=1e-10, atol=1e-12)
 
 
+def test_stop_rule_fires_at_the_first_qualifying_sweep():
+    # Eq. 5.01: the loop ends at the first k >= 1 with |e_{k-1} - e_k| <= eta ||A||_F.
+    # The error sequence comes from a run that never stops (eta < 0); the stop
+    # index is found in it directly, and the stopped run must end exactly there
+    # with the same errors
+    s = np.array([10.0, 9.0, 8.0, 4.0, 2.0, 1.0, 0.5])
+    m, _, _ = _spectral_matrix(30, 60, s, 12)
+    na = np.linalg.norm(m)
+    free = O.als(m, 3, eta=-1.0, norm_a=na, seed=4, max_sweeps=40)
+    assert free.sweeps == 40 and not free.converged
+    d = np.abs(np.diff(np.array(free.errs)))
+    for eta in (1e-3, 1e-6, 1e-9):
+        hits = np.nonzero(d <= eta * na)[0]
+        assert hits.size > 0
+        k_stop = int(hits[0]) + 1                  # d[k-1] = |e_k - e_{k-1}|
+        res = O.als(m, 3, eta=eta, norm_a=na, seed=4, max_sweeps=40)
+        assert res.converged and res.sweeps == k_stop + 1
+        assert res.errs == free.errs[:k_stop + 1]
+    # max_sweeps bounds the loop when the rule never fires
+    res = O.als(m, 3, eta=0.0, norm_a=na, seed=4, max_sweeps=5)
+    assert res.sweeps == 5 and not res.converged
+
+
 def test_als_literal_iteration_is_stationary_at_convergence():
     s = np.array([9.0, 7, 5, 0.01, 0.005])
     m, _, _ = _spectral_matrix(15, 30, s, 7)
