@@ -416,6 +416,48 @@ def test_pins_catch_a_dropped_inverse(monkeypatch):
     assert not np.allclose(r2.L, l1, rtol=1e-6)
 
 
+def test_pins_catch_a_transposed_operand(monkeypatch):
+    """Plant a transposed factor in the mode product (contract X's mode with U's
+    first index instead of its second) and check that the brute-force pin fails."""
+    def transposed(x, u, n):
+        return np.moveaxis(np.tensordot(u, x, axes=([0], [n])), 0, n)
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((3, 4, 5))
+    u = rng.standard_normal((4, 4))                # square, so the shapes still agree
+    monkeypatch.setattr(O, "mode_product", transposed)
+    y = O.mode_product(x, u, 1)
+    monkeypatch.undo()
+    ref = np.zeros((3, 4, 5))
+    for a in range(3):
+        for j in range(4):
+            for c in range(5):
+                ref[a, j, c] = sum(x[a, i, c] * u[j, i] for i in range(4))
+    assert not np.allclose(y, ref, atol=1e-6)
+
+
+def test_pins_catch_a_sign_error_in_an_adjoint(monkeypatch):
+    """Plant a wrong sign in one factor's term of the reconstruction adjoint and
+    check that the finite-difference pin fails."""
+    real = O.reconstruct_vjp
+
+    def broken(g, us, b_bar):
+        gb, ub = real(g, us, b_bar)
+        return gb, [ub[0], -ub[1], ub[2]]
+    rng = np.random.default_rng(22)
+    g = rng.standard_normal((2, 3, 2))
+    us = [rng.standard_normal((d, r)) for d, r in zip((5, 4, 6), (2, 3, 2))]
+    bbar = rng.standard_normal((5, 4, 6))
+    monkeypatch.setattr(O, "reconstruct_vjp", broken)
+    _, ub = O.reconstruct_vjp(g, us, bbar)
+    monkeypatch.undo()
+
+    def fr(x):
+        v = list(us); v[1] = x
+        return float(np.sum(O.reconstruct(g, v) * bbar))
+    with pytest.raises(AssertionError):
+        _fd_check(fr, us[1], ub[1])
+
+
 def test_workload_generator_recipe():
     p = W.planted(5, (10, 9, 8), (3, 2, 4), "inv_k", 1e-2, dtype=np.float64)
     for u in p.factors:
