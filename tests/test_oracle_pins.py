@@ -469,3 +469,20 @@ def test_workload_generator_recipe():
         assert sv[p.core.shape[n]] < 1e-12 * sv[0]
     again = W.planted(5, (10, 9, 8), (3, 2, 4), "inv_k", 1e-2, dtype=np.float64)
     assert np.array_equal(again.A, p.A)
+
+
+def test_batched_workload_recipe():
+    # 4096 uneven third-order tensors: sizes ~ U{16..96}, ranks ~ U{4..16}, every
+    # sequential truncation feasible (R_n <= I_n and R_n <= the product of the others)
+    shapes = W.batched_shapes(W.SEED_BASE + 3, 4096)
+    assert len(shapes) == 4096 and shapes == W.batched_shapes(W.SEED_BASE + 3, 4096)
+    dims = np.array([d for d, _ in shapes])
+    ranks = np.array([r for _, r in shapes])
+    assert dims.min() == 16 and dims.max() == 96 and ranks.min() == 4 and ranks.max() == 16
+    assert np.all(ranks <= dims)
+    for n in range(3):
+        other = np.prod(np.delete(ranks, n, axis=1), axis=1)
+        assert np.all(ranks[:, n] <= other)
+    # the sizes spread over the whole range (not a few repeated shapes)
+    assert len({d for d, _ in shapes}) > 3000
+
