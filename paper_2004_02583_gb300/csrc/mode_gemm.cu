@@ -23,6 +23,7 @@
 // fallback for views the pipelined form does not take (unaligned bases, rows
 // not a multiple of four floats).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "internal.h"
@@ -470,10 +471,14 @@ __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
   }
 }
 
+// Resident CTAs per SM of one instantiation, computed once per process (the
+// attribute and the occupancy query are idempotent, so two threads racing on
+// the first call both store the same value).
 template <bool ROWS, bool MRES, bool RESID, int TA>
 int mg_blocks_per_sm() {
-  static int occ = -1;
-  if (occ < 0) {
+  static std::atomic<int> occ{-1};
+  int v = occ.load(std::memory_order_relaxed);
+  if (v < 0) {
     const size_t smem = mg_smem_floats<ROWS, MRES, TA>() * sizeof(float);
     cudaFuncSetAttribute(mg_pipe<ROWS, MRES, RESID, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
@@ -481,9 +486,10 @@ int mg_blocks_per_sm() {
             cudaSuccess ||
         n < 1)
       n = 1;
-    occ = n;
+    occ.store(n, std::memory_order_relaxed);
+    v = n;
   }
-  return occ;
+  return v;
 }
 
 template <bool ROWS, bool MRES, bool RESID, int TA>
@@ -492,16 +498,17 @@ void mg_run(const MgArgs& a, unsigned grid, cudaStream_t s) {
 }
 
 int mg_sms() {
-  static int sms[64] = {0};
+  static std::atomic<int> sms[64];   // zero-initialised (static storage)
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 152;
-  if (sms[dev] == 0) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int v = sms[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = n > 0 ? n : 152;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    sms[dev].store(n, std::memory_order_relaxed);
+    v = n;
   }
-  return sms[dev];
+  return v;
 }
 
 // The pipelined form's launch for a view; ok = false where it does not apply
