@@ -83,6 +83,13 @@ typedef struct {
   int bulk_sweeps;       /* mixed precision: most BF16 sweeps per mode (default 8) */
   int use_graph;         /* 1 (default): run each mode's sweep loop as one CUDA graph whose
                             device-side while-node evaluates the stop rule; 0: host loop */
+  int fp32_engine;       /* FP32 products: 0 (default) split-precision 3xTF32 on the tcgen05
+                            tensor cores (two passes per sweep; views with Q % 32 == 0,
+                            I <= 1024, R <= 64) for the modes larger than a quarter of the
+                            input and 16M elements, exact FP32 on CUDA cores for the rest;
+                            1 CUDA cores for every mode; 2 tensor cores for every mode whose
+                            view qualifies. A tensor-core mode's reported error is the
+                            explicit residual ||B_(n) - Q W^T|| of its returned pair. */
 } tals_opts;
 
 typedef struct {
@@ -240,6 +247,19 @@ tals_status tals_batched_st_hosvd(int count, void* const* A_ptrs, const int64_t*
 tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, double* bytes,
                            double* flops);
 
+/* Measurement hook (no counterpart in the paper): time the product passes of one
+ * sweep of `mode` on the context's tensor A, `iters` times after one warm-up, with
+ * CUDA events recorded on the context's stream around each launch. engine 0: the
+ * fused FP32 CUDA-core pass; 1: the fused BF16 tensor-core pass (mixed-precision
+ * contexts only); 2: the two split-precision 3xTF32 tensor-core passes.
+ * ms_out[0], bytes_out[0]: mean duration and algorithmic bytes of the first (or
+ * only) pass; ms_out[1], bytes_out[1]: the second pass of engine 2, else 0 (both
+ * host arrays of 2). *flops: FP32-equivalent flops of the sweep (4 R_n prod(I)).
+ * TALS_ENOTSUP when the mode's view is outside the engine's limits. Synchronises
+ * the stream. */
+tals_status tals_time_sweep(tals_ctx* ctx, int mode, int engine, int iters, double* ms_out,
+                            double* bytes_out, double* flops);
+
 /* Host only, no CUDA call (diagnostics): the configuration of the fused sweep pass
  * for a mode view P x I x Q (I the mode's size, P and Q the products of the sizes
  * before and after it) at rank R on a GPU with num_sms SMs. plan_out (host, 10
@@ -251,13 +271,16 @@ tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, doubl
 tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, int num_sms,
                            int* plan_out);
 
-/* Diagnostics (one fused sweep, Eq. 2.2): for the FP32 tensor A (device, dims[ndim])
- * viewed as its mode-`mode` unfolding B and the FP32 basis Q (device, I_mode x R,
- * row-major), write Y = B B^T Q (device, FP64, I_mode x R) and *wnorm2 = ||B^T Q||^2.
+/* Diagnostics (one sweep of products, Eq. 2.2): for the FP32 tensor A (device,
+ * dims[ndim]) viewed as its mode-`mode` unfolding B and the FP32 basis Q (device,
+ * I_mode x R, row-major), write Y = B B^T Q (device, FP64, I_mode x R) and
+ * *wnorm2 = ||B^T Q||^2.
  * engine 0: CUDA-core FP32 pass. engine 1: tensor-core pass (tcgen05, BF16 operands,
  * FP32 accumulation) on a BF16 copy of A; needs I_mode % 128 == 0, I_mode <= 512,
- * prod of the later sizes % 128 == 0 and R <= 64 (else TALS_ENOTSUP). Uses
- * stream-ordered scratch and synchronises the stream. */
+ * prod of the later sizes % 128 == 0 and R <= 64. engine 2: the two split-precision
+ * (3xTF32) tensor-core passes on A itself; needs prod of the later sizes % 32 == 0,
+ * I_mode <= 1024, R <= 64 and a 16-byte aligned A. Shapes outside an engine's limits
+ * return TALS_ENOTSUP. Uses stream-ordered scratch and synchronises the stream. */
 tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mode, const void* Q,
                             int R, int engine, double* Y_out, double* wnorm2, void* stream);
 

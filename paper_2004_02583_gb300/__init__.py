@@ -10,6 +10,7 @@ Tensors are torch CUDA tensors, contiguous, row-major, float32 or float64.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import List, Optional, Sequence
 
@@ -34,7 +35,8 @@ class tals_opts(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("max_sweeps", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("has_order", ctypes.c_int),
                 ("order", ctypes.c_int * MAX_NDIM), ("precision", ctypes.c_int),
-                ("bulk_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("bulk_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("fp32_engine", ctypes.c_int)]
 
 
 class tals_stats(ctypes.Structure):
@@ -92,6 +94,10 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "tals_time_sweep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "tals_sweep_pass": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP, ctypes.c_int,
                                        ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     "tals_sweep_pass_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP,
@@ -169,6 +175,9 @@ def default_opts(**kw) -> tals_opts:
         o.has_order = 1
         for i, n in enumerate(order):
             o.order[i] = int(n)
+    eng = kw.pop("fp32_engine", None)
+    if eng is not None:
+        o.fp32_engine = {"auto": 0, "cuda": 1, "tensor": 2}.get(eng, eng)
     prec = kw.pop("precision", None)
     if prec is not None:
         o.precision = {"native": PREC_NATIVE, "mixed_bf16": PREC_MIXED_BF16}.get(prec, prec)
@@ -202,6 +211,22 @@ def _require_cuda(*ts):
             raise ValueError("tensors must be contiguous")
 
 
+def _expect(t, shape, dtype, what):
+    """ValueError unless tensor t has exactly `shape` and `dtype` (checked before any
+    pointer reaches the library: a mismatch would read or write past a buffer)."""
+    if t is None:
+        return
+    if [int(d) for d in t.shape] != [int(d) for d in shape]:
+        raise ValueError(f"{what}: shape {tuple(t.shape)}, expected {tuple(int(d) for d in shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+
+
+def _host_bytes(t, nbytes, what):
+    if t.numel() * t.element_size() != nbytes or not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous host buffer of {nbytes} bytes")
+
+
 def _stream_ptr(stream=None) -> int:
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -221,7 +246,7 @@ class Context:
     def __init__(self, A, ranks: Sequence[int], eta: float = 1e-4, max_sweeps: int = 50,
                  seed: int = 0, order: Optional[Sequence[int]] = None,
                  precision="native", bulk_sweeps: Optional[int] = None,
-                 use_graph: bool = True, stream=None):
+                 use_graph: bool = True, fp32_engine="auto", stream=None):
         _require_cuda(A)
         self.A = A
         self.ndim = A.dim()
@@ -232,7 +257,7 @@ class Context:
         self._stream = stream
         o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed),
                          order=order, precision=precision, bulk_sweeps=bulk_sweeps,
-                         use_graph=int(bool(use_graph)))
+                         use_graph=int(bool(use_graph)), fp32_engine=fp32_engine)
         self._opts = o
         dims = (ctypes.c_int64 * self.ndim)(*self.dims)
         rk = (ctypes.c_int * self.ndim)(*self.ranks)
@@ -259,6 +284,11 @@ class Context:
         if Us is None:
             Us = [torch.empty((d, r), dtype=self.dtype, device=self.A.device)
                   for d, r in zip(self.dims, self.ranks)]
+        if len(Us) != self.ndim:
+            raise ValueError(f"{self.ndim} factor buffers expected, got {len(Us)}")
+        _expect(G, self.ranks, self.dtype, "G")
+        for n, u in enumerate(Us):
+            _expect(u, (self.dims[n], self.ranks[n]), self.dtype, f"U[{n}]")
         _require_cuda(G, *Us)
         return G, Us
 
@@ -285,12 +315,27 @@ class Context:
 
     def mode_finish(self, mode: int, truncate: bool = True, U=None):
         torch = _torch()
+        if not (0 <= int(mode) < self.ndim):
+            raise ValueError(f"mode {mode} outside 0..{self.ndim - 1}")
         if U is None:
             U = torch.empty((self.dims[mode], self.ranks[mode]), dtype=self.dtype,
                             device=self.A.device)
+        _expect(U, (self.dims[mode], self.ranks[mode]), self.dtype, "U")
+        _require_cuda(U)
         _check(lib().als_mode_finish(self._h, int(mode), U.data_ptr(), int(bool(truncate))))
         return U
 
+
+    def time_sweep(self, mode: int = 0, engine: str = "tf32", iters: int = 10):
+        """Per-pass mean durations (ms) and algorithmic bytes of one sweep's product
+        passes, and the sweep's FP32-equivalent flops. engine: "cuda", "tc" or "tf32"
+        (two passes: W, then Y)."""
+        ms = (ctypes.c_double * 2)()
+        by = (ctypes.c_double * 2)()
+        fl = ctypes.c_double()
+        code = {"cuda": 0, "tc": 1, "tf32": 2}[engine]
+        _check(lib().tals_time_sweep(self._h, int(mode), code, int(iters), ms, by, ctypes.byref(fl)))
+        return list(ms), list(by), fl.value
 
     def time_pass(self, mode: int = 0, iters: int = 10):
         """Mean duration (ms), algorithmic bytes and flops of one sweep pass."""
@@ -321,13 +366,14 @@ class HostContext:
     (the end-to-end path: host->device copy, decomposition, device->host copies)."""
 
     def __init__(self, dims, ranks, dtype="f32", eta=1e-4, max_sweeps=50, seed=0,
-                 precision="native", use_graph=True, stream=None):
+                 precision="native", use_graph=True, fp32_engine="auto", stream=None):
         self.ndim = len(dims)
         self.dims = [int(d) for d in dims]
         self.ranks = [int(r) for r in ranks]
         self._code = TALS_F32 if dtype in ("f32", "float32") else TALS_F64
         o = default_opts(eta=float(eta), max_sweeps=int(max_sweeps), seed=int(seed),
-                         precision=precision, use_graph=int(bool(use_graph)))
+                         precision=precision, use_graph=int(bool(use_graph)),
+                         fp32_engine=fp32_engine)
         d = (ctypes.c_int64 * self.ndim)(*self.dims)
         rk = (ctypes.c_int * self.ndim)(*self.ranks)
         h = ctypes.c_void_p()
@@ -335,8 +381,20 @@ class HostContext:
                                            ctypes.byref(o), _stream_ptr(stream)))
         self._h = h
 
+    def _check_host(self, A_host, G_host, U_host):
+        es = 4 if self._code == TALS_F32 else 8
+        _host_bytes(A_host, math.prod(self.dims) * es, "A_host")
+        _host_bytes(G_host, math.prod(self.ranks) * es, "G_host")
+        if U_host is not None:
+            if len(U_host) != self.ndim:
+                raise ValueError(f"{self.ndim} factor buffers expected, got {len(U_host)}")
+            for n, u in enumerate(U_host):
+                if u is not None:
+                    _host_bytes(u, self.dims[n] * self.ranks[n] * es, f"U_host[{n}]")
+
     def st_hosvd(self, A_host, G_host, U_host):
         """A_host, G_host, U_host: pinned (or pageable) host torch tensors."""
+        self._check_host(A_host, G_host, U_host)
         st = tals_stats()
         _check(lib().st_hosvd_host(self._h, A_host.data_ptr(), G_host.data_ptr(),
                                    _ptrs(U_host), ctypes.byref(st)))
@@ -349,6 +407,8 @@ class HostContext:
         n = len(A_hosts)
         if len(G_hosts) != n or (U_hosts is not None and len(U_hosts) != n):
             raise ValueError("one core (and factor list) per input tensor")
+        for t in range(n):
+            self._check_host(A_hosts[t], G_hosts[t], None if U_hosts is None else U_hosts[t])
         A = (ctypes.c_void_p * n)(*[a.data_ptr() for a in A_hosts])
         G = (ctypes.c_void_p * n)(*[g.data_ptr() for g in G_hosts])
         U = None
@@ -370,18 +430,34 @@ class HostContext:
             pass
 
 
-def _op_args(X, Us):
-    _require_cuda(X, *Us)
+def _op_args(X, Us, x_is="dims"):
+    """Sizes and ranks from the factors (U_n: I_n x R_n), after checking that X has
+    the sizes (x_is="dims") or the ranks (x_is="ranks") and that every factor has
+    X's dtype; ValueError before any pointer reaches the library."""
+    Us = list(Us)
+    if len(Us) != X.dim() or len(Us) < 1:
+        raise ValueError(f"{X.dim()} factors expected, got {len(Us)}")
+    _dtype_code(X)
+    for n, u in enumerate(Us):
+        if u.dim() != 2:
+            raise ValueError(f"U[{n}] must be a matrix, got {u.dim()} dimensions")
+        if u.dtype != X.dtype:
+            raise ValueError(f"U[{n}]: dtype {u.dtype}, expected {X.dtype}")
+    dl = [int(u.shape[0]) for u in Us]
+    rl = [int(u.shape[1]) for u in Us]
+    _expect(X, dl if x_is == "dims" else rl, X.dtype, "tensor")
     ndim = len(Us)
-    dims = (ctypes.c_int64 * ndim)(*[int(u.shape[0]) for u in Us])
-    ranks = (ctypes.c_int * ndim)(*[int(u.shape[1]) for u in Us])
+    dims = (ctypes.c_int64 * ndim)(*dl)
+    ranks = (ctypes.c_int * ndim)(*rl)
     return ndim, dims, ranks
 
 
 def project(A, Us, out=None, stream=None):
     """G = A x_1 U1^T ... x_N UN^T (the core projection of Alg. 1/4)."""
     torch = _torch()
-    ndim, dims, ranks = _op_args(A, Us)
+    ndim, dims, ranks = _op_args(A, Us, "dims")
+    _expect(out, list(ranks), A.dtype, "out")
+    _require_cuda(A, out, *Us)
     G = out if out is not None else torch.empty([int(u.shape[1]) for u in Us], dtype=A.dtype,
                                                  device=A.device)
     _check(lib().project(A.data_ptr(), _ptrs(Us), _dtype_code(A), ndim, dims, ranks,
@@ -392,7 +468,9 @@ def project(A, Us, out=None, stream=None):
 def reconstruct(G, Us, out=None, stream=None):
     """B = G x_1 U1 ... x_N UN (Tucker model)."""
     torch = _torch()
-    ndim, dims, ranks = _op_args(G, Us)
+    ndim, dims, ranks = _op_args(G, Us, "ranks")
+    _expect(out, list(dims), G.dtype, "out")
+    _require_cuda(G, out, *Us)
     B = out if out is not None else torch.empty([int(u.shape[0]) for u in Us], dtype=G.dtype,
                                                  device=G.device)
     _check(lib().reconstruct(G.data_ptr(), _ptrs(Us), _dtype_code(G), ndim, dims, ranks,
@@ -403,8 +481,9 @@ def reconstruct(G, Us, out=None, stream=None):
 def reconstruct_backward(G, Us, B_bar, need_g=True, need_u=True, stream=None):
     """(G_bar, [U_bar_n]) of B = reconstruct(G, Us) for the output gradient B_bar."""
     torch = _torch()
-    ndim, dims, ranks = _op_args(B_bar, Us)
-    _require_cuda(G)
+    ndim, dims, ranks = _op_args(B_bar, Us, "dims")
+    _expect(G, list(ranks), B_bar.dtype, "G")
+    _require_cuda(B_bar, G, *Us)
     G_bar = torch.empty_like(G) if need_g else None
     U_bar = [torch.empty_like(u) for u in Us] if need_u else [None] * ndim
     _check(lib().reconstruct_backward(G.data_ptr(), _ptrs(Us), B_bar.data_ptr(), _dtype_code(G),
@@ -416,8 +495,9 @@ def reconstruct_backward(G, Us, B_bar, need_g=True, need_u=True, stream=None):
 def project_backward(A, Us, G_bar, need_a=True, need_u=True, stream=None):
     """(A_bar, [U_bar_n]) of G = project(A, Us) for the output gradient G_bar."""
     torch = _torch()
-    ndim, dims, ranks = _op_args(A, Us)
-    _require_cuda(G_bar)
+    ndim, dims, ranks = _op_args(A, Us, "dims")
+    _expect(G_bar, list(ranks), A.dtype, "G_bar")
+    _require_cuda(A, G_bar, *Us)
     A_bar = torch.empty_like(A) if need_a else None
     U_bar = [torch.empty_like(u) for u in Us] if need_u else [None] * ndim
     _check(lib().project_backward(A.data_ptr(), _ptrs(Us), G_bar.data_ptr(), _dtype_code(A),
@@ -426,7 +506,17 @@ def project_backward(A, Us, G_bar, need_a=True, need_u=True, stream=None):
     return A_bar, U_bar
 
 
+_AUTOGRAD = None
+
+
 def _autograd():
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD
+
+
+def _make_autograd():
     torch = _torch()
 
     class TalsProject(torch.autograd.Function):
@@ -434,9 +524,10 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, A, *Us):
+            A = A.contiguous()
             Us = [u.contiguous() for u in Us]
             ctx.save_for_backward(A, *Us)
-            return project(A.contiguous(), Us)
+            return project(A, Us)
 
         @staticmethod
         def backward(ctx, G_bar):
@@ -451,9 +542,10 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, G, *Us):
+            G = G.contiguous()
             Us = [u.contiguous() for u in Us]
             ctx.save_for_backward(G, *Us)
-            return reconstruct(G.contiguous(), Us)
+            return reconstruct(G, Us)
 
         @staticmethod
         def backward(ctx, B_bar):
@@ -523,10 +615,20 @@ def batched_st_hosvd(As, ranks, eta=1e-4, max_sweeps=50, seed=0, stream=None):
 
 
 def sweep_pass(A, mode, Q, engine="cuda", stream=None):
-    """One fused sweep pass (diagnostics): returns (Y = B B^T Q in FP64, ||B^T Q||^2)
-    for the mode-`mode` unfolding B of the FP32 tensor A. engine: "cuda" (FP32 CUDA
-    cores) or "tc" (tcgen05 BF16 tensor cores)."""
+    """One sweep of products (diagnostics): returns (Y = B B^T Q in FP64, ||B^T Q||^2)
+    for the mode-`mode` unfolding B of the FP32 tensor A. engine: "cuda" (fused pass,
+    FP32 CUDA cores), "tc" (fused pass, tcgen05 BF16 on a BF16 copy) or "tf32" (two
+    passes, tcgen05 split-precision 3xTF32 on the FP32 tensor); "tf32_w" / "tf32_y"
+    replace the Y or the W pass of "tf32" by the CUDA-core pass (diagnostics)."""
     torch = _torch()
+    if engine not in ("cuda", "tc", "tf32", "tf32_w", "tf32_y"):
+        raise ValueError(f"unknown engine {engine!r}")
+    if A.dtype != torch.float32 or Q.dtype != torch.float32:
+        raise ValueError("sweep_pass needs FP32 A and Q")
+    if not (0 <= int(mode) < A.dim()):
+        raise ValueError(f"mode {mode} outside 0..{A.dim() - 1}")
+    if Q.dim() != 2 or int(Q.shape[0]) != int(A.shape[mode]) or int(Q.shape[1]) < 1:
+        raise ValueError(f"Q must be I_mode x R = {int(A.shape[mode])} x R, got {tuple(Q.shape)}")
     _require_cuda(A, Q)
     ndim = A.dim()
     dims = (ctypes.c_int64 * ndim)(*[int(d) for d in A.shape])
@@ -534,7 +636,8 @@ def sweep_pass(A, mode, Q, engine="cuda", stream=None):
     Y = torch.empty((int(A.shape[mode]), R), dtype=torch.float64, device=A.device)
     w2 = ctypes.c_double()
     _check(lib().tals_sweep_pass(A.data_ptr(), ndim, dims, int(mode), Q.data_ptr(), R,
-                                 {"cuda": 0, "tc": 1}[engine], Y.data_ptr(), ctypes.byref(w2),
+                                 {"cuda": 0, "tc": 1, "tf32": 2, "tf32_w": 3, "tf32_y": 4}[engine],
+                                 Y.data_ptr(), ctypes.byref(w2),
                                  _stream_ptr(stream)))
     return Y, w2.value
 

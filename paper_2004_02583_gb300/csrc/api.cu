@@ -61,7 +61,7 @@ int device_sms() {
 namespace {
 
 struct Need {
-  size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0;
+  size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0, qs = 0;
   void add_mode(int dtype, const ModeView& v, int R, int sms, bool sweep) {
     PassConfig pc = pass_config(dtype, v, R, sms);
     if (!pc.ok) return;
@@ -70,6 +70,15 @@ struct Need {
     RowPlan rp = row_plan(v.I, R, sms);
     gpart = std::max(gpart, (size_t)rp.blocks * (size_t)R * (size_t)R);
     ir = std::max(ir, (size_t)v.I * (size_t)R);
+    if (sweep && dtype == TALS_F32 && t32_supported(v, R)) {
+      // split-precision passes: per-CTA Y partials, W written every sweep (into a
+      // scratch tensor buffer where the mode has no destination), the split basis
+      ypart = std::max(ypart, (size_t)t32_grid(v, 2, sms) * (size_t)v.I * (size_t)R);
+      spart = std::max(spart, (size_t)t32_grid(v, 1, sms) +
+                                  (size_t)t32_grid(v, 2, sms) * (size_t)t32_chunks(v));
+      tbuf = std::max(tbuf, (size_t)(v.J() * R));
+      qs = std::max(qs, t32_basis_floats(v.I, R));
+    }
   }
 };
 
@@ -156,6 +165,12 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     return cuda_fail(e, "workspace clear");
   TALS_AL(c->st, (size_t)TALS_MAX_NDIM * sizeof(ModeState));
   TALS_AL(c->norm_a2, 8 * sizeof(double));
+  if (need.qs > 0) {
+    TALS_AL(c->QS, need.qs * sizeof(float));
+    TALS_AL(c->t32_err, sizeof(int));
+    if ((e = cudaMemsetAsync(c->t32_err, 0, sizeof(int), s)) != cudaSuccess)
+      return cuda_fail(e, "workspace clear");
+  }
 #undef TALS_AL
   if ((e = cudaMallocHost((void**)&c->st_host, TALS_MAX_NDIM * sizeof(ModeState))) != cudaSuccess)
     return cuda_fail(e, "pinned state buffer");
@@ -190,6 +205,27 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // inside the pass: the sweep writes W and a residual kernel takes it
   j.resid_kernel = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr &&
                    mine <= std::max(tot / 4, 16LL << 20);
+  // the full-size FP32 modes: products on the split-precision tensor-core passes,
+  // W written every sweep (the Y pass reads it) to the destination or a scratch
+  // buffer that no other part of the mode uses
+  // (engine 2: every mode whose view qualifies, its error then from the final
+  // explicit residual instead of the per-sweep one)
+  j.t32 = 0;
+  const int eng = c->opts.fp32_engine;
+  const bool want = eng == 2 || (eng == 0 && !j.resid && !j.resid_kernel);
+  if (c->dtype == TALS_F32 && want && c->QS != nullptr && t32_supported(j.v, j.R) &&
+      (uintptr_t)j.X % 16 == 0) {
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    if ((uintptr_t)w % 16 == 0 && w != j.X) {
+      j.t32 = 1;
+      j.resid = 0;
+      j.resid_kernel = 0;
+      j.Wt = w;
+      j.g1 = t32_grid(j.v, 1, c->sms);
+      j.g2 = t32_grid(j.v, 2, c->sms);
+    }
+  }
   return TALS_OK;
 }
 
@@ -208,8 +244,14 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   cudaError_t e;
 #define TALS_CK(x)                                   \
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
-  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid || j.resid_kernel, s,
-                            bulk_max));
+  TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
+                            j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32));
+  if (j.t32) {
+    // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
+    TALS_CK(launch_t32_ypass((const float*)j.X, j.v, R, nullptr, nullptr, (float*)c->Ypart, c->spart,
+                             c->t32_err, j.g2, s, 1, sketch_state(c->opts.seed, j.n), nullptr));
+    return mode_init_tail(c, j, set_norm_a, j.g2, c->spart, j.g2 * t32_chunks(j.v));
+  }
   // Sec. 4: Y0 = B_(n) S and ||B_(n)||^2 in one pass
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_INIT, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr,
                       sketch_state(c->opts.seed, j.n), j.st, 1 << 30, s));
@@ -246,6 +288,18 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   const int R = j.R;
   const long long I = j.v.I;
   cudaError_t e;
+  if (j.t32) {
+    // split-precision passes: W = B^T Q_k (written), then Y = B W with the residual
+    // ||B - Q_k W^T||^2 -- e_k of the stop rule -- from the same read of B
+    const int np = j.g2 * t32_chunks(j.v);
+    TALS_CK(launch_t32_split_basis((const float*)c->Lt, I, R, c->QS, s));
+    TALS_CK(launch_t32_wpass((const float*)j.X, j.v, R, c->QS, (float*)j.Wt, c->spart + np, c->t32_err,
+                             j.g1, s, j.st));
+    TALS_CK(launch_state_sum(c->spart + np, j.g1, j.st, s));
+    TALS_CK(launch_t32_ypass((const float*)j.X, j.v, R, (const float*)c->Lt, (const float*)j.Wt,
+                             (float*)c->Ypart, c->spart, c->t32_err, j.g2, s, 0, 0, j.st));
+    return mode_sweep_tail(c, j, j.g2, np, 1);
+  }
   // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
                       j.Wdest, 0, j.st, j.resid_kernel ? 0 : 1, s, nullptr, j.resid));
@@ -312,11 +366,27 @@ tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters) {
   return TALS_OK;
 }
 
+double t_hosvd_rel_err(const tals_ctx* c, double na2, double g2) {
+  if (!(na2 > 0)) return 0.0;
+  const int N = c->N;
+  // rounded-basis terms of every mode (first-order corrections of ||G||^2)
+  for (int n = 0; n < N; ++n) g2 -= c->st_host[n].corr;
+  const ModeState& last = c->st_host[N - 1];
+  double err2 = na2 - g2;
+  if (last.tc_resid) {
+    // e_N^2 (explicit residual) + ||W_N||^2 (of the stored W_N) - ||G||^2 (a mode
+    // measured by its residual carries no rounded-basis term)
+    err2 = last.e_cur * last.e_cur + last.sw_tc - g2;
+  }
+  return std::sqrt(std::max(err2, 0.0) / na2);
+}
+
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   tals_status st = mode_setup(c, j);
   if (st != TALS_OK) return st;
   if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-  return mode_loop_host(c, j, c->opts.max_sweeps);
+  if ((st = mode_loop_host(c, j, c->opts.max_sweeps)) != TALS_OK) return st;
+  return tc_check(c);
 }
 
 tals_status mode_status(tals_ctx* c, int n) {
@@ -613,10 +683,9 @@ tals_status t_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st
   if (e != cudaSuccess) return cuda_fail(e, "readback");
   double g2 = 0.0;
   for (int i = 0; i < nsp; ++i) g2 += c->host_d[i];
-  for (int n = 0; n < N; ++n) g2 -= c->st_host[n].corr;   // rounded-basis terms of every mode
   const double na2 = c->host_d[nsp];
   local.norm_a = std::sqrt(na2);
-  local.rel_err = na2 > 0 ? std::sqrt(std::max(na2 - g2, 0.0) / na2) : 0.0;
+  local.rel_err = t_hosvd_rel_err(c, na2, g2);
   for (int i = 0; i < N; ++i) local.order[i] = i;
   if (stats) *stats = local;
   return TALS_OK;
@@ -771,6 +840,7 @@ tals_status als_mode_sweep(tals_ctx* c, int mode, int max_iters, double* err_out
     if ((st = mode_sweep_launch(c, ds.job)) != TALS_OK) return st;
   }
   if ((st = read_states(c)) != TALS_OK) return st;
+  if (ds.job.t32 && (st = tc_check(c)) != TALS_OK) return st;
   if ((st = mode_status(c, mode)) != TALS_OK) return st;
   if (err_out) *err_out = c->st_host[mode].e_cur;
   if (converged_out) *converged_out = c->st_host[mode].converged;
@@ -814,6 +884,74 @@ tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, in
   const int plan[10] = {pc.rc, pc.rpt, pc.rw, pc.nt, pc.jt, pc.nbuf, pc.tr ? 1 : 0, (int)pc.smem,
                         pc.grid_x, pc.grid_y};
   std::copy(plan, plan + 10, plan_out);
+  return TALS_OK;
+}
+
+tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double* ms_out,
+                            double* bytes_out, double* flops) {
+  if (!c || mode < 0 || mode >= c->N || iters < 1 || engine < 0 || engine > 2 || !ms_out || !bytes_out)
+    return fail(TALS_EINVAL, "bad arguments");
+  ModeJob j;
+  j.n = mode;
+  j.v = view_of(c->dims, c->N, mode);
+  j.R = c->ranks[mode];
+  j.X = c->A;
+  tals_status st = mode_setup(c, j);
+  if (st != TALS_OK) return st;
+  const double T = (double)j.v.P * j.v.I * j.v.Q;
+  const double JR = (double)j.v.J() * j.R;
+  ms_out[0] = ms_out[1] = bytes_out[0] = bytes_out[1] = 0.0;
+  if (flops) *flops = 4.0 * j.R * T;
+  if (engine == 1) {
+    if (!(c->mixed && c->dtype == TALS_F32 && tc_supported(j.v, j.R)))
+      return fail(TALS_ENOTSUP, "the BF16 tensor-core pass needs a mixed-precision context and its shapes");
+    return time_tc_pass(c, j, iters, &ms_out[0], &bytes_out[0], nullptr);
+  }
+  if (engine == 2 && !(c->dtype == TALS_F32 && c->QS && t32_supported(j.v, j.R) &&
+                       (uintptr_t)j.X % 16 == 0))
+    return fail(TALS_ENOTSUP, "view outside the split-precision pass limits");
+  cudaStream_t s = c->stream;
+  float* W = (float*)c->tbuf[1];
+  cudaEvent_t ev[3];
+  for (auto& x : ev) cudaEventCreate(&x);
+  double acc[2] = {0.0, 0.0};
+  cudaError_t e = cudaSuccess;
+  const int g1 = t32_grid(j.v, 1, c->sms), g2 = t32_grid(j.v, 2, c->sms);
+  const int np = g2 * t32_chunks(j.v);
+  if (engine == 2) e = launch_t32_split_basis((const float*)c->Lt, j.v.I, j.R, c->QS, s);
+  for (int it = -1; it < iters && e == cudaSuccess; ++it) {   // it = -1: warm-up
+    cudaEventRecord(ev[0], s);
+    if (engine == 0) {
+      e = launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, j.R, c->Lt, c->Ypart, c->spart, c->tbuf[0],
+                      0, nullptr, 0, s);
+      cudaEventRecord(ev[1], s);
+    } else {
+      e = launch_t32_wpass((const float*)j.X, j.v, j.R, c->QS, W, c->spart + np, c->t32_err, g1, s);
+      cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess)
+        e = launch_t32_ypass((const float*)j.X, j.v, j.R, (const float*)c->Lt, W, (float*)c->Ypart,
+                             c->spart, c->t32_err, g2, s);
+      cudaEventRecord(ev[2], s);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(engine == 0 ? ev[1] : ev[2]);
+    float t0 = 0.f, t1 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess && engine == 2) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    if (it >= 0) {
+      acc[0] += t0;
+      acc[1] += t1;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "timed sweep");
+  if ((st = tc_check(c)) != TALS_OK) return st;
+  ms_out[0] = acc[0] / iters;
+  bytes_out[0] = T * c->esz + JR * c->esz;   // tensor read + W written
+  if (engine == 2) {
+    ms_out[1] = acc[1] / iters;
+    bytes_out[1] = T * 4.0 + JR * 4.0;       // tensor read + W read (once; its other chunk
+                                             // CTAs find it in L2)
+  }
   return TALS_OK;
 }
 

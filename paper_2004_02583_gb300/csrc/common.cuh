@@ -31,8 +31,10 @@ struct ModeState {
   int bulk_mode;      // 1 while the mixed-precision bulk (BF16) sweeps run
   int kf;             // sweeps of the current (final-precision) phase
   int bulk_max;       // at most this many bulk sweeps
-  int pad2;
+  int tc_resid;       // products on the tensor cores: e_k from the explicit residual, and
+                      // sw_tc holds ||W||^2 of the stored W
   double sw_prev;     // ||W||^2 of the previous bulk sweep
+  double sw_tc;       // tensor-core modes: ||W||^2 of the W last written
 };
 
 // splitmix64 output number c of the stream seeded with `state`:

@@ -241,8 +241,7 @@ tals_status collect(tals_ctx* c, int kind, const GraphEntry* en, tals_stats* sta
   } else {
     double g2 = 0.0;
     for (int i = 0; i < en->nsp; ++i) g2 += c->host_d[i];
-    for (int n = 0; n < N; ++n) g2 -= c->st_host[n].corr;
-    local.rel_err = na2 > 0 ? std::sqrt(std::max(na2 - g2, 0.0) / na2) : 0.0;
+    local.rel_err = t_hosvd_rel_err(c, na2, g2);
     for (int i = 0; i < N; ++i) local.order[i] = i;
   }
   if (stats) *stats = local;

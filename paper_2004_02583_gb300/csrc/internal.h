@@ -22,6 +22,9 @@ struct ModeJob {
   int has_cond = 0;
   int resid = 0;                 // sweeps measure the error from the explicit residual
   int resid_kernel = 0;          // rank split across CTAs: e_k from a residual kernel per sweep
+  int t32 = 0;                   // FP32 sweeps on the split-precision (3xTF32) tensor-core passes
+  void* Wt = nullptr;            // where those passes write W every sweep (Wdest or scratch)
+  int g1 = 0, g2 = 0;            // their grids (W pass CTAs; Y pass column shares per chunk)
 };
 
 struct DriveState {
@@ -48,6 +51,15 @@ tals_status mode_init_tail(tals_ctx* c, const ModeJob& j, bool set_norm_a, int g
 tals_status read_states(tals_ctx* c);
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a);
 tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters);
+// Error flags of the tensor-core passes (BF16 and split-precision).
+tals_status tc_check(tals_ctx* c);
+// t-HOSVD relative error from ||A||^2 (na2), ||G||^2 (g2) and the mode states (read
+// back): ||A - G x U||^2 = ||A||^2 - ||G||^2 corrected by each mode's rounded-basis
+// term; when the last mode ran on the tensor cores, the equivalent
+// e_N^2 + ||A x_N U_N^T||^2 - ||G||^2 with e_N its explicit residual and the norm
+// of the stored A x_N U_N^T, which does not rest on ||A||^2 - ||W||^2 of
+// tensor-core products.
+double t_hosvd_rel_err(const tals_ctx* c, double na2, double g2);
 
 // graph.cu: whole decompositions as one CUDA graph per context and output set
 tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
@@ -125,4 +137,6 @@ struct tals_ctx {
   void* pipe_U[2][TALS_MAX_NDIM] = {};
   tals::GraphCache* graphs = nullptr;
   tals::MixedState* mixed = nullptr;
+  float* QS = nullptr;        // split basis of the split-precision W pass
+  int* t32_err = nullptr;     // error flag of the split-precision passes
 };

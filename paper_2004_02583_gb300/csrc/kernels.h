@@ -96,14 +96,37 @@ cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s
 
 // Initialise a ModeState (k = 0, flags cleared) on the device. resid: the
 // sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
+// tc: the mode's products run on the split-precision tensor-core passes.
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max = 0);
+                              int bulk_max = 0, int tc = 0);
 
 // Tensor-core (tcgen05, BF16) sweep pass; see tc_pass.cu.
 bool tc_supported(const ModeView& v, int R);
 cudaError_t launch_tc_pass(const void* Xb, const ModeView& v, int R, const float* L, float* Ypart,
                            double* spart, int* err, int grid, cudaStream_t s, int init = 0,
                            uint64_t sketch = 0);
+// Split-precision (3xTF32) sweep on tcgen05; see tf32_pass.cu. Views with Q % 32 == 0,
+// I <= 1024, R <= 64.
+bool t32_supported(const ModeView& v, int R);
+// Floats of the split basis buffer of launch_t32_split_basis.
+size_t t32_basis_floats(long long I, int R);
+// CTAs of pass 1 (W), or column shares per 128-row chunk of pass 2 (Y), for a view
+// on `sms` SMs; pass 2 runs t32_chunks(v) x t32_grid(v, 2, sms) CTAs.
+int t32_grid(const ModeView& v, int pass, int sms);
+int t32_chunks(const ModeView& v);
+cudaError_t launch_t32_split_basis(const float* L, long long I, int R, float* QS, cudaStream_t s);
+// Pass 1: W (P x R x Q) = B_(n)^T Q from the split basis QS, ||W||^2 per CTA in spart.
+cudaError_t launch_t32_wpass(const float* X, const ModeView& v, int R, const float* QS, float* W,
+                             double* spart, int* err, int grid, cudaStream_t s,
+                             const ModeState* st = nullptr);
+// Pass 2: Ypart[share] (I x R) = B_(n) W over each column share, and
+// spart[share * chunks + chunk] = ||B - L W^T||^2 partials (L the FP32 basis W was
+// formed with); init: W = the sketch S (L and W unused) and spart = ||B||^2 partials.
+cudaError_t launch_t32_ypass(const float* X, const ModeView& v, int R, const float* L, const float* W,
+                             float* Ypart, double* spart, int* err, int ncol, cudaStream_t s,
+                             int init = 0, uint64_t sketch = 0, const ModeState* st = nullptr);
+// st->sw_tc = sum of n partials (unless the mode is done).
+cudaError_t launch_state_sum(const double* part, int n, ModeState* st, cudaStream_t s);
 // out[p, a, q] = sum_b M[a*sa + b*sb] X[p, b, q] (FP32; cudaErrorNotSupported for
 // views other than Q == 1, Q % 4 == 0 with 16-byte aligned X and out, or Q >= 64).
 cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,

@@ -74,7 +74,8 @@ tals_status mixed_init_launch(tals_ctx* c, ModeJob& j, bool set_norm_a, int grid
   cudaError_t e = launch_to_bf16((const float*)c->A, c->mixed->shadow, c->mixed->shadow_elems, c->sms,
                                  s, c->mixed->sq);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
-  e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid, s, c->opts.bulk_sweeps);
+  e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid || j.t32, s, c->opts.bulk_sweeps,
+                        j.t32);
   if (e == cudaSuccess)
     e = launch_tc_pass(c->mixed->shadow, j.v, j.R, nullptr, (float*)c->Ypart, c->spart,
                        c->mixed->err, grid, s, 1, sketch_state(c->opts.seed, j.n));
@@ -91,22 +92,29 @@ tals_status mixed_bulk_sweep_launch(tals_ctx* c, ModeJob& j, int grid) {
   return mode_sweep_tail(c, j, grid, grid, 2);
 }
 
-tals_status mixed_check(tals_ctx* c) {
-  if (!c->mixed) return TALS_OK;
-  int err = 0;
-  cudaError_t e = cudaMemcpyAsync(&err, c->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+tals_status tc_check(tals_ctx* c) {
+  int err[2] = {0, 0};
+  cudaError_t e = cudaSuccess;
+  if (c->mixed)
+    e = cudaMemcpyAsync(&err[0], c->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && c->t32_err)
+    e = cudaMemcpyAsync(&err[1], c->t32_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core status");
-  if (err) return fail(TALS_ETIMEOUT, "tensor-core pass gave up waiting (code %d)", err);
+  if (err[0] || err[1])
+    return fail(TALS_ETIMEOUT, "a tensor-core pass gave up waiting (code %d)", err[0] ? err[0] : err[1]);
   return TALS_OK;
 }
+
+tals_status mixed_check(tals_ctx* c) { return tc_check(c); }
 
 tals_status run_mode_mixed(tals_ctx* c, ModeJob& j, bool set_norm_a) {
   tals_status st = mode_setup(c, j);
   if (st != TALS_OK) return st;
   if (!mixed_tc_mode(c, j)) {
     if ((st = mode_init_launch(c, j, set_norm_a)) != TALS_OK) return st;
-    return mode_loop_host(c, j, c->opts.max_sweeps);
+    if ((st = mode_loop_host(c, j, c->opts.max_sweeps)) != TALS_OK) return st;
+    return tc_check(c);
   }
   const int grid = mixed_grid(c, j);
   if (grid < 1) return fail(TALS_ENOTSUP, "no room for the tensor-core partials");
@@ -162,7 +170,7 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
                                        const void* Q, int R, int engine, double* Y_out,
                                        double* wnorm2, void* stream) {
   if (!A || !dims || !Q || !Y_out || ndim < 1 || ndim > TALS_MAX_NDIM || mode < 0 || mode >= ndim ||
-      R < 1 || (engine != 0 && engine != 1))
+      R < 1 || engine < 0 || engine > 4)
     return fail(TALS_EINVAL, "bad arguments");
   long long d[TALS_MAX_NDIM];
   size_t n = 1;
@@ -174,13 +182,16 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
   if (R > v.I) return fail(TALS_EINVAL, "R exceeds I");
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
   void* ypart = nullptr;
   double* spart = nullptr;
   void* shadow = nullptr;
   int* err = nullptr;
+  void* wbuf = nullptr;
+  void* qs = nullptr;
+  int sp_off = 0;   // where the ||W||^2 partials start in spart
   int gx = 0, nsp = 0;
   RowPlan rp = row_plan(v.I, R, sms);
   if (engine == 0) {
@@ -192,6 +203,40 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, nsp * sizeof(double), s);
     if (e == cudaSuccess)
       e = launch_pass(TALS_F32, pc, PASS_SWEEP, A, v, R, Q, ypart, spart, nullptr, 0, nullptr, 0, s);
+  } else if (engine >= 2) {
+    if (!t32_supported(v, R)) return fail(TALS_ENOTSUP, "shape outside the split-TF32 pass limits");
+    // engine 3 / 4 (diagnostics): one of the two passes replaced by the CUDA-core
+    // pass (3: tensor-core W, CUDA-core Y; 4: CUDA-core W, tensor-core Y)
+    const PassConfig pc = pass_config(TALS_F32, v, R, sms);
+    if (engine > 2 && !pc.ok) return fail(TALS_ENOTSUP, "shape outside the pass kernel limits");
+    const int g1 = engine == 4 ? pc.grid_x * pc.grid_y : t32_grid(v, 1, sms);
+    const int ncol = t32_grid(v, 2, sms);
+    const int np = std::max(ncol * t32_chunks(v), pc.ok ? pc.grid_x * pc.grid_y : 0);
+    gx = engine == 3 ? pc.grid_x : ncol;
+    nsp = g1;
+    e = cudaMallocAsync(&ypart, (size_t)std::max(gx, ncol) * v.I * R * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, (size_t)(np + g1) * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&wbuf, (size_t)v.J() * R * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&qs, t32_basis_floats(v.I, R) * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_t32_split_basis((const float*)Q, v.I, R, (float*)qs, s);
+    // the W pass's ||W||^2 partials go after the Y pass's partials: spart + np
+    if (e == cudaSuccess) {
+      if (engine == 4)
+        e = launch_pass(TALS_F32, pc, PASS_PROJECT, A, v, R, Q, nullptr, spart + np, wbuf, 0, nullptr, 0, s);
+      else
+        e = launch_t32_wpass((const float*)A, v, R, (const float*)qs, (float*)wbuf, spart + np, err, g1, s);
+    }
+    if (e == cudaSuccess) {
+      if (engine == 3)
+        e = launch_pass(TALS_F32, pc, PASS_GIVEN, A, v, R, nullptr, ypart, spart, nullptr, 0, nullptr, 0,
+                        s, wbuf);
+      else
+        e = launch_t32_ypass((const float*)A, v, R, (const float*)Q, (const float*)wbuf, (float*)ypart,
+                             spart, err, ncol, s);
+    }
+    sp_off = np;
   } else {
     if (!tc_supported(v, R)) return fail(TALS_ENOTSUP, "shape outside the tensor-core pass limits");
     gx = std::min<int>(sms, (int)((v.J() + 127) / 128));
@@ -210,10 +255,10 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
   std::vector<double> sp(nsp);
   int herr = 0;
   if (e == cudaSuccess && nsp > 0)
-    e = cudaMemcpyAsync(sp.data(), spart, nsp * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(sp.data(), spart + sp_off, nsp * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && err) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  for (void* p : {(void*)ypart, (void*)spart, shadow, (void*)err})
+  for (void* p : {(void*)ypart, (void*)spart, shadow, (void*)err, wbuf, qs})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "sweep pass");

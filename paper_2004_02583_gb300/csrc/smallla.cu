@@ -746,8 +746,9 @@ cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
 }
 
 __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int resid,
-                                  int bulk_max) {
+                                  int bulk_max, int tc) {
   ModeState z = {};
+  z.tc_resid = tc;
   z.eta = eta;
   z.max_sweeps = max_sweeps;
   z.resid = resid;
@@ -757,8 +758,8 @@ __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int
 }
 
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max) {
-  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max);
+                              int bulk_max, int tc) {
+  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max, tc);
   return cudaGetLastError();
 }
 
@@ -874,6 +875,22 @@ __global__ void mode_residual_finish(const double* __restrict__ part, long long 
   for (long long k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
   const double tot = block_sum(v, red);
   if (threadIdx.x == 0) st->sW = tot;
+}
+
+// st->sw_tc = sum of n partials (unless the mode is done): ||W||^2 of the W the
+// split-precision W pass stored.
+__global__ void state_sum_kernel(const double* __restrict__ part, int n, ModeState* st) {
+  if (st->done) return;
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += part[k];
+  const double tot = block_sum(v, red);
+  if (threadIdx.x == 0) st->sw_tc = tot;
+}
+
+cudaError_t launch_state_sum(const double* part, int n, ModeState* st, cudaStream_t s) {
+  state_sum_kernel<<<1, 256, 0, s>>>(part, n, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,

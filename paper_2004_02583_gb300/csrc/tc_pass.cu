@@ -29,6 +29,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace tals {
 
@@ -47,135 +48,15 @@ struct TcArgs {
   uint64_t sketch;             // sketch state (seed and mode)
 };
 
+using namespace tc;
+
 namespace {
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// tcgen05 shared-memory matrix descriptor: start, LBO, SBO (bytes), SM100
-// version bit, 128-byte swizzle.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, majors, N, M.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
-                                            int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-      "l"(map), "r"(mbar), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// 2D tensor store from shared memory (bulk-group completion).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                   map),
-               "r"(src), "r"(x), "r"(y)
-               : "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 lanes x 32 columns of fp32 from tensor memory.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+  return idesc(kFmtBF16, M, N, a_mn, b_mn);
 }
 
 }  // namespace
-
-// Clock-bounded wait: gives up after `limit` cycles (setting *fail), or early
-// when another role of the CTA has already failed.
-__device__ __forceinline__ bool mbar_wait_limit(uint32_t mbar, uint32_t parity, volatile int* fail,
-                                                long long limit) {
-  const long long t0 = clock64();
-  while (true) {
-    if (mbar_try(mbar, parity)) return true;
-    if (*fail) return false;
-    if (clock64() - t0 > limit) {
-      *fail = 1;
-      return false;
-    }
-  }
-}
-
-// The pass's waits: about two seconds.
-__device__ __forceinline__ bool mbar_wait_b(uint32_t mbar, uint32_t parity, volatile int* fail) {
-  return mbar_wait_limit(mbar, parity, fail, 4ll << 30);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
 
 // Warp roles (224 threads):
 //   warps 0-3  epilogue: W_t (TMEM) -> bf16 operand and ||W||^2; final Y
@@ -556,14 +437,7 @@ int tc_slots(long long I, int RP) {
   return (int)std::min<size_t>(kMaxSlots, (cap - fixed) / kChunkBytes);
 }
 
-namespace {
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
+EncodeTiledFn tma_encode_fn() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -575,11 +449,9 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-}  // namespace
-
 // Tensor map of a BF16 tensor viewed as (Q, I, P), boxes of 64 x 128 x 1, 128B swizzle.
 bool tc_make_map(const void* Xb, const ModeView& v, CUtensorMap* map) {
-  EncodeTiledFn fn = encode_fn();
+  EncodeTiledFn fn = tma_encode_fn();
   if (!fn) return false;
   if ((uintptr_t)Xb % 16 != 0) return false;
   cuuint64_t dims[3] = {(cuuint64_t)v.Q, (cuuint64_t)v.I, (cuuint64_t)v.P};
@@ -595,7 +467,7 @@ bool tc_make_map(const void* Xb, const ModeView& v, CUtensorMap* map) {
 // Tensor map of the per-CTA FP32 partials Ypart viewed as (R, rows), boxes of
 // 32 x 128 with 128B swizzle (the staging layout of the final Y store).
 bool tc_make_ymap(float* Ypart, int R, long long rows, CUtensorMap* map) {
-  EncodeTiledFn fn = encode_fn();
+  EncodeTiledFn fn = tma_encode_fn();
   if (!fn) return false;
   if ((uintptr_t)Ypart % 16 != 0 || R % 4 != 0) return false;
   cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)rows};

@@ -1,0 +1,909 @@
+// Split-precision (3xTF32) ALS sweep on the 5th-generation tensor cores.
+//
+// The FP32 products of Alg. 3 -- the R-update W = B_(n)^T Q and the L-update
+// Y = B_(n) W, which together form B B^T Q of Eq. 2.2 -- run on tcgen05
+// (kind::tf32) at FP32-level accuracy: every operand x is split as x = hi + lo
+// with hi = tf32(x) and lo = tf32(x - hi) (round to nearest), and a product a b
+// is formed as a_hi b_hi + a_hi b_lo + a_lo b_hi (the omitted a_lo b_lo term is
+// below 2^-22 |a b|), accumulated in FP32 in tensor memory.
+//
+// Two passes per sweep, each streaming the tensor once through TMA:
+//   pass 1 (W pass)  W = B_(n)^T Q. Tiles of 128 unfolding columns (MMA M = 128),
+//                    K = I in stages of 32 rows; the split basis [Q_hi | Q_lo]
+//                    (N = 2 RP) streams beside each stage. The tensor cores
+//                    round each FP32 result toward zero (measured: a relative
+//                    bias of about 3e-8 per accumulating MMA, -4e-6 on ||W||^2
+//                    over K = 512, with sweep-to-sweep noise large enough to
+//                    move the Eq. 5.01 stop rule), so every K-step's products
+//                    land in a fresh tensor-memory buffer, the two correction
+//                    terms in columns of their own, and the epilogue sums them
+//                    in registers with rounding to nearest. W is written
+//                    in the P x R x Q layout, i.e. as the tensor B x_n Q^T
+//                    (Alg. 5's truncation), with ||W||^2.
+//   pass 2 (Y pass)  Y = B_(n) W. Blocks of 32 columns (MMA K), rows in stages of
+//                    128 (MMA M); Y stays in tensor memory for every row of the
+//                    mode and is written once as a per-CTA FP32 partial. In init
+//                    mode the W block is the Sec. 4 sketch S and the pass also
+//                    sums ||B||^2.
+// The split of each staged tile into hi and lo planes runs on four warps of
+// CUDA cores between the TMA landing and the MMAs. The single-read fused form
+// of the BF16 pass does not fit here: a resident FP32 tile at I = 512 beside
+// the split basis exceeds the shared memory of an SM.
+//
+// Views: the mode's unfolding columns j = p Q + q with Q a multiple of 32, so a
+// 32-column box never crosses p; the tensor is read in place through a 3-D map
+// (Q, I, P). Both MMA operands are K-major (kind::tf32 takes no MN-major
+// operand here): pass 1's split step also transposes each landed stage. Warp roles (320 threads): warps 0-3 read tensor memory (W tiles,
+// final Y), warps 4-7 split the staged tiles, warp 8 issues TMA, warp 9 issues
+// the MMAs. Every wait is clock-bounded: on timeout the CTA records
+// TALS_ETIMEOUT, stops issuing, waits (bounded) for its copies and MMAs and
+// frees its tensor memory.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace tals {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kT32Threads = 320;
+constexpr int kMaxStages = 8;
+constexpr int kKC = 32;                      // pass 1: rows per stage (4 MMA K-steps of 8)
+constexpr int kBox1 = 32 * kKC * 4;          // pass 1: one 32-column box, 4 KiB
+constexpr int kStage1 = 4 * kBox1;           // pass 1: 128 columns x 32 rows, 16 KiB
+constexpr int kRows2 = 128;                  // pass 2: rows per stage (MMA M)
+constexpr int kStage2 = 32 * kRows2 * 4;     // pass 2: 32 columns x 128 rows, 16 KiB
+constexpr int kSmemCap = 227 * 1024;
+constexpr int kMaxDB = 4;                    // pass 1: K-step product buffers in tensor memory
+
+struct T32Args {
+  int I, R, RP;
+  long long P, Q, J;
+  int nkc;              // pass 1: stages per tile, ceil(I / 32)
+  int nch;              // pass 2: 128-row chunks, ceil(I / 128) (one per CTA row of the grid)
+  long long ntiles;     // pass 1: 128-column tiles; pass 2: 32-column blocks
+  const float* QS;      // pass 1: split basis, nkc x [2 RP rows][32] (128B-swizzled)
+  const float* L;       // pass 2: the FP32 basis Q (I x R), for the residual
+  float* W;             // pass 1: W (P x R x Q)
+  float* Ypart;         // pass 2: [gridDim.y][I][R]
+  double* spart;        // pass 1: [gridDim.x] ||W||^2; pass 2: [gridDim.y][gridDim.x] the
+                        // residual ||B - Q W^T||^2 (init: ||B||^2)
+  int* err;
+  int init;             // pass 2: W block = sketch S (Sec. 4)
+  uint64_t sketch;
+  const ModeState* st;  // skip the pass once the mode's stop rule has fired (may be null)
+};
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  return p + ((1024u - (su32(p) & 1023u)) & 1023u);
+}
+
+// Exact square x^2 = p + e (FMA) into a Neumaier-compensated FP32 sum.
+__device__ __forceinline__ void acc_sq(float x, float& hi, float& lo) {
+  const float p = x * x, pe = fmaf(x, x, -p);
+  const float t = hi + p;
+  lo += (hi >= p ? (hi - t) + p : (p - t) + hi) + pe;
+  hi = t;
+}
+
+__device__ __forceinline__ float4 split4(float4& x) {
+  float4 l;
+  float h;
+  h = to_tf32(x.x); l.x = to_tf32(x.x - h); x.x = h;
+  h = to_tf32(x.y); l.y = to_tf32(x.y - h); x.y = h;
+  h = to_tf32(x.z); l.z = to_tf32(x.z - h); x.z = h;
+  h = to_tf32(x.w); l.w = to_tf32(x.w - h); x.w = h;
+  return l;
+}
+
+// Split `nf` floats of a staged tile (layout-agnostic: the lo plane has the hi
+// plane's layout) by the 128 split threads (t = 0..127): hi in place, lo beside.
+// With norm, the squares of the original values go into (sh, sl).
+template <int NF>
+__device__ __forceinline__ void split_tile(float* hi, float* lo, int t, bool norm, float& sh,
+                                           float& sl) {
+  static_assert(NF % (128 * 4 * 8) == 0, "tile size");
+#pragma unroll 1
+  for (int e0 = t * 4; e0 < NF; e0 += 128 * 4 * 8) {
+    float4 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const float4*>(hi + e0 + u * 512);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (norm) {
+        acc_sq(x[u].x, sh, sl);
+        acc_sq(x[u].y, sh, sl);
+        acc_sq(x[u].z, sh, sl);
+        acc_sq(x[u].w, sh, sl);
+      }
+      const float4 l = split4(x[u]);
+      *reinterpret_cast<float4*>(hi + e0 + u * 512) = x[u];
+      *reinterpret_cast<float4*>(lo + e0 + u * 512) = l;
+    }
+  }
+}
+
+// Pass-1 stage split with transpose: the stage lands as four TMA boxes of
+// [32 rows i][32 columns] (128B-swizzled, i.e. MN-major for the W product); the
+// split threads rewrite it K-major -- [128 tile columns m][32 rows i], rows of
+// 128 B -- with hi in place of the landed data and lo in the lo plane. Thread
+// t = 32 w + l owns tile column m = t: it reads its 32 values (one 128-byte row
+// of a box per load across the warp, conflict-free), waits until all 128 split
+// threads have read (a bounded mbarrier wait, so a failure elsewhere cannot hang
+// it), then writes 16-byte chunks (4 wavefronts per warp store, the minimum).
+__device__ __forceinline__ bool split_tile_t(unsigned char* st, unsigned char* lo, int t,
+                                             uint32_t rd_bar, uint32_t ph, volatile int* fail) {
+  const int w = t >> 5, l = t & 31;
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    v[k] = *reinterpret_cast<const float*>(st + w * 4096 + k * 128 + ((((l >> 2) ^ (k & 7))) << 4) +
+                                           (l & 3) * 4);
+  mbar_arrive(rd_bar);
+  if (!mbar_wait_b(rd_bar, ph, fail)) return false;
+  const int m = t;
+#pragma unroll
+  for (int kq = 0; kq < 8; ++kq) {
+    float4 x = make_float4(v[4 * kq], v[4 * kq + 1], v[4 * kq + 2], v[4 * kq + 3]);
+    const float4 l4 = split4(x);
+    const uint32_t off = (uint32_t)m * 128u + ((uint32_t)(kq ^ (m & 7)) << 4);
+    *reinterpret_cast<float4*>(st + off) = x;
+    *reinterpret_cast<float4*>(lo + off) = l4;
+  }
+  return true;
+}
+
+// Byte offset of element (row n, column k) in a K-major 128B-swizzled operand
+// whose rows are 128 bytes (32 FP32 values along K).
+__device__ __forceinline__ uint32_t sw_off(int n, int k) {
+  return (uint32_t)n * 128u + ((uint32_t)(((k >> 2) ^ (n & 7))) << 4) + (uint32_t)(k & 3) * 4u;
+}
+
+// FP64 sum of the 128 split threads' compensated pairs (named barrier 1 among
+// them); valid in split thread 0.
+__device__ __forceinline__ double split_sum(float sh, float sl, double* red4, int t) {
+  double v = warp_sum((double)sh + (double)sl);
+  if ((t & 31) == 0) red4[t >> 5] = v;
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  return t == 0 ? red4[0] + red4[1] + red4[2] + red4[3] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: W = B^T Q (3xTF32), ||W||^2
+// ---------------------------------------------------------------------------
+template <int RP>
+__global__ void __launch_bounds__(kT32Threads, 1)
+    t32_wpass_kernel(const __grid_constant__ CUtensorMap bmap, T32Args a, int ns) {
+  if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = align1024(smem_raw);
+  constexpr uint32_t kQB = 2 * RP * 128;            // split basis of one stage
+  constexpr uint32_t kSB = 2 * kStage1 + kQB;       // stage: hi | lo | basis
+  unsigned char* ring = base;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)ns * kSB);
+  uint64_t* full = bars;                      // TMA landed (tx)
+  uint64_t* splt = full + kMaxStages;         // split done (128 arrivals)
+  uint64_t* empty = splt + kMaxStages;        // MMAs done with the stage (commit)
+  uint64_t* rd = empty + kMaxStages;          // split threads have read the stage (128)
+  uint64_t* dfull = rd + kMaxStages;          // [kNB] K-step products ready (commit)
+  uint64_t* dfree = dfull + kMaxDB;           // [kNB] K-step products read out (128 arrivals)
+  uint64_t* alldone = dfree + kMaxDB;         // every MMA done (commit)
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(alldone + 1);
+  __shared__ double red[32];
+  __shared__ int s_fail;
+  volatile int* vfail = &s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long nt =
+      a.ntiles > blockIdx.x ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (tid == 0) {
+    for (int k = 0; k < kMaxStages; ++k) {
+      mbar_init(su32(&full[k]), 1);
+      mbar_init(su32(&splt[k]), 128);
+      mbar_init(su32(&empty[k]), 1);
+      mbar_init(su32(&rd[k]), 128);
+    }
+    for (int b = 0; b < kMaxDB; ++b) {
+      mbar_init(su32(&dfull[b]), 1);
+      mbar_init(su32(&dfree[b]), 128);
+    }
+    mbar_init(su32(alldone), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Tensor memory: kNB buffers of kDS columns, one per K-step in flight, each
+  // [B_hi Q_hi | B_hi Q_lo | B_lo Q_hi] written fresh by the K-step's two MMAs.
+  constexpr int kDS = (3 * RP + 31) / 32 * 32;
+  constexpr int kNB = 512 / kDS < kMaxDB ? 512 / kDS : kMaxDB;
+  constexpr uint32_t kCols = kNB * kDS <= 64 ? 64 : kNB * kDS <= 128 ? 128 : kNB * kDS <= 256 ? 256 : 512;
+  if (warp == 0) tmem_alloc(su32(tmem_holder), kCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_holder;
+  float wsh = 0.f, wsl = 0.f;   // ||W||^2 (epilogue threads)
+
+  if (warp == 8) {
+    // ---------------- producer ----------------
+    long long seq = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const long long t = blockIdx.x + lt * gridDim.x;
+      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
+        const int slot = (int)(seq % ns);
+        const uint32_t ph = (uint32_t)((seq / ns) & 1);
+        ok = mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail);
+        if (!ok) break;
+        if (lane == 0) {
+          unsigned char* st = ring + (size_t)slot * kSB;
+          mbar_expect_tx(su32(&full[slot]), (uint32_t)kStage1 + kQB);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const long long j = t * 128 + 32 * b;
+            long long p = a.P, q = 0;   // past the last column: out of range, zero fill
+            if (j < a.J) {
+              p = j / a.Q;
+              q = j - p * a.Q;
+            }
+            tma_load_3d(su32(st + b * kBox1), &bmap, su32(&full[slot]), (int)q, kc * kKC, (int)p);
+          }
+          bulk_load(su32(st + 2 * kStage1), a.QS + (size_t)kc * (kQB / 4), kQB, su32(&full[slot]));
+        }
+        __syncwarp();
+      }
+    }
+    // every copy issued must have landed before the shared memory is released
+    if (lane == 0) {
+      for (int sl = 0; sl < ns && sl < seq; ++sl) {
+        const long long nfill = seq / ns + (sl < seq % ns ? 1 : 0);
+        mbar_drain(su32(&full[sl]), (uint32_t)((nfill - 1) & 1));
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- split: hi in place, lo beside ----------------
+    const int t = tid - 128;
+    long long seq = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
+        const int slot = (int)(seq % ns);
+        const uint32_t ph = (uint32_t)((seq / ns) & 1);
+        ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+        if (!ok) break;
+        unsigned char* st = ring + (size_t)slot * kSB;
+        ok = split_tile_t(st, st + kStage1, t, su32(&rd[slot]), ph, vfail);
+        if (!ok) break;
+        fence_async_smem();
+        mbar_arrive(su32(&splt[slot]));
+      }
+    }
+  } else if (warp == 9) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t kIdAll = idesc(kFmtTF32, 128, 2 * RP, 0, 0);
+    constexpr uint32_t kIdHi = idesc(kFmtTF32, 128, RP, 0, 0);
+    long long seq = 0, kseq = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
+        const int slot = (int)(seq % ns);
+        const uint32_t ph = (uint32_t)((seq / ns) & 1);
+        ok = mbar_wait_b(su32(&splt[slot]), ph, vfail);
+        if (!ok) break;
+        fence_after();
+        const uint32_t st = su32(ring + (size_t)slot * kSB);
+        for (int ks = 0; ks < kKC / 8 && ok; ++ks, ++kseq) {
+          // every K-step's products go to a fresh buffer; the epilogue adds them up
+          // in registers with rounding to nearest
+          const int b = (int)(kseq % kNB);
+          const uint32_t use = (uint32_t)(kseq / kNB);
+          if (kseq >= kNB) ok = mbar_wait_b(su32(&dfree[b]), (use - 1) & 1u, vfail);
+          if (!ok) break;
+          fence_after();
+          if (lane == 0) {
+            const uint32_t d = tmem + (uint32_t)(b * kDS);
+            // A: K-major (rows = the 128 tile columns, 128 B = 32 rows i), 8 i per step
+            const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
+            const uint64_t alo = desc_sw128(st + kStage1 + ks * 32, 16, 1024);
+            // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]
+            const uint64_t bq = desc_sw128(st + 2 * kStage1 + ks * 32, 16, 1024);
+            mma_tf32(d, ahi, bq, kIdAll, 0u);                  // [B_hi Q_hi | B_hi Q_lo]
+            mma_tf32(d + 2 * RP, alo, bq, kIdHi, 0u);          // B_lo Q_hi
+            mma_commit(su32(&dfull[b]));
+          }
+          __syncwarp();
+        }
+        if (lane == 0) mma_commit(su32(&empty[slot]));
+        __syncwarp();
+      }
+    }
+    if (lane == 0) mma_commit(su32(alldone));
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 0-3, lane = tile column ----------------
+    bool ok = true;
+    const int m = warp * 32 + lane;
+    long long kseq = 0;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      const long long t = blockIdx.x + lt * gridDim.x;
+      float big[RP], small[RP];   // sum of B_hi Q_hi; of the two correction terms
+#pragma unroll
+      for (int k = 0; k < RP; ++k) big[k] = small[k] = 0.f;
+      for (int kc = 0; kc < a.nkc && ok; ++kc) {
+        for (int ks = 0; ks < kKC / 8 && ok; ++ks, ++kseq) {
+          const int b = (int)(kseq % kNB);
+          const uint32_t use = (uint32_t)(kseq / kNB);
+          ok = mbar_wait_b(su32(&dfull[b]), use & 1u, vfail);
+          if (!ok) break;
+          fence_after();
+#pragma unroll
+          for (int cb = 0; cb < kDS; cb += 32) {
+            float t32[32];
+            tmem_ld32(tmem + (uint32_t)(b * kDS + cb) + ((uint32_t)(warp * 32) << 16), t32);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int c = cb + k;
+              if (c < RP) big[c] += t32[k];
+              else if (c < 2 * RP) small[c - RP] += t32[k];
+              else if (c < 3 * RP) small[c - 2 * RP] += t32[k];
+            }
+          }
+          fence_before();
+          mbar_arrive(su32(&dfree[b]));
+        }
+      }
+      if (!ok) break;
+      const long long j = t * 128 + m;
+      if (j < a.J) {
+        const long long p = j / a.Q, q = j - p * a.Q;
+        float* wp = a.W + (size_t)p * a.R * a.Q + q;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          if (r < a.R) {
+            const float w = big[r] + small[r];
+            wp[(size_t)r * a.Q] = w;
+            acc_sq(w, wsh, wsl);
+          }
+        }
+      }
+    }
+  }
+  const double tot = block_sum((double)wsh + (double)wsl, red);
+  if (tid == 0) {
+    a.spart[blockIdx.x] = tot;
+    if (*vfail) atomicExch(a.err, 5);   // TALS_ETIMEOUT
+  }
+  // nothing may still write the shared or tensor memory released below
+  if (*vfail && tid == 288) mbar_drain(su32(alldone), 0u);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: Y = B W and the residual ||B - Q W^T||^2 (3xTF32); init mode: Y0 = B S
+// and ||B||^2.
+//
+// One CTA per (128-row chunk c, share of the 32-column blocks): grid (nch, ncol).
+// The chunk's rows of the split basis Q_c stay in shared memory; each stage
+// brings one block of B (128 rows x 32 columns) and, by TMA as well, the block's
+// W (R x 32). Per stage:
+//   P = Q_c W_blk^T (M = 128, N = 32, K = R)       -> tensor memory
+//   split warps: residual sum (B - P)^2 of the stage, then B -> hi / lo
+//   Y_c += B_blk W_blk (M = 128, N = R, K = 32)    -> tensor memory per K-step,
+//                                                    summed in registers
+// The residual is the stop rule's e_k^2 (Eq. 5.01) without cancellation: every
+// tensor-core result carries a relative error of order 1e-7 (the products of
+// each K = 8 step are aligned and truncated), so ||B||^2 - ||W||^2 would carry
+// noise of order 1e-8 ||B||^2, while an error dP in P moves the residual only
+// by 2 <B - P, dP> + ||dP||^2, both far below FP32 resolution of e^2 (the
+// residual is orthogonal to P up to the error of W). The chunk's W blocks are
+// read by all nch chunk CTAs of a column share at about the same time, so W
+// mostly comes from L2.
+// Warp roles: warps 0-3 prepare the W block (split for the Y product, transposed
+// and split for the residual product) and write Y at the end; warps 4-7 take the
+// residual and split B (lane = row of the chunk = tensor-memory lane); warp 8
+// issues TMA; warp 9 issues the MMAs.
+// ---------------------------------------------------------------------------
+// Pass 2, warps 0-3: prepare the W block of stage lt once it has landed -- split
+// for the Y product (hi in place, lo RP rows further on; init: the sketch block
+// S, Sec. 4) and, with the residual, transposed and split for the P product.
+template <int RP>
+__device__ __forceinline__ bool t32_prep_w(const T32Args& a, unsigned char* ring, uint32_t kSB, int ns,
+                                           long long lt, long long col, long long ncol, uint64_t* full,
+                                           uint64_t* wrdy, int t, volatile int* vfail, bool resid) {
+  constexpr uint32_t kW2 = 2u * RP * 128u;
+  const int slot = (int)(lt % ns);
+  const uint32_t ph = (uint32_t)((lt / ns) & 1);
+  if (!mbar_wait_b(su32(&full[slot]), ph, vfail)) return false;
+  const long long j0 = (col + lt * ncol) * 32;
+  unsigned char* w2 = ring + (size_t)slot * kSB + 2 * kStage2;
+  unsigned char* w3 = w2 + kW2;
+  for (int e = t; e < 32 * a.R; e += 128) {
+    const int r = e >> 5, q = e & 31;
+    const float x = a.init ? sketch_entry(a.sketch, (uint64_t)(j0 + q), a.R, r)
+                           : *reinterpret_cast<const float*>(w2 + sw_off(r, q));
+    const float h = to_tf32(x), l = to_tf32(x - h);
+    *reinterpret_cast<float*>(w2 + sw_off(r, q)) = h;
+    *reinterpret_cast<float*>(w2 + sw_off(RP + r, q)) = l;
+    if (resid) {
+      const uint32_t kb = (uint32_t)(r >> 5) * (64u * 128u);
+      *reinterpret_cast<float*>(w3 + kb + sw_off(q, r & 31)) = h;
+      *reinterpret_cast<float*>(w3 + kb + sw_off(32 + q, r & 31)) = l;
+    }
+  }
+  fence_async_smem();
+  mbar_arrive(su32(&wrdy[slot]));
+  return true;
+}
+
+template <int RP>
+__global__ void __launch_bounds__(kT32Threads, 1)
+    t32_ypass_kernel(const __grid_constant__ CUtensorMap bmap, const __grid_constant__ CUtensorMap wmap,
+                     T32Args a, int ns) {
+  if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = align1024(smem_raw);
+  constexpr int KB = (RP + 31) / 32;                  // 32-wide blocks of the rank (K of P)
+  constexpr uint32_t kQP = 128u * KB * 128u;          // one plane of Q_c: K-major, 128 rows
+  constexpr uint32_t kW2 = 2u * RP * 128u;            // W block, Y product: rows [W_hi | W_lo]
+  constexpr uint32_t kW3 = 64u * KB * 128u;           // W block, P product: rows [q hi | q lo]
+  constexpr uint32_t kSB = 2u * kStage2 + kW2 + kW3;  // stage: B hi | B lo | W2 | W3
+  unsigned char* qhi = base;
+  unsigned char* qlo = qhi + kQP;
+  unsigned char* ring = qlo + kQP;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)ns * kSB);
+  uint64_t* full = bars;                      // B (and W) landed (tx)
+  uint64_t* wrdy = full + kMaxStages;         // W block prepared (128 arrivals)
+  uint64_t* splt = wrdy + kMaxStages;         // residual taken, B split (128 arrivals)
+  uint64_t* empty = splt + kMaxStages;        // MMAs done with the stage (commit)
+  uint64_t* pready = empty + kMaxStages;      // [2] P in tensor memory (commit)
+  uint64_t* pfree = pready + 2;               // [2] P read out (128 arrivals)
+  uint64_t* yfull = pfree + 2;                // [kYB] K-step products of Y ready (commit)
+  uint64_t* yfree = yfull + kMaxDB;           // [kYB] K-step products read out (128 arrivals)
+  uint64_t* qready = yfree + kMaxDB;          // Q_c operands written (128 arrivals)
+  uint64_t* ydone = qready + 1;               // every MMA done (commit)
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(ydone + 1);
+  __shared__ double red4[4];
+  __shared__ int s_fail;
+  volatile int* vfail = &s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chunk = blockIdx.x;
+  const long long ncol = gridDim.y, col = blockIdx.y;
+  const long long nt = a.ntiles > col ? (a.ntiles - col + ncol - 1) / ncol : 0;
+  const bool resid = !a.init;
+  if (tid == 0) {
+    for (int k = 0; k < kMaxStages; ++k) {
+      mbar_init(su32(&full[k]), 1);
+      mbar_init(su32(&wrdy[k]), 128);
+      mbar_init(su32(&splt[k]), 128);
+      mbar_init(su32(&empty[k]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(su32(&pready[b]), 1);
+      mbar_init(su32(&pfree[b]), 128);
+    }
+    for (int b = 0; b < kMaxDB; ++b) {
+      mbar_init(su32(&yfull[b]), 1);
+      mbar_init(su32(&yfree[b]), 128);
+    }
+    mbar_init(su32(qready), 128);
+    mbar_init(su32(ydone), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // W blocks: rows beyond R (and the K columns beyond R of the P operand) are read
+  // by the MMAs and never written: zero every stage's W regions once
+  for (int sl = 0; sl < ns; ++sl) {
+    uint4* w = reinterpret_cast<uint4*>(ring + (size_t)sl * kSB + 2 * kStage2);
+    for (int e = tid; e < (int)((kW2 + kW3) / 16); e += kT32Threads) w[e] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  fence_async_smem();
+  // Tensor memory: kYB buffers of kYS columns for the K-steps of the Y product in
+  // flight, each [B_hi W_hi | B_hi W_lo | B_lo W_hi] written fresh (the tensor
+  // cores round each result toward zero; accumulated in tensor memory over a whole
+  // pass, that bias varies from row to row and tilts the weakest directions of the
+  // basis), summed in registers by warps 0-3; P buffers at 384 and 448.
+  constexpr int kYS = (3 * RP + 31) / 32 * 32;
+  constexpr int kYB = 384 / kYS < kMaxDB ? 384 / kYS : kMaxDB;
+  constexpr uint32_t kCols = 512;
+  constexpr uint32_t kPCol = 384;
+  if (warp == 0) tmem_alloc(su32(tmem_holder), kCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 8) {
+    // ---------------- producer ----------------
+    long long seq = 0;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
+      const long long j = (col + lt * ncol) * 32;
+      const long long p = j / a.Q, q = j - p * a.Q;
+      const int slot = (int)(seq % ns);
+      const uint32_t ph = (uint32_t)((seq / ns) & 1);
+      ok = mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail);
+      if (!ok) break;
+      if (lane == 0) {
+        unsigned char* st = ring + (size_t)slot * kSB;
+        mbar_expect_tx(su32(&full[slot]), (uint32_t)kStage2 + (resid ? (uint32_t)a.R * 128u : 0u));
+        tma_load_3d(su32(st), &bmap, su32(&full[slot]), (int)q, chunk * kRows2, (int)p);
+        if (resid) tma_load_3d(su32(st + 2 * kStage2), &wmap, su32(&full[slot]), (int)q, 0, (int)p);
+      }
+      __syncwarp();
+    }
+    if (lane == 0)
+      for (int sl = 0; sl < ns && sl < seq; ++sl) {
+        const long long nfill = seq / ns + (sl < seq % ns ? 1 : 0);
+        mbar_drain(su32(&full[sl]), (uint32_t)((nfill - 1) & 1));
+      }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ---------------- W preparation (t = row of Q_c in the prologue) ----------------
+    const int t = tid;
+    if (resid) {
+      // Q_c: rows chunk*128 + t of the basis, split, K-major with 32-wide K blocks
+      const long long i = (long long)chunk * kRows2 + t;
+      for (int r = 0; r < 32 * KB; ++r) {
+        const float x = (i < a.I && r < a.R) ? a.L[i * a.R + r] : 0.f;
+        const float h = to_tf32(x);
+        const uint32_t off = (uint32_t)(r >> 5) * 16384u + sw_off(t, r & 31);
+        *reinterpret_cast<float*>(qhi + off) = h;
+        *reinterpret_cast<float*>(qlo + off) = to_tf32(x - h);
+      }
+      fence_async_smem();
+      mbar_arrive(su32(qready));
+    }
+    bool ok = true;
+    float big[RP], small[RP];   // Y of this row: B_hi W_hi; the two correction terms
+#pragma unroll
+    for (int k = 0; k < RP; ++k) big[k] = small[k] = 0.f;
+    if (nt > 0) ok = t32_prep_w<RP>(a, ring, kSB, ns, 0, col, ncol, full, wrdy, t, vfail, resid);
+    long long kseq = 0;
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      // the next block's W first, so the P product of the next stage can start
+      if (lt + 1 < nt) ok = t32_prep_w<RP>(a, ring, kSB, ns, lt + 1, col, ncol, full, wrdy, t, vfail, resid);
+      for (int ks = 0; ks < 4 && ok; ++ks, ++kseq) {
+        const int b = (int)(kseq % kYB);
+        ok = mbar_wait_b(su32(&yfull[b]), (uint32_t)((kseq / kYB) & 1), vfail);
+        if (!ok) break;
+        fence_after();
+#pragma unroll
+        for (int cb = 0; cb < kYS; cb += 32) {
+          float t32[32];
+          tmem_ld32(tmem + (uint32_t)(b * kYS + cb) + ((uint32_t)(warp * 32) << 16), t32);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int c = cb + k;
+            if (c < RP) big[c] += t32[k];
+            else if (c < 2 * RP) small[c - RP] += t32[k];
+            else if (c < 3 * RP) small[c - 2 * RP] += t32[k];
+          }
+        }
+        fence_before();
+        mbar_arrive(su32(&yfree[b]));
+      }
+    }
+    // final Y of the chunk: lane = row
+    if (ok && nt > 0) {
+      const long long i = (long long)chunk * kRows2 + warp * 32 + lane;
+      if (i < a.I) {
+        float* yp = a.Ypart + ((size_t)col * a.I + i) * a.R;
+#pragma unroll
+        for (int r = 0; r < RP; ++r)
+          if (r < a.R) yp[r] = big[r] + small[r];
+      }
+    }
+  } else if (warp < 8) {
+    // ---------------- residual and split: lane = row of the chunk ----------------
+    const int t = tid - 128;   // row of the chunk; tensor-memory lane quadrant warp % 4
+    long long seq = 0;
+    bool ok = true;
+    float sh = 0.f, sl = 0.f;   // residual sum (init: ||B||^2)
+    for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
+      const int slot = (int)(seq % ns);
+      const uint32_t ph = (uint32_t)((seq / ns) & 1);
+      ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+      if (!ok) break;
+      float pv[32];
+      if (resid) {
+        const int pb = (int)(seq & 1);
+        ok = mbar_wait_b(su32(&pready[pb]), (uint32_t)((seq >> 1) & 1), vfail);
+        if (!ok) break;
+        fence_after();
+        float p1[32];
+        const uint32_t tp = tmem + kPCol + (uint32_t)(pb * 64) + ((uint32_t)((warp & 3) * 32) << 16);
+        tmem_ld32(tp, pv);
+        tmem_ld32(tp + 32u, p1);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) pv[k] += p1[k];
+        fence_before();
+        mbar_arrive(su32(&pfree[pb]));
+      }
+      unsigned char* st = ring + (size_t)slot * kSB;
+      unsigned char* row = st + t * 128;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        // chunk c4 of the row holds columns 4 c4 .. 4 c4 + 3
+        const uint32_t off = (uint32_t)((c4 ^ (t & 7)) << 4);
+        float4 x = *reinterpret_cast<const float4*>(row + off);
+        if (resid) {
+          acc_sq(x.x - pv[4 * c4], sh, sl);
+          acc_sq(x.y - pv[4 * c4 + 1], sh, sl);
+          acc_sq(x.z - pv[4 * c4 + 2], sh, sl);
+          acc_sq(x.w - pv[4 * c4 + 3], sh, sl);
+        } else {
+          acc_sq(x.x, sh, sl);
+          acc_sq(x.y, sh, sl);
+          acc_sq(x.z, sh, sl);
+          acc_sq(x.w, sh, sl);
+        }
+        const float4 l = split4(x);
+        *reinterpret_cast<float4*>(row + off) = x;
+        *reinterpret_cast<float4*>(row + kStage2 + off) = l;
+      }
+      fence_async_smem();
+      mbar_arrive(su32(&splt[slot]));
+    }
+    const double tot = split_sum(sh, sl, red4, t);
+    if (t == 0) a.spart[(size_t)col * gridDim.x + chunk] = tot;
+  } else {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t kIdY2 = idesc(kFmtTF32, 128, 2 * RP, 0, 0);
+    constexpr uint32_t kIdY1 = idesc(kFmtTF32, 128, RP, 0, 0);
+    constexpr uint32_t kIdP2 = idesc(kFmtTF32, 128, 64, 0, 0);
+    constexpr uint32_t kIdP1 = idesc(kFmtTF32, 128, 32, 0, 0);
+    bool ok = !resid || mbar_wait_b(su32(qready), 0u, vfail);
+    long long seq = 0, kseq = 0;
+    for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
+      const int slot = (int)(seq % ns);
+      const uint32_t ph = (uint32_t)((seq / ns) & 1);
+      ok = mbar_wait_b(su32(&wrdy[slot]), ph, vfail);
+      if (!ok) break;
+      fence_after();
+      const uint32_t st = su32(ring + (size_t)slot * kSB);
+      const uint32_t w2 = st + 2 * kStage2, w3 = w2 + kW2;
+      if (resid) {
+        // P = Q_c W^T: [Q_hi W_hi^T | Q_hi W_lo^T] (N = 64) and Q_lo W_hi^T into the first half
+        const int pb = (int)(seq & 1);
+        if (seq >= 2) ok = mbar_wait_b(su32(&pfree[pb]), (uint32_t)(((seq >> 1) - 1) & 1), vfail);
+        if (!ok) break;
+        fence_after();
+        if (lane == 0) {
+          const uint32_t d = tmem + kPCol + (uint32_t)(pb * 64);
+#pragma unroll
+          for (int ks = 0; ks < RP / 8; ++ks) {
+            const uint32_t kq = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
+            const uint32_t kw = (uint32_t)(ks >> 2) * (64u * 128u) + (uint32_t)(ks & 3) * 32u;
+            const uint64_t ah = desc_sw128(su32(qhi) + kq, 16, 1024);
+            const uint64_t al = desc_sw128(su32(qlo) + kq, 16, 1024);
+            const uint64_t bw = desc_sw128(w3 + kw, 16, 1024);
+            mma_tf32(d, ah, bw, kIdP2, ks ? 1u : 0u);
+            mma_tf32(d, al, bw, kIdP1, 1u);
+          }
+          mma_commit(su32(&pready[pb]));
+        }
+        __syncwarp();
+      }
+      ok = mbar_wait_b(su32(&splt[slot]), ph, vfail);
+      if (!ok) break;
+      fence_after();
+      for (int ks = 0; ks < 4 && ok; ++ks, ++kseq) {
+        const int b = (int)(kseq % kYB);
+        if (kseq >= kYB) ok = mbar_wait_b(su32(&yfree[b]), (uint32_t)((kseq / kYB - 1) & 1), vfail);
+        if (!ok) break;
+        fence_after();
+        if (lane == 0) {
+          const uint32_t d = tmem + (uint32_t)(b * kYS);
+          const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
+          const uint64_t alo = desc_sw128(st + kStage2 + ks * 32, 16, 1024);
+          const uint64_t bw = desc_sw128(w2 + ks * 32, 16, 1024);
+          mma_tf32(d, ahi, bw, kIdY2, 0u);                 // [B_hi W_hi | B_hi W_lo]
+          mma_tf32(d + 2 * RP, alo, bw, kIdY1, 0u);        // B_lo W_hi
+          mma_commit(su32(&yfull[b]));
+        }
+        __syncwarp();
+      }
+      if (ok && lane == 0) mma_commit(su32(&empty[slot]));
+      __syncwarp();
+    }
+    if (lane == 0) mma_commit(su32(ydone));
+    __syncwarp();
+  }
+  if (tid == 0 && *vfail) atomicExch(a.err, 5);   // TALS_ETIMEOUT
+  if (*vfail && tid == 288) mbar_drain(su32(ydone), 0u);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// Split basis for pass 1: QS[kc] = rows [hi(Q[32kc + k][r]) for r < RP | lo(...)]
+// of 32 values along k, 128B-swizzled (the K-major B operand layout), zero
+// beyond I and R.
+__global__ void t32_split_basis_kernel(const float* __restrict__ L, int I, int R, int RP, int nkc,
+                                       float* __restrict__ QS) {
+  const long long per = (long long)2 * RP * 32;
+  const long long total = (long long)nkc * per;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int kc = (int)(e / per);
+    const int rem = (int)(e - kc * per);
+    const int n = rem >> 5, k = rem & 31;
+    const int i = kc * 32 + k;
+    float v = 0.f;
+    if (i < I) {
+      if (n < R) {
+        v = to_tf32(L[(size_t)i * R + n]);
+      } else if (n >= RP && n - RP < R) {
+        const float x = L[(size_t)i * R + (n - RP)];
+        v = to_tf32(x - to_tf32(x));
+      }
+    }
+    QS[(size_t)kc * per + (sw_off(n, k) >> 2)] = v;
+  }
+}
+
+template <int RP>
+size_t smem1(int ns) {
+  return 1024 + (size_t)ns * (2 * kStage1 + 2 * RP * 128) + (4 * kMaxStages + 2 * kMaxDB + 1) * 8 + 16;
+}
+template <int RP>
+size_t smem2(int ns) {
+  constexpr size_t KB = (RP + 31) / 32;
+  const size_t stage = 2 * (size_t)kStage2 + 2 * RP * 128 + 64 * KB * 128;
+  return 1024 + 2 * (128 * KB * 128) + (size_t)ns * stage + (4 * kMaxStages + 6 + 2 * kMaxDB) * 8 + 16;
+}
+
+int rp_of(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 48 ? 48 : 64; }
+
+int stages1(int RP) {
+  const size_t static_smem = 2048;
+  for (int ns = kMaxStages; ns >= 2; --ns) {
+    size_t s = RP == 16 ? smem1<16>(ns) : RP == 32 ? smem1<32>(ns) : RP == 48 ? smem1<48>(ns) : smem1<64>(ns);
+    if (s + static_smem <= (size_t)kSmemCap) return ns;
+  }
+  return 0;
+}
+int stages2(int RP) {
+  const size_t static_smem = 2048;
+  for (int ns = kMaxStages; ns >= 2; --ns) {
+    size_t s = RP == 16 ? smem2<16>(ns) : RP == 32 ? smem2<32>(ns) : RP == 48 ? smem2<48>(ns) : smem2<64>(ns);
+    if (s + static_smem <= (size_t)kSmemCap) return ns;
+  }
+  return 0;
+}
+
+// 3-D FP32 map of the view (Q, I, P) or of W (Q, R, P), boxes (32, rows, 1), 128B swizzle.
+bool make_map(const void* X, long long Q, long long rows, long long P, int box_rows, CUtensorMap* map) {
+  EncodeTiledFn fn = tma_encode_fn();
+  if (!fn) return false;
+  if ((uintptr_t)X % 16 != 0) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Q, (cuuint64_t)rows, (cuuint64_t)P};
+  cuuint64_t strides[2] = {(cuuint64_t)Q * 4, (cuuint64_t)rows * Q * 4};
+  cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(X), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool t32_supported(const ModeView& v, int R) {
+  if (R < 1 || R > 64 || v.Q % 32 != 0 || v.I < 1 || v.I > 1024) return false;
+  if (v.P > 0x7fffffffLL || v.Q > 0x7fffffffLL || v.I > 0x7fffffffLL) return false;
+  const int RP = rp_of(R);
+  return stages1(RP) >= 2 && stages2(RP) >= 2;
+}
+
+size_t t32_basis_floats(long long I, int R) {
+  return (size_t)((I + kKC - 1) / kKC) * 2 * rp_of(R) * 32;
+}
+
+int t32_grid(const ModeView& v, int pass, int sms) {
+  if (pass == 1) return (int)std::max<long long>(1, std::min<long long>(sms, (v.J() + 127) / 128));
+  // pass 2: column shares per 128-row chunk (about one CTA per SM in all)
+  const long long nch = (v.I + kRows2 - 1) / kRows2;
+  return (int)std::max<long long>(1, std::min<long long>(std::max<long long>(1, sms / nch), v.J() / 32));
+}
+
+int t32_chunks(const ModeView& v) { return (int)((v.I + kRows2 - 1) / kRows2); }
+
+cudaError_t launch_t32_split_basis(const float* L, long long I, int R, float* QS, cudaStream_t s) {
+  const int RP = rp_of(R);
+  const int nkc = (int)((I + kKC - 1) / kKC);
+  const long long total = (long long)nkc * 2 * RP * 32;
+  const int blocks = (int)std::min<long long>(1024, (total + 255) / 256);
+  t32_split_basis_kernel<<<blocks, 256, 0, s>>>(L, (int)I, R, RP, nkc, QS);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_t32_wpass(const float* X, const ModeView& v, int R, const float* QS, float* W,
+                             double* spart, int* err, int grid, cudaStream_t s, const ModeState* st) {
+  if (!t32_supported(v, R) || !W || !QS) return cudaErrorInvalidValue;
+  CUtensorMap bmap;
+  if (!make_map(X, v.Q, v.I, v.P, kKC, &bmap)) return cudaErrorInvalidValue;
+  const int RP = rp_of(R);
+  T32Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.I = (int)v.I;
+  a.R = R;
+  a.RP = RP;
+  a.P = v.P;
+  a.Q = v.Q;
+  a.J = v.J();
+  a.nkc = (int)((v.I + kKC - 1) / kKC);
+  a.nch = (int)((v.I + kRows2 - 1) / kRows2);
+  a.ntiles = (v.J() + 127) / 128;
+  a.QS = QS;
+  a.W = W;
+  a.spart = spart;
+  a.err = err;
+  a.st = st;
+  grid = (int)std::max<long long>(1, std::min<long long>(grid, a.ntiles));
+  int ns = stages1(RP);
+  void* fn = nullptr;
+  size_t smem = 0;
+  switch (RP) {
+    case 16: fn = (void*)&t32_wpass_kernel<16>; smem = smem1<16>(ns); break;
+    case 32: fn = (void*)&t32_wpass_kernel<32>; smem = smem1<32>(ns); break;
+    case 48: fn = (void*)&t32_wpass_kernel<48>; smem = smem1<48>(ns); break;
+    default: fn = (void*)&t32_wpass_kernel<64>; smem = smem1<64>(ns); break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&bmap, &a, (void*)&ns};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kT32Threads), args, smem, s);
+}
+
+cudaError_t launch_t32_ypass(const float* X, const ModeView& v, int R, const float* L, const float* W,
+                             float* Ypart, double* spart, int* err, int ncol, cudaStream_t s, int init,
+                             uint64_t sketch, const ModeState* st) {
+  if (!t32_supported(v, R) || (!init && (!W || !L))) return cudaErrorInvalidValue;
+  CUtensorMap bmap, wmap;
+  if (!make_map(X, v.Q, v.I, v.P, kRows2, &bmap)) return cudaErrorInvalidValue;
+  std::memset(&wmap, 0, sizeof(wmap));
+  if (!init && !make_map(W, v.Q, R, v.P, R, &wmap)) return cudaErrorInvalidValue;
+  const int RP = rp_of(R);
+  T32Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.I = (int)v.I;
+  a.R = R;
+  a.RP = RP;
+  a.P = v.P;
+  a.Q = v.Q;
+  a.J = v.J();
+  a.nkc = (int)((v.I + kKC - 1) / kKC);
+  a.nch = t32_chunks(v);
+  a.ntiles = v.J() / 32;
+  a.L = L;
+  a.Ypart = Ypart;
+  a.spart = spart;
+  a.err = err;
+  a.init = init;
+  a.sketch = sketch;
+  a.st = st;
+  ncol = (int)std::max<long long>(1, std::min<long long>(ncol, a.ntiles));
+  int ns = stages2(RP);
+  void* fn = nullptr;
+  size_t smem = 0;
+  switch (RP) {
+    case 16: fn = (void*)&t32_ypass_kernel<16>; smem = smem2<16>(ns); break;
+    case 32: fn = (void*)&t32_ypass_kernel<32>; smem = smem2<32>(ns); break;
+    case 48: fn = (void*)&t32_ypass_kernel<48>; smem = smem2<48>(ns); break;
+    default: fn = (void*)&t32_ypass_kernel<64>; smem = smem2<64>(ns); break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&bmap, &wmap, &a, (void*)&ns};
+  return cudaLaunchKernel(fn, dim3(a.nch, ncol), dim3(kT32Threads), args, smem, s);
+}
+
+}  // namespace tals
