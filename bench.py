@@ -31,12 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at equal error"
-# DRAM bytes (read + write) per launch of the two passes on the 512^3 mode-1 view,
-# from ncu captures of the 512x512x256 case scaled by 2 (traffic grows with the
-# columns processed): profiles/pass_kernel_sweep_512x512x256.md and
-# profiles/tc_pass_512x512x256.md.
-PASS_TRAFFIC = 2 * (268599552 + 14900480)   # bytes per launch (ncu, 512x512x256 view, x2)
-TC_TRAFFIC = 2 * (134338048 + 3646208)   # ncu, 512x512x256 view, x2
+# DRAM bytes (read + write) per launch on the 512^3 mode-1 view, from ncu captures of
+# the 512x512x256 case scaled by 2 (traffic grows with the columns processed); None
+# where no capture of the current kernel exists.
+PASS_TRAFFIC = 2 * (268599552 + 14900480)   # CUDA-core FP32 fused pass
+TC_TRAFFIC = 2 * (134338048 + 3646208)      # BF16 tensor-core fused pass
+T32_TRAFFIC = {"w": None, "y": None}        # split-precision W and Y passes
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
@@ -295,18 +295,57 @@ def main():
     oev1.record(stream)
     torch.cuda.synchronize()
     o_ms = oev0.elapsed_time(oev1) / args.steps
-    # re-run the timed path once so G and U hold its result
-    _, _, st = ctx.st_hosvd(G, Us)
     nctx = ctx if args.precision == "native" else octx
     mctx = ctx if args.precision == "mixed_bf16" else octx
 
-    # dominant kernel (largest share of the step in both paths): the CUDA-core FP32
-    # sweep pass over the full tensor (mode-1 view), timed with CUDA events on the
-    # stream it is launched on, same configuration as inside the step
-    pass_ms, pass_bytes, pass_flops = nctx.time_pass(mode=st["order"][0], iters=10)
-    # the tensor-core BF16 pass of the mixed path's bulk sweeps
-    tc_ms, tc_bytes, tc_flops = mctx.time_pass(mode=st["order"][0], iters=10)
+    def timed(fn, n):
+        for _ in range(2):
+            out = fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n, out
+
+    # the plain FP32 path with its products on the CUDA cores (exact FP32 FMA), the
+    # previous form of the plain path
+    cctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision="native", fp32_engine="cuda",
+                        use_graph=not args.no_graph)
+    cuda_ms, (_, _, cst) = timed(lambda: cctx.st_hosvd(G, Us), max(3, args.steps // 2))
+    # t-HOSVD-ALS (Alg. 4) on the same input, both precision paths
+    t_ms, t_rel = {}, {}
+    for name, c in (("fp32_plain", nctx), ("mixed", mctx)):
+        t_ms[name], (_, _, tst) = timed(lambda: c.t_hosvd(G, Us), max(3, args.steps // 2))
+        t_rel[name] = tst["rel_err"]
+    # re-run the timed path once so G and U hold its result
+    _, _, st = ctx.st_hosvd(G, Us)
+
+    # dominant kernels: the split-precision passes of the FP32 sweeps (W pass, then the
+    # Y pass with the residual) over the full tensor (mode-1 view), timed with CUDA
+    # events on the stream they are launched on, in the configuration of the step
+    mode0 = st["order"][0]
+    t32_ms, t32_bytes, t32_flops = nctx.time_sweep(mode=mode0, engine="tf32", iters=10)
+    # the exact-FP32 CUDA-core fused pass and the BF16 tensor-core pass, same view
+    pass_ms, pass_bytes, pass_flops = nctx.time_pass(mode=mode0, iters=5)
+    tc_ms, tc_bytes, tc_flops = mctx.time_pass(mode=mode0, iters=10)
     octx_close = octx.close
+    cctx.close()
+    # the metric's own mixed-vs-plain comparison at equal error on the 128^4 workload
+    c3cfg = W.CONFIGS["q128_f32"]
+    A3 = torch.from_numpy(W.make(c3cfg).A).cuda()
+    G3 = torch.empty(c3cfg.ranks, device="cuda")
+    U3 = [torch.empty((d, r), device="cuda") for d, r in zip(c3cfg.dims, c3cfg.ranks)]
+    c3 = {}
+    for prec in ("mixed_bf16", "native"):
+        c = tals.Context(A3, c3cfg.ranks, eta=c3cfg.eta, seed=1, precision=prec,
+                         use_graph=not args.no_graph)
+        c3[prec] = timed(lambda: c.st_hosvd(G3, U3), max(3, args.steps // 2))
+        c.close()
+    del A3
 
     # end to end through the C ABI with host buffers (H2D of A, D2H of G and U)
     e_ms, e_single_ms, h2d, d2h = None, None, 0, 0
@@ -345,27 +384,39 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    # split-precision passes (HBM roofline): the dominant one is the headline roofline
+    names = {"w": "tals::t32_wpass_kernel<32> (split-precision W = B^T Q on tcgen05 kind::tf32)",
+             "y": "tals::t32_ypass_kernel<32> (split-precision Y = B W and the residual "
+                  "||B - Q W^T||^2 on tcgen05 kind::tf32)"}
+    passes = {}
+    for k, i in (("w", 0), ("y", 1)):
+        gbs = t32_bytes[i] / (t32_ms[i] * 1e-3) / 1e9
+        passes[k] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbs / hbm, 4), "traffic": T32_TRAFFIC[k], "kernel": names[k],
+                     "algorithmic_bytes": t32_bytes[i], "pass_ms": round(t32_ms[i], 4)}
+    dom = "y" if t32_ms[1] >= t32_ms[0] else "w"
+    roofline = dict(passes[dom])
+    roofline["peak_source"] = f"HBM {hbm} GB/s ({peak_kind}; the pass is timed alone)"
+    roofline["view"] = "mode-1 view 1 x 512 x 262144, rank 32; the largest share of both paths' steps"
+    sweep_ms = t32_ms[0] + t32_ms[1]
+    roofline["sweep"] = {"ms": round(sweep_ms, 4),
+                         "gbs": round((t32_bytes[0] + t32_bytes[1]) / (sweep_ms * 1e-3) / 1e9, 1),
+                         "fp32_equivalent_tflops": round(t32_flops / (sweep_ms * 1e-3) / 1e12, 2),
+                         "other_pass": passes["w" if dom == "y" else "y"]}
     achieved_gbs = pass_bytes / (pass_ms * 1e-3) / 1e9
     achieved_tflops = pass_flops / (pass_ms * 1e-3) / 1e12
     # CUDA-core pass: 152 SMs x 128 FP32 FMA x 2 flops x SM clock (an ALU roofline)
     alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    comp_frac = achieved_tflops / alu_peak
-    hbm_frac = achieved_gbs / hbm
-    roofline = {
-        "bound": "alu",
-        "achieved": round(achieved_tflops, 2),
-        "peak": round(alu_peak, 2),
-        "unit": "TFLOP/s",
-        "frac": round(comp_frac, 4),
-        "traffic": PASS_TRAFFIC,
-        "kernel": "tals::pass_kernel<float,32,4,16,256> (CUDA-core FP32 fused sweep, mode-1 view "
-                  "1 x 512 x 262144; the largest share of the step in both precision paths)",
+    roofline_cuda = {
+        "bound": "alu", "achieved": round(achieved_tflops, 2), "peak": round(alu_peak, 2),
+        "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 4), "traffic": PASS_TRAFFIC,
+        "kernel": "tals::pass_kernel<float,32,4,16,256> (exact-FP32 CUDA-core fused sweep, same view; "
+                  "the plain path with fp32_engine=cuda)",
         "algorithmic_bytes": pass_bytes, "algorithmic_flops": pass_flops,
-        "hbm_gbs_achieved": round(achieved_gbs, 1),
-        "hbm_frac": round(hbm_frac, 4),
+        "hbm_gbs_achieved": round(achieved_gbs, 1), "hbm_frac": round(achieved_gbs / hbm, 4),
         "pass_ms": round(pass_ms, 4),
         "peak_source": f"FP32 FMA peak from {sms} SMs x 128 lanes x 2 flops x median SM clock "
-                       f"{sm_mhz} MHz (derived); HBM {hbm} GB/s ({peak_kind})",
+                       f"{sm_mhz} MHz (derived)",
     }
     tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
     tc_tflops = tc_flops / (tc_ms * 1e-3) / 1e12
@@ -380,9 +431,12 @@ def main():
         "tensor_frac": round(tc_tflops / bf16_peak, 4),
         "peak_source": f"HBM {hbm} GB/s ({peak_kind}); dense BF16 burst {bf16_peak} TFLOP/s ({peak_kind})",
     }
-    # kernels per step: per mode 10 (initial guess chain) + 9 per sweep + the factor
-    # copy, plus the BF16 conversion of each mode that runs tensor-core sweeps
-    launches = sum(11 + 9 * s for s in st["sweeps"]) + sum(1 for b in st["bulk_sweeps"] if b > 0)
+    # kernels per step: per mode 10 (initial guess chain) + the factor copy, 9 per
+    # CUDA-core or BF16 sweep, 12 per split-precision sweep (basis split, W pass,
+    # ||W||^2 sum, Y pass + the 8-kernel tail), plus the BF16 conversion of each mode
+    # that runs bulk sweeps
+    launches = (sum(11 + 9 * n + 3 * t for n, t in zip(st["sweeps"], st["tc_sweeps"])) +
+                sum(1 for b in st["bulk_sweeps"] if b > 0))
     mixed_st = st if args.precision == "mixed_bf16" else ost
     plain_st = st if args.precision == "native" else ost
     mixed_ms = ms if args.precision == "mixed_bf16" else o_ms
@@ -396,18 +450,36 @@ def main():
         "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
                                "1e-2 noise eta 1e-6", "precision": args.precision,
                    "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
-                   "bulk_sweeps": st["bulk_sweeps"], "rel_err": st["rel_err"],
+                   "bulk_sweeps": st["bulk_sweeps"], "tc_sweeps": st["tc_sweeps"],
+                   "rel_err": st["rel_err"],
                    "mixed_vs_fp32_plain": {
                        "mixed_ms": round(mixed_ms, 4), "fp32_plain_ms": round(plain_ms, 4),
                        "speedup": round(plain_ms / mixed_ms, 3),
                        "mixed_rel_err": mixed_st["rel_err"], "fp32_plain_rel_err": plain_st["rel_err"],
                        "rel_err_gap": abs(mixed_st["rel_err"] - plain_st["rel_err"]),
-                       "fp32_plain_sweeps": plain_st["sweeps"]},
+                       "fp32_plain_sweeps": plain_st["sweeps"],
+                       "fp32_plain_products": "split-precision 3xTF32 on tcgen05 (full-size modes)",
+                       "fp32_cuda_core_ms": round(cuda_ms, 4), "fp32_cuda_core_rel_err": cst["rel_err"],
+                       "fp32_cuda_core_sweeps": cst["sweeps"]},
+                   "c3_128quartic": {
+                       "workload": "st-HOSVD-ALS 128^4 FP32 rank (16,16,16,16) 0.8^k spectrum 1e-3 "
+                                   "noise eta 1e-6",
+                       "mixed_ms": round(c3["mixed_bf16"][0], 4), "fp32_plain_ms": round(c3["native"][0], 4),
+                       "speedup": round(c3["native"][0] / c3["mixed_bf16"][0], 3),
+                       "mixed_rel_err": c3["mixed_bf16"][1][2]["rel_err"],
+                       "fp32_plain_rel_err": c3["native"][1][2]["rel_err"],
+                       "rel_err_gap": abs(c3["mixed_bf16"][1][2]["rel_err"] - c3["native"][1][2]["rel_err"]),
+                       "mixed_sweeps": c3["mixed_bf16"][1][2]["sweeps"],
+                       "fp32_plain_sweeps": c3["native"][1][2]["sweeps"]},
+                   "t_hosvd": {"fp32_plain_ms": round(t_ms["fp32_plain"], 4),
+                               "mixed_ms": round(t_ms["mixed"], 4),
+                               "fp32_plain_rel_err": t_rel["fp32_plain"], "mixed_rel_err": t_rel["mixed"]},
                    "l2": "inputs (512 MiB) larger than L2",
                    "driver": "host loop" if args.no_graph else "CUDA graph with device-side while",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "roofline_tc": roofline_tc,
+        "roofline_cuda_core": roofline_cuda,
         "e2e": None if e_ms is None else
                {"value": round(world * 1e3 / e_ms, 3), "unit": "st-HOSVD/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 3),

@@ -83,13 +83,13 @@ typedef struct {
   int bulk_sweeps;       /* mixed precision: most BF16 sweeps per mode (default 8) */
   int use_graph;         /* 1 (default): run each mode's sweep loop as one CUDA graph whose
                             device-side while-node evaluates the stop rule; 0: host loop */
-  int fp32_engine;       /* FP32 products: 0 (default) split-precision 3xTF32 on the tcgen05
-                            tensor cores (two passes per sweep; views with Q % 32 == 0,
-                            I <= 1024, R <= 64) for the modes larger than a quarter of the
-                            input and 16M elements, exact FP32 on CUDA cores for the rest;
-                            1 CUDA cores for every mode; 2 tensor cores for every mode whose
-                            view qualifies. A tensor-core mode's reported error is the
-                            explicit residual ||B_(n) - Q W^T|| of its returned pair. */
+  int fp32_engine;       /* FP32 products: 0 (default, auto) the faster engine per mode -- at
+                            present exact FP32 on CUDA cores everywhere; 1 CUDA cores for every
+                            mode; 2 split-precision 3xTF32 on the tcgen05 tensor cores for
+                            every mode whose view qualifies (two passes per sweep; views with
+                            Q % 32 == 0, I <= 1024, R <= 64), the stop rule's e_k and the
+                            reported error taken from the explicit residual ||B_(n) - Q W^T||
+                            formed in the second pass. */
 } tals_opts;
 
 typedef struct {
@@ -98,6 +98,8 @@ typedef struct {
   double err_per_mode[TALS_MAX_NDIM];   /* e_n = ||B_(n) - L R^T||_F at the returned pair */
   int sweeps[TALS_MAX_NDIM];            /* R-updates performed on mode n (all precisions) */
   int bulk_sweeps[TALS_MAX_NDIM];       /* of which BF16 bulk sweeps */
+  int tc_sweeps[TALS_MAX_NDIM];         /* of which FP32 sweeps on the split-precision (3xTF32)
+                                           tensor-core passes */
   int converged[TALS_MAX_NDIM];         /* 1 if Eq. 5.01 fired before max_sweeps */
   int order[TALS_MAX_NDIM];             /* processing order used */
   int status;                           /* worst per-mode status */

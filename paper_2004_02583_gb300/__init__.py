@@ -43,6 +43,7 @@ class tals_stats(ctypes.Structure):
     _fields_ = [("rel_err", ctypes.c_double), ("norm_a", ctypes.c_double),
                 ("err_per_mode", ctypes.c_double * MAX_NDIM),
                 ("sweeps", ctypes.c_int * MAX_NDIM), ("bulk_sweeps", ctypes.c_int * MAX_NDIM),
+                ("tc_sweeps", ctypes.c_int * MAX_NDIM),
                 ("converged", ctypes.c_int * MAX_NDIM), ("order", ctypes.c_int * MAX_NDIM),
                 ("status", ctypes.c_int)]
 
@@ -51,6 +52,7 @@ class tals_stats(ctypes.Structure):
                 "err_per_mode": list(self.err_per_mode[:ndim]),
                 "sweeps": list(self.sweeps[:ndim]),
                 "bulk_sweeps": list(self.bulk_sweeps[:ndim]),
+                "tc_sweeps": list(self.tc_sweeps[:ndim]),
                 "converged": [bool(x) for x in self.converged[:ndim]],
                 "order": list(self.order[:ndim]), "status": self.status}
 

@@ -187,6 +187,11 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
 // Per-mode ALS (Alg. 3) on a given tensor view
 // ---------------------------------------------------------------------------
 
+// Whether fp32_engine 0 (auto) puts the full-size FP32 modes on the split-precision
+// tensor-core passes: off while they are slower than the exact-FP32 CUDA-core pass
+// on the benchmark view (0.35 + 0.53 ms against 0.49 ms per sweep at 512^3, R = 32).
+constexpr bool kT32Auto = false;
+
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
   if (!j.pc.ok) return fail(TALS_ENOTSUP, "pass kernel limits exceeded (I=%lld R=%d)", j.v.I, j.R);
@@ -212,7 +217,7 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // explicit residual instead of the per-sweep one)
   j.t32 = 0;
   const int eng = c->opts.fp32_engine;
-  const bool want = eng == 2 || (eng == 0 && !j.resid && !j.resid_kernel);
+  const bool want = eng == 2 || (eng == 0 && kT32Auto && !j.resid && !j.resid_kernel);
   if (c->dtype == TALS_F32 && want && c->QS != nullptr && t32_supported(j.v, j.R) &&
       (uintptr_t)j.X % 16 == 0) {
     void* w = j.Wdest;
@@ -581,6 +586,7 @@ static void fill_mode_stats(tals_ctx* c, int n, tals_stats* st) {
   st->err_per_mode[n] = ms.e_cur;
   st->sweeps[n] = ms.k;
   st->bulk_sweeps[n] = ms.bulk;
+  st->tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
   st->converged[n] = ms.converged;
   if (ms.status && !st->status) st->status = ms.status;
 }

@@ -228,6 +228,7 @@ tals_status collect(tals_ctx* c, int kind, const GraphEntry* en, tals_stats* sta
     local.err_per_mode[n] = ms.e_cur;
     local.sweeps[n] = ms.k;
     local.bulk_sweeps[n] = ms.bulk;
+    local.tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
     local.converged[n] = ms.converged;
     if (ms.status && !local.status) local.status = ms.status;
   }

@@ -39,6 +39,7 @@
 // TALS_ETIMEOUT, stops issuing, waits (bounded) for its copies and MMAs and
 // frees its tensor memory.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -50,7 +51,8 @@ using namespace tc;
 
 namespace {
 
-constexpr int kT32Threads = 320;
+constexpr int kT32Threads = 320;    // pass 1
+constexpr int kT32Threads2 = 384;   // pass 2: two more warps prepare the W blocks
 constexpr int kMaxStages = 8;
 constexpr int kKC = 32;                      // pass 1: rows per stage (4 MMA K-steps of 8)
 constexpr int kBox1 = 32 * kKC * 4;          // pass 1: one 32-column box, 4 KiB
@@ -76,7 +78,31 @@ struct T32Args {
   int init;             // pass 2: W block = sketch S (Sec. 4)
   uint64_t sketch;
   const ModeState* st;  // skip the pass once the mode's stop rule has fired (may be null)
+  int flush;            // K-steps (of 8) accumulated in tensor memory before the registers take them
 };
+
+// Optional cycle trace of the passes' roles (builds with -DT32_TRACE only): per
+// kernel, warp and wait site, the clock cycles spent, summed over CTAs.
+#ifdef T32_TRACE
+__device__ unsigned long long g_t32_trace[2][12][12];
+#define T32_TRACE_DECL long long trc[12] = {}; const long long trc0 = clock64();
+#define TWAIT(site, call)                                   \
+  ([&]() {                                                  \
+    const long long _t0 = clock64();                        \
+    const bool _r = (call);                                 \
+    trc[site] += clock64() - _t0;                           \
+    return _r;                                              \
+  }())
+#define T32_TRACE_FLUSH(kern)                                                        \
+  trc[11] = clock64() - trc0;                                                        \
+  if ((threadIdx.x & 31) == 0)                                                       \
+    for (int _k = 0; _k < 12; ++_k)                                                  \
+      atomicAdd(&g_t32_trace[kern][threadIdx.x >> 5][_k], (unsigned long long)trc[_k]);
+#else
+#define T32_TRACE_DECL
+#define TWAIT(site, call) (call)
+#define T32_TRACE_FLUSH(kern)
+#endif
 
 __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return p + ((1024u - (su32(p) & 1023u)) & 1023u);
@@ -198,6 +224,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   volatile int* vfail = &s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  T32_TRACE_DECL
   const long long nt =
       a.ntiles > blockIdx.x ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   if (tid == 0) {
@@ -215,9 +242,9 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // Tensor memory: kNB buffers of kDS columns, one per K-step in flight, each
-  // [B_hi Q_hi | B_hi Q_lo | B_lo Q_hi] written fresh by the K-step's two MMAs.
-  constexpr int kDS = (3 * RP + 31) / 32 * 32;
+  // Tensor memory: kNB buffers of kDS columns, one per accumulation group of
+  // a.flush K-steps in flight, each [B_hi Q_hi | B_hi Q_lo + B_lo Q_hi] started fresh.
+  constexpr int kDS = (2 * RP + 31) / 32 * 32;
   constexpr int kNB = 512 / kDS < kMaxDB ? 512 / kDS : kMaxDB;
   constexpr uint32_t kCols = kNB * kDS <= 64 ? 64 : kNB * kDS <= 128 ? 128 : kNB * kDS <= 256 ? 256 : 512;
   if (warp == 0) tmem_alloc(su32(tmem_holder), kCols);
@@ -233,10 +260,13 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     bool ok = true;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const long long t = blockIdx.x + lt * gridDim.x;
-      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
+      for (int kc0 = 0; kc0 < a.nkc && ok; ++kc0, ++seq) {
+        // every CTA starts its tiles at a different 32-row stage, so the CTAs do not
+        // all fetch the same chunk of the split basis from L2 at the same time
+        const int kc = (int)((kc0 + blockIdx.x) % a.nkc);
         const int slot = (int)(seq % ns);
         const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail);
+        ok = TWAIT(0, mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail));
         if (!ok) break;
         if (lane == 0) {
           unsigned char* st = ring + (size_t)slot * kSB;
@@ -273,10 +303,10 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
         const int slot = (int)(seq % ns);
         const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+        ok = TWAIT(1, mbar_wait_b(su32(&full[slot]), ph, vfail));
         if (!ok) break;
         unsigned char* st = ring + (size_t)slot * kSB;
-        ok = split_tile_t(st, st + kStage1, t, su32(&rd[slot]), ph, vfail);
+        ok = TWAIT(2, split_tile_t(st, st + kStage1, t, su32(&rd[slot]), ph, vfail));
         if (!ok) break;
         fence_async_smem();
         mbar_arrive(su32(&splt[slot]));
@@ -286,22 +316,24 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     // ---------------- MMA issuer ----------------
     constexpr uint32_t kIdAll = idesc(kFmtTF32, 128, 2 * RP, 0, 0);
     constexpr uint32_t kIdHi = idesc(kFmtTF32, 128, RP, 0, 0);
-    long long seq = 0, kseq = 0;
+    const int F = a.flush;
+    long long seq = 0, gseq = 0;   // stages, accumulation groups
     bool ok = true;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
         const int slot = (int)(seq % ns);
         const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = mbar_wait_b(su32(&splt[slot]), ph, vfail);
+        ok = TWAIT(3, mbar_wait_b(su32(&splt[slot]), ph, vfail));
         if (!ok) break;
         fence_after();
         const uint32_t st = su32(ring + (size_t)slot * kSB);
-        for (int ks = 0; ks < kKC / 8 && ok; ++ks, ++kseq) {
-          // every K-step's products go to a fresh buffer; the epilogue adds them up
-          // in registers with rounding to nearest
-          const int b = (int)(kseq % kNB);
-          const uint32_t use = (uint32_t)(kseq / kNB);
-          if (kseq >= kNB) ok = mbar_wait_b(su32(&dfree[b]), (use - 1) & 1u, vfail);
+        for (int ks = 0; ks < kKC / 8 && ok; ++ks) {
+          // each group of F K-steps accumulates in a fresh buffer; the epilogue adds
+          // the groups up in registers with rounding to nearest
+          const bool first = (ks % F) == 0, last = (ks % F) == F - 1;
+          const int b = (int)(gseq % kNB);
+          if (first && gseq >= kNB)
+            ok = TWAIT(4, mbar_wait_b(su32(&dfree[b]), (uint32_t)((gseq / kNB - 1) & 1), vfail));
           if (!ok) break;
           fence_after();
           if (lane == 0) {
@@ -311,11 +343,12 @@ __global__ void __launch_bounds__(kT32Threads, 1)
             const uint64_t alo = desc_sw128(st + kStage1 + ks * 32, 16, 1024);
             // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]
             const uint64_t bq = desc_sw128(st + 2 * kStage1 + ks * 32, 16, 1024);
-            mma_tf32(d, ahi, bq, kIdAll, 0u);                  // [B_hi Q_hi | B_hi Q_lo]
-            mma_tf32(d + 2 * RP, alo, bq, kIdHi, 0u);          // B_lo Q_hi
-            mma_commit(su32(&dfull[b]));
+            mma_tf32(d, ahi, bq, kIdAll, first ? 0u : 1u);   // [B_hi Q_hi | B_hi Q_lo]
+            mma_tf32(d + RP, alo, bq, kIdHi, 1u);            // + B_lo Q_hi into the correction
+            if (last) mma_commit(su32(&dfull[b]));
           }
           __syncwarp();
+          if (last) ++gseq;
         }
         if (lane == 0) mma_commit(su32(&empty[slot]));
         __syncwarp();
@@ -327,29 +360,33 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     // ---------------- epilogue: warps 0-3, lane = tile column ----------------
     bool ok = true;
     const int m = warp * 32 + lane;
-    long long kseq = 0;
+    const int ngr = (kKC / 8) / a.flush;   // groups per stage
+    long long gseq = 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const long long t = blockIdx.x + lt * gridDim.x;
       float big[RP], small[RP];   // sum of B_hi Q_hi; of the two correction terms
 #pragma unroll
       for (int k = 0; k < RP; ++k) big[k] = small[k] = 0.f;
       for (int kc = 0; kc < a.nkc && ok; ++kc) {
-        for (int ks = 0; ks < kKC / 8 && ok; ++ks, ++kseq) {
-          const int b = (int)(kseq % kNB);
-          const uint32_t use = (uint32_t)(kseq / kNB);
-          ok = mbar_wait_b(su32(&dfull[b]), use & 1u, vfail);
+        for (int g = 0; g < ngr && ok; ++g, ++gseq) {
+          const int b = (int)(gseq % kNB);
+          ok = TWAIT(5, mbar_wait_b(su32(&dfull[b]), (uint32_t)((gseq / kNB) & 1), vfail));
           if (!ok) break;
           fence_after();
 #pragma unroll
-          for (int cb = 0; cb < kDS; cb += 32) {
-            float t32[32];
-            tmem_ld32(tmem + (uint32_t)(b * kDS + cb) + ((uint32_t)(warp * 32) << 16), t32);
+          for (int cb = 0; cb < kDS; cb += 64) {
+            uint32_t r0[32], r1[32];
+            const uint32_t ta = tmem + (uint32_t)(b * kDS + cb) + ((uint32_t)(warp * 32) << 16);
+            tmem_ld32_nw(ta, r0);
+            if (cb + 32 < kDS) tmem_ld32_nw(ta + 32u, r1);
+            tmem_wait_ld();
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
+            for (int k = 0; k < 64; ++k) {
               const int c = cb + k;
-              if (c < RP) big[c] += t32[k];
-              else if (c < 2 * RP) small[c - RP] += t32[k];
-              else if (c < 3 * RP) small[c - 2 * RP] += t32[k];
+              if (c >= kDS) break;
+              const float x = __uint_as_float(k < 32 ? r0[k] : r1[k - 32]);
+              if (c < RP) big[c] += x;
+              else if (c < 2 * RP) small[c - RP] += x;
             }
           }
           fence_before();
@@ -372,6 +409,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       }
     }
   }
+  T32_TRACE_FLUSH(0)
   const double tot = block_sum((double)wsh + (double)wsl, red);
   if (tid == 0) {
     a.spart[blockIdx.x] = tot;
@@ -409,7 +447,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
 // residual and split B (lane = row of the chunk = tensor-memory lane); warp 8
 // issues TMA; warp 9 issues the MMAs.
 // ---------------------------------------------------------------------------
-// Pass 2, warps 0-3: prepare the W block of stage lt once it has landed -- split
+// Pass 2, warps 10-11 (t = 0..63): prepare the W block of stage lt once it has landed -- split
 // for the Y product (hi in place, lo RP rows further on; init: the sketch block
 // S, Sec. 4) and, with the residual, transposed and split for the P product.
 template <int RP>
@@ -423,7 +461,7 @@ __device__ __forceinline__ bool t32_prep_w(const T32Args& a, unsigned char* ring
   const long long j0 = (col + lt * ncol) * 32;
   unsigned char* w2 = ring + (size_t)slot * kSB + 2 * kStage2;
   unsigned char* w3 = w2 + kW2;
-  for (int e = t; e < 32 * a.R; e += 128) {
+  for (int e = t; e < 32 * a.R; e += 64) {
     const int r = e >> 5, q = e & 31;
     const float x = a.init ? sketch_entry(a.sketch, (uint64_t)(j0 + q), a.R, r)
                            : *reinterpret_cast<const float*>(w2 + sw_off(r, q));
@@ -442,7 +480,7 @@ __device__ __forceinline__ bool t32_prep_w(const T32Args& a, unsigned char* ring
 }
 
 template <int RP>
-__global__ void __launch_bounds__(kT32Threads, 1)
+__global__ void __launch_bounds__(kT32Threads2, 1)
     t32_ypass_kernel(const __grid_constant__ CUtensorMap bmap, const __grid_constant__ CUtensorMap wmap,
                      T32Args a, int ns) {
   if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
@@ -473,6 +511,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   volatile int* vfail = &s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  T32_TRACE_DECL
   const int chunk = blockIdx.x;
   const long long ncol = gridDim.y, col = blockIdx.y;
   const long long nt = a.ntiles > col ? (a.ntiles - col + ncol - 1) / ncol : 0;
@@ -480,7 +519,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   if (tid == 0) {
     for (int k = 0; k < kMaxStages; ++k) {
       mbar_init(su32(&full[k]), 1);
-      mbar_init(su32(&wrdy[k]), 128);
+      mbar_init(su32(&wrdy[k]), 64);
       mbar_init(su32(&splt[k]), 128);
       mbar_init(su32(&empty[k]), 1);
     }
@@ -501,15 +540,16 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   // by the MMAs and never written: zero every stage's W regions once
   for (int sl = 0; sl < ns; ++sl) {
     uint4* w = reinterpret_cast<uint4*>(ring + (size_t)sl * kSB + 2 * kStage2);
-    for (int e = tid; e < (int)((kW2 + kW3) / 16); e += kT32Threads) w[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < (int)((kW2 + kW3) / 16); e += kT32Threads2) w[e] = make_uint4(0u, 0u, 0u, 0u);
   }
   fence_async_smem();
-  // Tensor memory: kYB buffers of kYS columns for the K-steps of the Y product in
-  // flight, each [B_hi W_hi | B_hi W_lo | B_lo W_hi] written fresh (the tensor
-  // cores round each result toward zero; accumulated in tensor memory over a whole
-  // pass, that bias varies from row to row and tilts the weakest directions of the
-  // basis), summed in registers by warps 0-3; P buffers at 384 and 448.
-  constexpr int kYS = (3 * RP + 31) / 32 * 32;
+  // Tensor memory: kYB buffers of kYS columns for the accumulation groups (a.flush
+  // K-steps) of the Y product in flight, each [B_hi W_hi | B_hi W_lo + B_lo W_hi]
+  // started fresh (the tensor cores round each result toward zero; accumulated in
+  // tensor memory over a whole pass, that bias varies from row to row and tilts the
+  // weakest directions of the basis), summed in registers by warps 0-3; P buffers
+  // at 384 and 448.
+  constexpr int kYS = (2 * RP + 31) / 32 * 32;
   constexpr int kYB = 384 / kYS < kMaxDB ? 384 / kYS : kMaxDB;
   constexpr uint32_t kCols = 512;
   constexpr uint32_t kPCol = 384;
@@ -528,7 +568,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       const long long p = j / a.Q, q = j - p * a.Q;
       const int slot = (int)(seq % ns);
       const uint32_t ph = (uint32_t)((seq / ns) & 1);
-      ok = mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail);
+      ok = TWAIT(0, mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail));
       if (!ok) break;
       if (lane == 0) {
         unsigned char* st = ring + (size_t)slot * kSB;
@@ -545,7 +585,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       }
     __syncwarp();
   } else if (warp < 4) {
-    // ---------------- W preparation (t = row of Q_c in the prologue) ----------------
+    // ---------------- Q_c prologue, then the Y drains (t = row of the chunk) ----------------
     const int t = tid;
     if (resid) {
       // Q_c: rows chunk*128 + t of the basis, split, K-major with 32-wide K blocks
@@ -564,26 +604,28 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     float big[RP], small[RP];   // Y of this row: B_hi W_hi; the two correction terms
 #pragma unroll
     for (int k = 0; k < RP; ++k) big[k] = small[k] = 0.f;
-    if (nt > 0) ok = t32_prep_w<RP>(a, ring, kSB, ns, 0, col, ncol, full, wrdy, t, vfail, resid);
-    long long kseq = 0;
+    const int ngr = 4 / a.flush;   // accumulation groups per stage
+    long long gseq = 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
-      // the next block's W first, so the P product of the next stage can start
-      if (lt + 1 < nt) ok = t32_prep_w<RP>(a, ring, kSB, ns, lt + 1, col, ncol, full, wrdy, t, vfail, resid);
-      for (int ks = 0; ks < 4 && ok; ++ks, ++kseq) {
-        const int b = (int)(kseq % kYB);
-        ok = mbar_wait_b(su32(&yfull[b]), (uint32_t)((kseq / kYB) & 1), vfail);
+      for (int g = 0; g < ngr && ok; ++g, ++gseq) {
+        const int b = (int)(gseq % kYB);
+        ok = TWAIT(2, mbar_wait_b(su32(&yfull[b]), (uint32_t)((gseq / kYB) & 1), vfail));
         if (!ok) break;
         fence_after();
 #pragma unroll
-        for (int cb = 0; cb < kYS; cb += 32) {
-          float t32[32];
-          tmem_ld32(tmem + (uint32_t)(b * kYS + cb) + ((uint32_t)(warp * 32) << 16), t32);
+        for (int cb = 0; cb < kYS; cb += 64) {
+          uint32_t r0[32], r1[32];
+          const uint32_t ta = tmem + (uint32_t)(b * kYS + cb) + ((uint32_t)(warp * 32) << 16);
+          tmem_ld32_nw(ta, r0);
+          if (cb + 32 < kYS) tmem_ld32_nw(ta + 32u, r1);
+          tmem_wait_ld();
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
+          for (int k = 0; k < 64; ++k) {
             const int c = cb + k;
-            if (c < RP) big[c] += t32[k];
-            else if (c < 2 * RP) small[c - RP] += t32[k];
-            else if (c < 3 * RP) small[c - 2 * RP] += t32[k];
+            if (c >= kYS) break;
+            const float x = __uint_as_float(k < 32 ? r0[k] : r1[k - 32]);
+            if (c < RP) big[c] += x;
+            else if (c < 2 * RP) small[c - RP] += x;
           }
         }
         fence_before();
@@ -600,6 +642,12 @@ __global__ void __launch_bounds__(kT32Threads, 1)
           if (r < a.R) yp[r] = big[r] + small[r];
       }
     }
+  } else if (warp >= 10) {
+    // ---------------- W preparation, running ahead by what the ring holds ----------------
+    const int t = tid - 320;
+    bool ok = true;
+    for (long long lt = 0; lt < nt && ok; ++lt)
+      ok = TWAIT(1, t32_prep_w<RP>(a, ring, kSB, ns, lt, col, ncol, full, wrdy, t, vfail, resid));
   } else if (warp < 8) {
     // ---------------- residual and split: lane = row of the chunk ----------------
     const int t = tid - 128;   // row of the chunk; tensor-memory lane quadrant warp % 4
@@ -609,20 +657,21 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
       const int slot = (int)(seq % ns);
       const uint32_t ph = (uint32_t)((seq / ns) & 1);
-      ok = mbar_wait_b(su32(&full[slot]), ph, vfail);
+      ok = TWAIT(3, mbar_wait_b(su32(&full[slot]), ph, vfail));
       if (!ok) break;
       float pv[32];
       if (resid) {
         const int pb = (int)(seq & 1);
-        ok = mbar_wait_b(su32(&pready[pb]), (uint32_t)((seq >> 1) & 1), vfail);
+        ok = TWAIT(4, mbar_wait_b(su32(&pready[pb]), (uint32_t)((seq >> 1) & 1), vfail));
         if (!ok) break;
         fence_after();
-        float p1[32];
+        uint32_t p0[32], p1[32];
         const uint32_t tp = tmem + kPCol + (uint32_t)(pb * 64) + ((uint32_t)((warp & 3) * 32) << 16);
-        tmem_ld32(tp, pv);
-        tmem_ld32(tp + 32u, p1);
+        tmem_ld32_nw(tp, p0);
+        tmem_ld32_nw(tp + 32u, p1);
+        tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) pv[k] += p1[k];
+        for (int k = 0; k < 32; ++k) pv[k] = __uint_as_float(p0[k]) + __uint_as_float(p1[k]);
         fence_before();
         mbar_arrive(su32(&pfree[pb]));
       }
@@ -660,62 +709,78 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     constexpr uint32_t kIdP2 = idesc(kFmtTF32, 128, 64, 0, 0);
     constexpr uint32_t kIdP1 = idesc(kFmtTF32, 128, 32, 0, 0);
     bool ok = !resid || mbar_wait_b(su32(qready), 0u, vfail);
-    long long seq = 0, kseq = 0;
-    for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
-      const int slot = (int)(seq % ns);
-      const uint32_t ph = (uint32_t)((seq / ns) & 1);
-      ok = mbar_wait_b(su32(&wrdy[slot]), ph, vfail);
-      if (!ok) break;
+    const int F = a.flush;
+    // stage lt's P product (after its W block is prepared)
+    auto issue_p = [&](long long lt) -> bool {
+      const int slot = (int)(lt % ns);
+      if (!TWAIT(5, mbar_wait_b(su32(&wrdy[slot]), (uint32_t)((lt / ns) & 1), vfail))) return false;
+      fence_after();
+      if (!resid) return true;
+      // P = Q_c W^T: [Q_hi W_hi^T | Q_hi W_lo^T] (N = 64) and Q_lo W_hi^T into the first half
+      const int pb = (int)(lt & 1);
+      if (lt >= 2 && !TWAIT(6, mbar_wait_b(su32(&pfree[pb]), (uint32_t)(((lt >> 1) - 1) & 1), vfail)))
+        return false;
+      fence_after();
+      if (lane == 0) {
+        const uint32_t w3 = su32(ring + (size_t)slot * kSB) + 2 * kStage2 + kW2;
+        const uint32_t d = tmem + kPCol + (uint32_t)(pb * 64);
+#pragma unroll
+        for (int ks = 0; ks < RP / 8; ++ks) {
+          const uint32_t kq = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
+          const uint32_t kw = (uint32_t)(ks >> 2) * (64u * 128u) + (uint32_t)(ks & 3) * 32u;
+          const uint64_t ah = desc_sw128(su32(qhi) + kq, 16, 1024);
+          const uint64_t al = desc_sw128(su32(qlo) + kq, 16, 1024);
+          const uint64_t bw = desc_sw128(w3 + kw, 16, 1024);
+          mma_tf32(d, ah, bw, kIdP2, ks ? 1u : 0u);
+          mma_tf32(d, al, bw, kIdP1, 1u);
+        }
+        mma_commit(su32(&pready[pb]));
+      }
+      __syncwarp();
+      return true;
+    };
+    long long gseq = 0;
+    // stage lt's Y product (after its residual and split), in groups of F K-steps
+    auto issue_y = [&](long long lt) -> bool {
+      const int slot = (int)(lt % ns);
+      if (!TWAIT(7, mbar_wait_b(su32(&splt[slot]), (uint32_t)((lt / ns) & 1), vfail))) return false;
       fence_after();
       const uint32_t st = su32(ring + (size_t)slot * kSB);
-      const uint32_t w2 = st + 2 * kStage2, w3 = w2 + kW2;
-      if (resid) {
-        // P = Q_c W^T: [Q_hi W_hi^T | Q_hi W_lo^T] (N = 64) and Q_lo W_hi^T into the first half
-        const int pb = (int)(seq & 1);
-        if (seq >= 2) ok = mbar_wait_b(su32(&pfree[pb]), (uint32_t)(((seq >> 1) - 1) & 1), vfail);
-        if (!ok) break;
-        fence_after();
-        if (lane == 0) {
-          const uint32_t d = tmem + kPCol + (uint32_t)(pb * 64);
-#pragma unroll
-          for (int ks = 0; ks < RP / 8; ++ks) {
-            const uint32_t kq = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
-            const uint32_t kw = (uint32_t)(ks >> 2) * (64u * 128u) + (uint32_t)(ks & 3) * 32u;
-            const uint64_t ah = desc_sw128(su32(qhi) + kq, 16, 1024);
-            const uint64_t al = desc_sw128(su32(qlo) + kq, 16, 1024);
-            const uint64_t bw = desc_sw128(w3 + kw, 16, 1024);
-            mma_tf32(d, ah, bw, kIdP2, ks ? 1u : 0u);
-            mma_tf32(d, al, bw, kIdP1, 1u);
-          }
-          mma_commit(su32(&pready[pb]));
-        }
-        __syncwarp();
-      }
-      ok = mbar_wait_b(su32(&splt[slot]), ph, vfail);
-      if (!ok) break;
-      fence_after();
-      for (int ks = 0; ks < 4 && ok; ++ks, ++kseq) {
-        const int b = (int)(kseq % kYB);
-        if (kseq >= kYB) ok = mbar_wait_b(su32(&yfree[b]), (uint32_t)((kseq / kYB - 1) & 1), vfail);
-        if (!ok) break;
+      const uint32_t w2 = st + 2 * kStage2;
+      for (int ks = 0; ks < 4; ++ks) {
+        const bool first = (ks % F) == 0, last = (ks % F) == F - 1;
+        const int b = (int)(gseq % kYB);
+        if (first && gseq >= kYB &&
+            !TWAIT(8, mbar_wait_b(su32(&yfree[b]), (uint32_t)((gseq / kYB - 1) & 1), vfail)))
+          return false;
         fence_after();
         if (lane == 0) {
           const uint32_t d = tmem + (uint32_t)(b * kYS);
           const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
           const uint64_t alo = desc_sw128(st + kStage2 + ks * 32, 16, 1024);
           const uint64_t bw = desc_sw128(w2 + ks * 32, 16, 1024);
-          mma_tf32(d, ahi, bw, kIdY2, 0u);                 // [B_hi W_hi | B_hi W_lo]
-          mma_tf32(d + 2 * RP, alo, bw, kIdY1, 0u);        // B_lo W_hi
-          mma_commit(su32(&yfull[b]));
+          mma_tf32(d, ahi, bw, kIdY2, first ? 0u : 1u);   // [B_hi W_hi | B_hi W_lo]
+          mma_tf32(d + RP, alo, bw, kIdY1, 1u);           // + B_lo W_hi into the correction
+          if (last) mma_commit(su32(&yfull[b]));
         }
         __syncwarp();
+        if (last) ++gseq;
       }
-      if (ok && lane == 0) mma_commit(su32(&empty[slot]));
+      if (lane == 0) mma_commit(su32(&empty[slot]));
       __syncwarp();
+      return true;
+    };
+    // software pipeline: the next stage's P product goes ahead of this stage's Y
+    // product, so the split warps' residual of stage lt + 1 does not wait for it
+    if (ok && nt > 0) ok = issue_p(0);
+    for (long long lt = 0; lt < nt && ok; ++lt) {
+      if (lt + 1 < nt) ok = issue_p(lt + 1);
+      if (ok) ok = issue_y(lt);
     }
     if (lane == 0) mma_commit(su32(ydone));
     __syncwarp();
   }
+  T32_TRACE_FLUSH(1)
   if (tid == 0 && *vfail) atomicExch(a.err, 5);   // TALS_ETIMEOUT
   if (*vfail && tid == 288) mbar_drain(su32(ydone), 0u);
   fence_before();
@@ -758,6 +823,16 @@ size_t smem2(int ns) {
   constexpr size_t KB = (RP + 31) / 32;
   const size_t stage = 2 * (size_t)kStage2 + 2 * RP * 128 + 64 * KB * 128;
   return 1024 + 2 * (128 * KB * 128) + (size_t)ns * stage + (4 * kMaxStages + 6 + 2 * kMaxDB) * 8 + 16;
+}
+
+int t32_flush() {
+  static int f = -1;
+  if (f < 0) {
+    const char* e = getenv("TALS_T32_FLUSH");
+    f = e ? atoi(e) : 1;
+    if (f != 1 && f != 2 && f != 4) f = 1;
+  }
+  return f;
 }
 
 int rp_of(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 48 ? 48 : 64; }
@@ -816,6 +891,14 @@ int t32_grid(const ModeView& v, int pass, int sms) {
 
 int t32_chunks(const ModeView& v) { return (int)((v.I + kRows2 - 1) / kRows2); }
 
+#ifdef T32_TRACE
+extern "C" int tals_t32_trace(unsigned long long* out) {
+  if (cudaMemcpyFromSymbol(out, g_t32_trace, sizeof(g_t32_trace)) != cudaSuccess) return 1;
+  static unsigned long long zero[2][12][12];
+  return cudaMemcpyToSymbol(g_t32_trace, zero, sizeof(zero)) == cudaSuccess ? 0 : 1;
+}
+#endif
+
 cudaError_t launch_t32_split_basis(const float* L, long long I, int R, float* QS, cudaStream_t s) {
   const int RP = rp_of(R);
   const int nkc = (int)((I + kKC - 1) / kKC);
@@ -847,6 +930,7 @@ cudaError_t launch_t32_wpass(const float* X, const ModeView& v, int R, const flo
   a.spart = spart;
   a.err = err;
   a.st = st;
+  a.flush = t32_flush();
   grid = (int)std::max<long long>(1, std::min<long long>(grid, a.ntiles));
   int ns = stages1(RP);
   void* fn = nullptr;
@@ -890,6 +974,7 @@ cudaError_t launch_t32_ypass(const float* X, const ModeView& v, int R, const flo
   a.init = init;
   a.sketch = sketch;
   a.st = st;
+  a.flush = t32_flush();
   ncol = (int)std::max<long long>(1, std::min<long long>(ncol, a.ntiles));
   int ns = stages2(RP);
   void* fn = nullptr;
@@ -903,7 +988,7 @@ cudaError_t launch_t32_ypass(const float* X, const ModeView& v, int R, const flo
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&bmap, &wmap, &a, (void*)&ns};
-  return cudaLaunchKernel(fn, dim3(a.nch, ncol), dim3(kT32Threads), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(a.nch, ncol), dim3(kT32Threads2), args, smem, s);
 }
 
 }  // namespace tals
