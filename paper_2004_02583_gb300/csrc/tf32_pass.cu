@@ -33,13 +33,13 @@
 // Views: the mode's unfolding columns j = p Q + q with Q a multiple of 32, so a
 // 32-column box never crosses p; the tensor is read in place through a 3-D map
 // (Q, I, P). Both MMA operands are K-major (kind::tf32 takes no MN-major
-// operand here): pass 1's split step also transposes each landed stage. Warp roles (320 threads): warps 0-3 read tensor memory (W tiles,
-// final Y), warps 4-7 split the staged tiles, warp 8 issues TMA, warp 9 issues
-// the MMAs. Every wait is clock-bounded: on timeout the CTA records
+// operand here): pass 1's split step also transposes each landed stage. Warp
+// roles: warps 0-3 read tensor memory (W tiles, final Y), warps 4-7 split the
+// staged tiles, warp 8 issues TMA, warp 9 issues the MMAs; in pass 2 warps 10-11
+// prepare the W blocks. Every wait is clock-bounded: on timeout the CTA records
 // TALS_ETIMEOUT, stops issuing, waits (bounded) for its copies and MMAs and
 // frees its tensor memory.
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -153,36 +153,6 @@ __device__ __forceinline__ void split_tile(float* hi, float* lo, int t, bool nor
   }
 }
 
-// Pass-1 stage split with transpose: the stage lands as four TMA boxes of
-// [32 rows i][32 columns] (128B-swizzled, i.e. MN-major for the W product); the
-// split threads rewrite it K-major -- [128 tile columns m][32 rows i], rows of
-// 128 B -- with hi in place of the landed data and lo in the lo plane. Thread
-// t = 32 w + l owns tile column m = t: it reads its 32 values (one 128-byte row
-// of a box per load across the warp, conflict-free), waits until all 128 split
-// threads have read (a bounded mbarrier wait, so a failure elsewhere cannot hang
-// it), then writes 16-byte chunks (4 wavefronts per warp store, the minimum).
-__device__ __forceinline__ bool split_tile_t(unsigned char* st, unsigned char* lo, int t,
-                                             uint32_t rd_bar, uint32_t ph, volatile int* fail) {
-  const int w = t >> 5, l = t & 31;
-  float v[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k)
-    v[k] = *reinterpret_cast<const float*>(st + w * 4096 + k * 128 + ((((l >> 2) ^ (k & 7))) << 4) +
-                                           (l & 3) * 4);
-  mbar_arrive(rd_bar);
-  if (!mbar_wait_b(rd_bar, ph, fail)) return false;
-  const int m = t;
-#pragma unroll
-  for (int kq = 0; kq < 8; ++kq) {
-    float4 x = make_float4(v[4 * kq], v[4 * kq + 1], v[4 * kq + 2], v[4 * kq + 3]);
-    const float4 l4 = split4(x);
-    const uint32_t off = (uint32_t)m * 128u + ((uint32_t)(kq ^ (m & 7)) << 4);
-    *reinterpret_cast<float4*>(st + off) = x;
-    *reinterpret_cast<float4*>(lo + off) = l4;
-  }
-  return true;
-}
-
 // Byte offset of element (row n, column k) in a K-major 128B-swizzled operand
 // whose rows are 128 bytes (32 FP32 values along K).
 __device__ __forceinline__ uint32_t sw_off(int n, int k) {
@@ -200,23 +170,57 @@ __device__ __forceinline__ double split_sum(float sh, float sl, double* red4, in
 
 // ---------------------------------------------------------------------------
 // Pass 1: W = B^T Q (3xTF32), ||W||^2
+//
+// Three rings decouple the stages: raw slots receive the tensor by TMA and are
+// released as soon as the split threads hold their column in registers, so a
+// raw slot recycles after one TMA round trip and many bytes stay in flight;
+// operand slots hold the stage split and transposed K-major ([128 tile columns][32 rows i], hi and lo planes)
+// until its MMAs are done; beside each operand slot, the stage's rows of the split
+// basis (released with it).
 // ---------------------------------------------------------------------------
+// The raw stage is row-major without swizzle: one box [32 rows][128 columns]
+// (wide), or four boxes [32 rows][32 columns] (narrow views, Q % 128 != 0). Thread
+// t = tile column m reads its 32 values; a warp reads 32 consecutive floats of a
+// row per load (conflict-free).
+__device__ __forceinline__ void t32_read_col(const unsigned char* raw, int t, bool wide, float (&v)[32]) {
+  const float* base = reinterpret_cast<const float*>(raw) + (wide ? t : (t >> 5) * 1024 + (t & 31));
+  const int pitch = wide ? 128 : 32;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = base[k * pitch];
+}
+
+// Column m of the stage as a K-major row of the hi and lo operands (16-byte chunks:
+// four wavefronts per warp store, the minimum for 512 bytes).
+__device__ __forceinline__ void t32_write_col(unsigned char* hi, unsigned char* lo, int m,
+                                              const float (&v)[32]) {
+#pragma unroll
+  for (int kq = 0; kq < 8; ++kq) {
+    float4 x = make_float4(v[4 * kq], v[4 * kq + 1], v[4 * kq + 2], v[4 * kq + 3]);
+    const float4 l4 = split4(x);
+    const uint32_t off = (uint32_t)m * 128u + ((uint32_t)(kq ^ (m & 7)) << 4);
+    *reinterpret_cast<float4*>(hi + off) = x;
+    *reinterpret_cast<float4*>(lo + off) = l4;
+  }
+}
+
 template <int RP>
 __global__ void __launch_bounds__(kT32Threads, 1)
-    t32_wpass_kernel(const __grid_constant__ CUtensorMap bmap, T32Args a, int ns) {
+    t32_wpass_kernel(const __grid_constant__ CUtensorMap bmap, T32Args a, int nr, int no, int nq) {
   if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = align1024(smem_raw);
   constexpr uint32_t kQB = 2 * RP * 128;            // split basis of one stage
-  constexpr uint32_t kSB = 2 * kStage1 + kQB;       // stage: hi | lo | basis
-  unsigned char* ring = base;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)ns * kSB);
-  uint64_t* full = bars;                      // TMA landed (tx)
-  uint64_t* splt = full + kMaxStages;         // split done (128 arrivals)
-  uint64_t* empty = splt + kMaxStages;        // MMAs done with the stage (commit)
-  uint64_t* rd = empty + kMaxStages;          // split threads have read the stage (128)
-  uint64_t* dfull = rd + kMaxStages;          // [kNB] K-step products ready (commit)
-  uint64_t* dfree = dfull + kMaxDB;           // [kNB] K-step products read out (128 arrivals)
+  unsigned char* raw = base;                                      // nr x 16 KiB
+  unsigned char* opr = raw + (size_t)nr * kStage1;                // no x (hi | lo) 32 KiB
+  unsigned char* qsr = opr + (size_t)no * 2 * kStage1;            // nq x kQB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(qsr + (size_t)nq * kQB);
+  uint64_t* rfull = bars;                     // raw stage landed (tx)
+  uint64_t* rempty = rfull + kMaxStages;      // raw stage read by the split threads (128)
+  uint64_t* ofull = rempty + kMaxStages;      // operands written (128)
+  uint64_t* oempty = ofull + kMaxStages;      // MMAs done with the operands (commit)
+  uint64_t* qfull = oempty + kMaxStages;      // basis chunk landed (tx)
+  uint64_t* dfull = qfull + kMaxStages;       // [kNB] group products ready (commit)
+  uint64_t* dfree = dfull + kMaxDB;           // [kNB] group products read out (128 arrivals)
   uint64_t* alldone = dfree + kMaxDB;         // every MMA done (commit)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(alldone + 1);
   __shared__ double red[32];
@@ -227,12 +231,14 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   T32_TRACE_DECL
   const long long nt =
       a.ntiles > blockIdx.x ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long nst = nt * a.nkc;   // stages of this CTA
   if (tid == 0) {
     for (int k = 0; k < kMaxStages; ++k) {
-      mbar_init(su32(&full[k]), 1);
-      mbar_init(su32(&splt[k]), 128);
-      mbar_init(su32(&empty[k]), 1);
-      mbar_init(su32(&rd[k]), 128);
+      mbar_init(su32(&rfull[k]), 1);
+      mbar_init(su32(&rempty[k]), 128);
+      mbar_init(su32(&ofull[k]), 128);
+      mbar_init(su32(&oempty[k]), 1);
+      mbar_init(su32(&qfull[k]), 1);
     }
     for (int b = 0; b < kMaxDB; ++b) {
       mbar_init(su32(&dfull[b]), 1);
@@ -255,104 +261,130 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   float wsh = 0.f, wsl = 0.f;   // ||W||^2 (epilogue threads)
 
   if (warp == 8) {
-    // ---------------- producer ----------------
-    long long seq = 0;
+    // ---------------- producer: raw stages and basis chunks ----------------
+    long long s = 0;
     bool ok = true;
+    const bool wide = a.Q % 128 == 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const long long t = blockIdx.x + lt * gridDim.x;
-      for (int kc0 = 0; kc0 < a.nkc && ok; ++kc0, ++seq) {
+      // the tile's four 32-column blocks: (p, q) of each, once per tile (past the
+      // last column: p out of range, zero fill)
+      int pb[4], qb[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const long long j = t * 128 + 32 * b;
+        pb[b] = (int)a.P;
+        qb[b] = 0;
+        if (j < a.J) {
+          const long long p = j / a.Q;
+          pb[b] = (int)p;
+          qb[b] = (int)(j - p * a.Q);
+        }
+      }
+      for (int kc0 = 0; kc0 < a.nkc && ok; ++kc0, ++s) {
         // every CTA starts its tiles at a different 32-row stage, so the CTAs do not
         // all fetch the same chunk of the split basis from L2 at the same time
         const int kc = (int)((kc0 + blockIdx.x) % a.nkc);
-        const int slot = (int)(seq % ns);
-        const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = TWAIT(0, mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail));
+        const int r = (int)(s % nr);
+        ok = TWAIT(0, mbar_wait_b(su32(&rempty[r]), (uint32_t)(((s / nr) & 1) ^ 1), vfail));
         if (!ok) break;
         if (lane == 0) {
-          unsigned char* st = ring + (size_t)slot * kSB;
-          mbar_expect_tx(su32(&full[slot]), (uint32_t)kStage1 + kQB);
+          unsigned char* st = raw + (size_t)r * kStage1;
+          mbar_expect_tx(su32(&rfull[r]), (uint32_t)kStage1);
+          if (wide) {
+            tma_load_3d(su32(st), &bmap, su32(&rfull[r]), qb[0], kc * kKC, pb[0]);
+          } else {
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const long long j = t * 128 + 32 * b;
-            long long p = a.P, q = 0;   // past the last column: out of range, zero fill
-            if (j < a.J) {
-              p = j / a.Q;
-              q = j - p * a.Q;
-            }
-            tma_load_3d(su32(st + b * kBox1), &bmap, su32(&full[slot]), (int)q, kc * kKC, (int)p);
+            for (int b = 0; b < 4; ++b)
+              tma_load_3d(su32(st + b * kBox1), &bmap, su32(&rfull[r]), qb[b], kc * kKC, pb[b]);
           }
-          bulk_load(su32(st + 2 * kStage1), a.QS + (size_t)kc * (kQB / 4), kQB, su32(&full[slot]));
         }
         __syncwarp();
       }
     }
     // every copy issued must have landed before the shared memory is released
     if (lane == 0) {
-      for (int sl = 0; sl < ns && sl < seq; ++sl) {
-        const long long nfill = seq / ns + (sl < seq % ns ? 1 : 0);
-        mbar_drain(su32(&full[sl]), (uint32_t)((nfill - 1) & 1));
-      }
+      for (int sl = 0; sl < nr && sl < s; ++sl)
+        mbar_drain(su32(&rfull[sl]), (uint32_t)(((s / nr + (sl < s % nr ? 1 : 0)) - 1) & 1));
+
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
-    // ---------------- split: hi in place, lo beside ----------------
+    // ---------------- split: column m = t to registers, raw slot released, K-major hi / lo ----
     const int t = tid - 128;
-    long long seq = 0;
+    const bool wide = a.Q % 128 == 0;
     bool ok = true;
-    for (long long lt = 0; lt < nt && ok; ++lt) {
-      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
-        const int slot = (int)(seq % ns);
-        const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = TWAIT(1, mbar_wait_b(su32(&full[slot]), ph, vfail));
-        if (!ok) break;
-        unsigned char* st = ring + (size_t)slot * kSB;
-        ok = TWAIT(2, split_tile_t(st, st + kStage1, t, su32(&rd[slot]), ph, vfail));
-        if (!ok) break;
-        fence_async_smem();
-        mbar_arrive(su32(&splt[slot]));
+    long long nq_issued = 0;
+    for (long long s = 0; s < nst && ok; ++s) {
+      const int r = (int)(s % nr), o = (int)(s % no);
+      ok = TWAIT(1, mbar_wait_b(su32(&rfull[r]), (uint32_t)((s / nr) & 1), vfail));
+      if (!ok) break;
+      float v[32];
+      t32_read_col(raw + (size_t)r * kStage1, t, wide, v);
+      mbar_arrive(su32(&rempty[r]));
+      ok = TWAIT(2, mbar_wait_b(su32(&oempty[o]), (uint32_t)(((s / no) & 1) ^ 1), vfail));
+      if (!ok) break;
+      if (t == 0) {
+        // the stage's rows of the split basis into the operand slot's basis slot
+        const int kc = (int)(((s % a.nkc) + blockIdx.x) % a.nkc);
+        mbar_expect_tx(su32(&qfull[o]), kQB);
+        bulk_load(su32(qsr + (size_t)o * kQB), a.QS + (size_t)kc * (kQB / 4), kQB, su32(&qfull[o]));
       }
+      unsigned char* op = opr + (size_t)o * 2 * kStage1;
+      t32_write_col(op, op + kStage1, t, v);
+      fence_async_smem();
+      mbar_arrive(su32(&ofull[o]));
+      ++nq_issued;
     }
+    // every basis copy issued must have landed before the shared memory is released
+    if (t == 0)
+      for (int sl = 0; sl < no && sl < nq_issued; ++sl)
+        mbar_drain(su32(&qfull[sl]),
+                   (uint32_t)(((nq_issued / no + (sl < nq_issued % no ? 1 : 0)) - 1) & 1));
   } else if (warp == 9) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t kIdAll = idesc(kFmtTF32, 128, 2 * RP, 0, 0);
     constexpr uint32_t kIdHi = idesc(kFmtTF32, 128, RP, 0, 0);
     const int F = a.flush;
-    long long seq = 0, gseq = 0;   // stages, accumulation groups
+    long long gseq = 0;   // accumulation groups
     bool ok = true;
-    for (long long lt = 0; lt < nt && ok; ++lt) {
-      for (int kc = 0; kc < a.nkc && ok; ++kc, ++seq) {
-        const int slot = (int)(seq % ns);
-        const uint32_t ph = (uint32_t)((seq / ns) & 1);
-        ok = TWAIT(3, mbar_wait_b(su32(&splt[slot]), ph, vfail));
-        if (!ok) break;
-        fence_after();
-        const uint32_t st = su32(ring + (size_t)slot * kSB);
-        for (int ks = 0; ks < kKC / 8 && ok; ++ks) {
-          // each group of F K-steps accumulates in a fresh buffer; the epilogue adds
-          // the groups up in registers with rounding to nearest
-          const bool first = (ks % F) == 0, last = (ks % F) == F - 1;
-          const int b = (int)(gseq % kNB);
-          if (first && gseq >= kNB)
-            ok = TWAIT(4, mbar_wait_b(su32(&dfree[b]), (uint32_t)((gseq / kNB - 1) & 1), vfail));
+    for (long long s = 0; s < nst && ok; ++s) {
+      const int o = (int)(s % no), q = o;
+      ok = TWAIT(3, mbar_wait_b(su32(&ofull[o]), (uint32_t)((s / no) & 1), vfail));
+      if (ok) ok = TWAIT(3, mbar_wait_b(su32(&qfull[q]), (uint32_t)((s / no) & 1), vfail));
+      if (!ok) break;
+      fence_after();
+      const uint32_t op = su32(opr + (size_t)o * 2 * kStage1);
+      const uint32_t qs = su32(qsr + (size_t)q * kQB);
+      // groups of F K-steps, each into a fresh buffer (the epilogue adds the groups
+      // up in registers with rounding to nearest); lane 0 issues a group's MMAs back
+      // to back (a fence or commit between MMAs costs issue cycles)
+      for (int g = 0; g < (kKC / 8) / F && ok; ++g, ++gseq) {
+        const int b = (int)(gseq % kNB);
+        if (gseq >= kNB) {
+          ok = TWAIT(4, mbar_wait_b(su32(&dfree[b]), (uint32_t)((gseq / kNB - 1) & 1), vfail));
           if (!ok) break;
           fence_after();
-          if (lane == 0) {
-            const uint32_t d = tmem + (uint32_t)(b * kDS);
-            // A: K-major (rows = the 128 tile columns, 128 B = 32 rows i), 8 i per step
-            const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
-            const uint64_t alo = desc_sw128(st + kStage1 + ks * 32, 16, 1024);
-            // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]
-            const uint64_t bq = desc_sw128(st + 2 * kStage1 + ks * 32, 16, 1024);
-            mma_tf32(d, ahi, bq, kIdAll, first ? 0u : 1u);   // [B_hi Q_hi | B_hi Q_lo]
-            mma_tf32(d + RP, alo, bq, kIdHi, 1u);            // + B_lo Q_hi into the correction
-            if (last) mma_commit(su32(&dfull[b]));
-          }
-          __syncwarp();
-          if (last) ++gseq;
         }
-        if (lane == 0) mma_commit(su32(&empty[slot]));
+        if (lane == 0) {
+          const uint32_t d = tmem + (uint32_t)(b * kDS);
+          for (int k = 0; k < F; ++k) {
+            const int ks = g * F + k;
+            // A: K-major (rows = the 128 tile columns, 128 B = 32 rows i), 8 i per step
+            const uint64_t ahi = desc_sw128(op + ks * 32, 16, 1024);
+            const uint64_t alo = desc_sw128(op + kStage1 + ks * 32, 16, 1024);
+            // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]
+            const uint64_t bq = desc_sw128(qs + ks * 32, 16, 1024);
+            mma_tf32(d, ahi, bq, kIdAll, k ? 1u : 0u);   // [B_hi Q_hi | B_hi Q_lo]
+            mma_tf32(d + RP, alo, bq, kIdHi, 1u);        // + B_lo Q_hi into the correction
+          }
+          mma_commit(su32(&dfull[b]));
+        }
         __syncwarp();
       }
+      // operand slot and basis slot released together
+      if (lane == 0) mma_commit(su32(&oempty[o]));
+      __syncwarp();
     }
     if (lane == 0) mma_commit(su32(alldone));
     __syncwarp();
@@ -421,6 +453,7 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
+
 
 // ---------------------------------------------------------------------------
 // Pass 2: Y = B W and the residual ||B - Q W^T||^2 (3xTF32); init mode: Y0 = B S
@@ -747,24 +780,25 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
       fence_after();
       const uint32_t st = su32(ring + (size_t)slot * kSB);
       const uint32_t w2 = st + 2 * kStage2;
-      for (int ks = 0; ks < 4; ++ks) {
-        const bool first = (ks % F) == 0, last = (ks % F) == F - 1;
+      for (int g = 0; g < 4 / F; ++g, ++gseq) {
         const int b = (int)(gseq % kYB);
-        if (first && gseq >= kYB &&
-            !TWAIT(8, mbar_wait_b(su32(&yfree[b]), (uint32_t)((gseq / kYB - 1) & 1), vfail)))
-          return false;
-        fence_after();
+        if (gseq >= kYB) {
+          if (!TWAIT(8, mbar_wait_b(su32(&yfree[b]), (uint32_t)((gseq / kYB - 1) & 1), vfail))) return false;
+          fence_after();
+        }
         if (lane == 0) {
           const uint32_t d = tmem + (uint32_t)(b * kYS);
-          const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
-          const uint64_t alo = desc_sw128(st + kStage2 + ks * 32, 16, 1024);
-          const uint64_t bw = desc_sw128(w2 + ks * 32, 16, 1024);
-          mma_tf32(d, ahi, bw, kIdY2, first ? 0u : 1u);   // [B_hi W_hi | B_hi W_lo]
-          mma_tf32(d + RP, alo, bw, kIdY1, 1u);           // + B_lo W_hi into the correction
-          if (last) mma_commit(su32(&yfull[b]));
+          for (int k = 0; k < F; ++k) {
+            const int ks = g * F + k;
+            const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
+            const uint64_t alo = desc_sw128(st + kStage2 + ks * 32, 16, 1024);
+            const uint64_t bw = desc_sw128(w2 + ks * 32, 16, 1024);
+            mma_tf32(d, ahi, bw, kIdY2, k ? 1u : 0u);   // [B_hi W_hi | B_hi W_lo]
+            mma_tf32(d + RP, alo, bw, kIdY1, 1u);       // + B_lo W_hi into the correction
+          }
+          mma_commit(su32(&yfull[b]));
         }
         __syncwarp();
-        if (last) ++gseq;
       }
       if (lane == 0) mma_commit(su32(&empty[slot]));
       __syncwarp();
@@ -814,10 +848,14 @@ __global__ void t32_split_basis_kernel(const float* __restrict__ L, int I, int R
   }
 }
 
+struct Ring1 { int nr, no, nq; };
+
 template <int RP>
-size_t smem1(int ns) {
-  return 1024 + (size_t)ns * (2 * kStage1 + 2 * RP * 128) + (4 * kMaxStages + 2 * kMaxDB + 1) * 8 + 16;
+size_t smem1(const Ring1& g) {
+  return 1024 + (size_t)g.nr * kStage1 + (size_t)g.no * 2 * kStage1 + (size_t)g.nq * (2 * RP * 128) +
+         (5 * kMaxStages + 2 * kMaxDB + 1) * 8 + 16;
 }
+
 template <int RP>
 size_t smem2(int ns) {
   constexpr size_t KB = (RP + 31) / 32;
@@ -825,26 +863,27 @@ size_t smem2(int ns) {
   return 1024 + 2 * (128 * KB * 128) + (size_t)ns * stage + (4 * kMaxStages + 6 + 2 * kMaxDB) * 8 + 16;
 }
 
-int t32_flush() {
-  static int f = -1;
-  if (f < 0) {
-    const char* e = getenv("TALS_T32_FLUSH");
-    f = e ? atoi(e) : 1;
-    if (f != 1 && f != 2 && f != 4) f = 1;
-  }
-  return f;
-}
+// K-steps (of 8) per accumulation group: four, i.e. one group per 32-row stage.
+// A group's products are summed by the tensor cores (truncating) and the groups
+// by the registers (rounding to nearest); four keeps the truncation bias of W and
+// Y below 1e-7 relative while the drains keep up with the MMAs.
+constexpr int kFlush = 4;
 
 int rp_of(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 48 ? 48 : 64; }
 
-int stages1(int RP) {
+// Pass 1 rings: three operand slots (each with its basis slot), as many raw slots
+// (up to kMaxStages) as fit.
+Ring1 ring1(int RP) {
   const size_t static_smem = 2048;
-  for (int ns = kMaxStages; ns >= 2; --ns) {
-    size_t s = RP == 16 ? smem1<16>(ns) : RP == 32 ? smem1<32>(ns) : RP == 48 ? smem1<48>(ns) : smem1<64>(ns);
-    if (s + static_smem <= (size_t)kSmemCap) return ns;
-  }
-  return 0;
+  for (int nq = 3; nq >= 3; --nq)
+    for (int nr = kMaxStages; nr >= 3; --nr) {
+      const Ring1 g{nr, 3, nq};
+      const size_t s = RP == 16 ? smem1<16>(g) : RP == 32 ? smem1<32>(g) : RP == 48 ? smem1<48>(g) : smem1<64>(g);
+      if (s + static_smem <= (size_t)kSmemCap) return g;
+    }
+  return Ring1{0, 0, 0};
 }
+
 int stages2(int RP) {
   const size_t static_smem = 2048;
   for (int ns = kMaxStages; ns >= 2; --ns) {
@@ -854,17 +893,20 @@ int stages2(int RP) {
   return 0;
 }
 
-// 3-D FP32 map of the view (Q, I, P) or of W (Q, R, P), boxes (32, rows, 1), 128B swizzle.
-bool make_map(const void* X, long long Q, long long rows, long long P, int box_rows, CUtensorMap* map) {
+// 3-D FP32 map of the view (Q, I, P) or of W (Q, R, P), boxes (box_cols, rows, 1),
+// 128B swizzle (box_cols 32) or none.
+bool make_map(const void* X, long long Q, long long rows, long long P, int box_rows, CUtensorMap* map,
+              int box_cols = 32, bool swizzle = true) {
   EncodeTiledFn fn = tma_encode_fn();
   if (!fn) return false;
   if ((uintptr_t)X % 16 != 0) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Q, (cuuint64_t)rows, (cuuint64_t)P};
   cuuint64_t strides[2] = {(cuuint64_t)Q * 4, (cuuint64_t)rows * Q * 4};
-  cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(X), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -875,7 +917,7 @@ bool t32_supported(const ModeView& v, int R) {
   if (R < 1 || R > 64 || v.Q % 32 != 0 || v.I < 1 || v.I > 1024) return false;
   if (v.P > 0x7fffffffLL || v.Q > 0x7fffffffLL || v.I > 0x7fffffffLL) return false;
   const int RP = rp_of(R);
-  return stages1(RP) >= 2 && stages2(RP) >= 2;
+  return ring1(RP).nr >= 3 && stages2(RP) >= 2;
 }
 
 size_t t32_basis_floats(long long I, int R) {
@@ -912,7 +954,7 @@ cudaError_t launch_t32_wpass(const float* X, const ModeView& v, int R, const flo
                              double* spart, int* err, int grid, cudaStream_t s, const ModeState* st) {
   if (!t32_supported(v, R) || !W || !QS) return cudaErrorInvalidValue;
   CUtensorMap bmap;
-  if (!make_map(X, v.Q, v.I, v.P, kKC, &bmap)) return cudaErrorInvalidValue;
+  if (!make_map(X, v.Q, v.I, v.P, kKC, &bmap, v.Q % 128 == 0 ? 128 : 32, false)) return cudaErrorInvalidValue;
   const int RP = rp_of(R);
   T32Args a;
   std::memset(&a, 0, sizeof(a));
@@ -930,20 +972,20 @@ cudaError_t launch_t32_wpass(const float* X, const ModeView& v, int R, const flo
   a.spart = spart;
   a.err = err;
   a.st = st;
-  a.flush = t32_flush();
+  a.flush = kFlush;
   grid = (int)std::max<long long>(1, std::min<long long>(grid, a.ntiles));
-  int ns = stages1(RP);
+  Ring1 g = ring1(RP);
   void* fn = nullptr;
   size_t smem = 0;
   switch (RP) {
-    case 16: fn = (void*)&t32_wpass_kernel<16>; smem = smem1<16>(ns); break;
-    case 32: fn = (void*)&t32_wpass_kernel<32>; smem = smem1<32>(ns); break;
-    case 48: fn = (void*)&t32_wpass_kernel<48>; smem = smem1<48>(ns); break;
-    default: fn = (void*)&t32_wpass_kernel<64>; smem = smem1<64>(ns); break;
+    case 16: fn = (void*)&t32_wpass_kernel<16>; smem = smem1<16>(g); break;
+    case 32: fn = (void*)&t32_wpass_kernel<32>; smem = smem1<32>(g); break;
+    case 48: fn = (void*)&t32_wpass_kernel<48>; smem = smem1<48>(g); break;
+    default: fn = (void*)&t32_wpass_kernel<64>; smem = smem1<64>(g); break;
   }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {&bmap, &a, (void*)&ns};
+  void* args[] = {&bmap, &a, (void*)&g.nr, (void*)&g.no, (void*)&g.nq};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kT32Threads), args, smem, s);
 }
 
@@ -974,7 +1016,7 @@ cudaError_t launch_t32_ypass(const float* X, const ModeView& v, int R, const flo
   a.init = init;
   a.sketch = sketch;
   a.st = st;
-  a.flush = t32_flush();
+  a.flush = kFlush;
   ncol = (int)std::max<long long>(1, std::min<long long>(ncol, a.ntiles));
   int ns = stages2(RP);
   void* fn = nullptr;
