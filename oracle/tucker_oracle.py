@@ -31,6 +31,18 @@ R6  Default st-HOSVD order: ascending R_n, ties by ascending n (Prop. 1).
 R7  Noise is relative Frobenius noise (see ``workloads``).
 R9  r = min(m, n) is allowed (Alg. 3 asks r < min(m, n)); ALS then reproduces
     the matrix exactly.
+R10 HOOI (Sec. 6.3 refines the t-/st-HOSVD results with it; the paper takes the
+    method from a toolbox and prints no steps): cycles over the modes in
+    ascending order; mode n is replaced by the R_n leading left singular
+    vectors of (A x_{m != n} U_m^T)_(n), using the factors already updated in
+    the cycle. After cycle k the core is G = A x_1 U_1^T ... x_N U_N^T and the
+    relative residual r_k = ||A - G x U|| / ||A||; r_0 is that of the initial
+    guess. The loop stops after the first cycle with |r_{k-1} - r_k| < tol
+    (the toolbox's change-of-fit test, fit = 1 - r), or after max_iters cycles.
+R11 Singular vectors of a t-HOSVD-ALS basis (Sec. 5, after Alg. 4): the SVD of
+    Qhat^T A_(n) = U S V^T gives U^(n) = Qhat U, in descending order of S. The
+    sign of each singular vector is free; it is fixed so that the entry of
+    largest magnitude of every column of U^(n) is positive (ties: the first).
 
 Parity pins: every function here is checked by ``tests/test_oracle_pins.py``
 against SVD-based definitions, closed forms, invariants, published test
@@ -51,6 +63,7 @@ __all__ = [
     "t_hosvd_svd", "st_hosvd_svd", "HOSVDResult", "rel_error",
     "project", "reconstruct", "project_vjp", "reconstruct_vjp",
     "recon_loss", "recon_loss_grad", "principal_angles",
+    "hooi", "HOOIResult", "singular_vectors", "sign_fix",
 ]
 
 MASK64 = (1 << 64) - 1
@@ -346,6 +359,73 @@ def st_hosvd_svd(a: np.ndarray, ranks: Sequence[int],
     return HOSVDResult(G=np.array(b), U=us, err_per_mode=errs, sweeps=[0] * a.ndim,
                        converged=[True] * a.ndim, order=order,
                        norm_a=float(np.sqrt(frob2(a))), als=[None] * a.ndim)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 6.3: HOOI from the t-/st-HOSVD initial guess (reading R10)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class HOOIResult:
+    G: np.ndarray
+    U: List[np.ndarray]
+    resid: List[float]     # r_0 (the initial guess), r_1 .. r_k
+    iters: int             # cycles performed (k)
+    converged: bool        # the change test fired before max_iters
+
+
+def hooi(a: np.ndarray, us0: Sequence[np.ndarray], tol: float = 1e-12,
+         max_iters: int = 50) -> HOOIResult:
+    """Higher-order orthogonal iteration from the initial factors ``us0``.
+
+    Cycle k, for n = 0 .. N-1:  Y = A x_{m != n} U_m^T  (current factors);
+    U_n = the R_n leading left singular vectors of Y_(n). Then G = Y x_n U_n^T
+    for the last n, r_k = ||A - G x U|| / ||A||, and the loop stops once
+    |r_{k-1} - r_k| < tol (reading R10).
+    """
+    a = np.asarray(a, dtype=np.float64)
+    N = a.ndim
+    us = [np.array(u, dtype=np.float64) for u in us0]
+    ranks = [u.shape[1] for u in us]
+    resid = [rel_error(a, project(a, us), us)]
+    g = None
+    converged = False
+    k = 0
+    for k in range(1, max_iters + 1):
+        for n in range(N):
+            y = _partial(a, us, n, transpose=True)
+            us[n] = _leading_left(unfold(y, n), ranks[n])[0]
+        g = mode_product(y, us[N - 1].T, N - 1)
+        resid.append(rel_error(a, g, us))
+        if abs(resid[-2] - resid[-1]) < tol:
+            converged = True
+            break
+    if g is None:
+        g = project(a, us)
+    return HOOIResult(G=g, U=us, resid=resid, iters=k, converged=converged)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5: singular vectors from the t-HOSVD-ALS basis (reading R11)
+# ---------------------------------------------------------------------------
+
+def sign_fix(u: np.ndarray) -> np.ndarray:
+    """Flip each column so that its entry of largest magnitude is positive
+    (first such entry on ties; reading R11)."""
+    u = np.array(u, dtype=np.float64)
+    idx = np.argmax(np.abs(u), axis=0)
+    s = np.sign(u[idx, np.arange(u.shape[1])])
+    s[s == 0] = 1.0
+    return u * s
+
+
+def singular_vectors(a: np.ndarray, n: int, qhat: np.ndarray):
+    """U^(n) = Qhat U and the singular values S, where Qhat^T A_(n) = U S V^T
+    (Sec. 5, after Alg. 4), signs fixed by ``sign_fix``."""
+    m = unfold(np.asarray(a, dtype=np.float64), n)
+    q = np.asarray(qhat, dtype=np.float64)
+    u, s, _ = np.linalg.svd(q.T @ m, full_matrices=False)
+    return sign_fix(q @ u), s
 
 
 def rel_error(a: np.ndarray, g: np.ndarray, us: Sequence[np.ndarray]) -> float:

@@ -24,6 +24,12 @@ the workloads the benchmark times):
 * ``A = A0 + E``, cast to the requested dtype. Consumers that need FP64 read
   ``float64(A)`` so that every side sees the same numbers.
 
+The CP-model workload (``cp_model``) follows Sec. 6.1.1 instead: ``A0 =
+sum_r lambda_r a_r o b_r o c_r`` with unit-norm Gaussian vectors ``a_r``
+(``I``), ``b_r`` (``J = I``), ``c_r`` (``K = 100 I``), ``lambda_r ~ U[5, 10]``,
+``R = 0.2 I`` terms, and ABSOLUTE noise ``A = A0 + delta E``, ``E`` i.i.d.
+N(0, 1), ``delta = 1e-4`` (Sec. 6.1's noise model).
+
 Seeds follow ``2004025830 + cfg`` for the named configurations.
 """
 from __future__ import annotations
@@ -117,6 +123,46 @@ def planted(seed: int, dims: Sequence[int], ranks: Sequence[int],
                    factors=factors, noise_rel=noise_rel, seed=seed)
 
 
+@dataclasses.dataclass
+class CPModel:
+    A: np.ndarray            # the input tensor, in the requested dtype
+    lam: np.ndarray          # the R weights lambda_r
+    factors: List[np.ndarray]   # a (I x R), b (J x R), c (K x R), unit-norm columns
+    delta: float
+    seed: int
+
+
+def cp_model(seed: int, I: int, R: int = None, delta: float = 1e-4, dtype=np.float32,
+             k_ratio: int = 100, work_dtype=None) -> CPModel:
+    """Sec. 6.1.1's random low CP-rank tensor plus absolute Gaussian noise.
+
+    Shape ``I x I x k_ratio*I`` (the paper: ``k_ratio = 100``), ``R = round(0.2 I)``
+    terms unless given; the truncation the paper applies is ``(R, R, R)``.
+    """
+    I = int(I)
+    J, K = I, int(k_ratio) * I
+    R = max(1, int(round(0.2 * I))) if R is None else int(R)
+    n = I * J * K
+    if work_dtype is None:
+        work_dtype = np.float64 if n <= (1 << 26) else np.float32
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fac = []
+    for d in (I, J, K):
+        x = rng.standard_normal((d, R))
+        fac.append(x / np.linalg.norm(x, axis=0))
+    lam = rng.uniform(5.0, 10.0, size=R)
+    # entry (i, j, k) = sum_r lam_r a[i, r] b[j, r] c[k, r]: the (i, j) pairs as rows
+    ab = ((fac[0] * lam)[:, None, :] * fac[1][None, :, :]).reshape(I * J, R)
+    a0 = (ab.astype(work_dtype) @ fac[2].T.astype(work_dtype)).reshape(I, J, K)
+    if delta > 0:
+        e = rng.standard_normal(a0.shape, dtype=np.float32 if work_dtype == np.float32
+                                else np.float64)
+        a0 += (delta * e).astype(work_dtype)
+        del e
+    return CPModel(A=np.ascontiguousarray(a0, dtype=dtype), lam=lam, factors=fac,
+                   delta=float(delta), seed=seed)
+
+
 def uniform_tensor(seed: int, dims: Sequence[int], dtype=np.float32) -> np.ndarray:
     """Plain U[-1, 1) tensor (gradient and projection tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -158,6 +204,12 @@ CONFIGS = {
     "d1024_f32": Config("d1024_f32", (1024, 1024, 512), (64, 64, 32), "inv_k", 1e-2,
                         1e-6, "f32", SEED_BASE + 4),
 }
+
+
+# Sec. 6.1.1's CP-model sizes: I = 20 .. 100 (step 20), shape I x I x 100 I,
+# truncation (0.2 I, 0.2 I, 0.2 I), delta = 1e-4; the largest is 100 x 100 x 10000
+CP_SIZES = (20, 40, 60, 80, 100)
+CP_SEED = SEED_BASE + 6
 
 
 def make(cfg: Config, **kw) -> Planted:
