@@ -306,6 +306,58 @@ tals_status tals_sweep_pass_noalloc(const void* A, int ndim, const int64_t* dims
                                     const void* Q, int R, double* Y_out, double* wnorm2_out,
                                     void* stream);
 
+/* Statistics of tals_hooi. */
+typedef struct {
+  int iters;                          /* HOOI cycles performed (k) */
+  int converged;                      /* 1: |r_{k-1} - r_k| < tol fired before max_iters */
+  double resid0;                      /* r_0 = ||A - G0 x U0|| / ||A|| of the initial guess */
+  double resid;                       /* r_k after the last cycle */
+  int inner_sweeps[TALS_MAX_NDIM];    /* ALS R-updates of mode n, summed over the cycles */
+} tals_hooi_stats;
+
+/* HOOI (higher-order orthogonal iteration) refinement of a Tucker approximation of
+ * the context's tensor A, started from the factors in U_io -- Sec. 6.3 runs it from
+ * the t-/st-HOSVD(-ALS) results (e.g. the U_out of st_hosvd or t_hosvd).
+ * Cycle k (k = 1 .. max_iters), modes n = 0 .. N-1 in turn:
+ *   Y = A x_{m != n} U_m^T  (the factors already updated in this cycle);
+ *   U_n = an orthonormal basis of the dominant R_n-dim left subspace of Y_(n),
+ *         found by the ALS of Alg. 3 on Y_(n) started from L_0 = U_n (instead of
+ *         the Sec. 4 sketch), with the Eq. 5.01 stop rule at tolerance inner_eta
+ *         (relative to ||A||; negative: never stop early) and at most inner_sweeps
+ *         R-updates per mode and cycle;
+ * then G = Y x_N U_N^T and r_k = sqrt(||A||^2 - ||G||^2) / ||A||. Stops after the
+ * first cycle with |r_{k-1} - r_k| < tol (r_0: the initial guess), or after
+ * max_iters cycles. The identity for r_k assumes orthonormal U (true of every
+ * factor it writes); in FP32 it cancels, so r_k is resolved only to about
+ * sqrt(1e-7) -- use FP64 contexts for tolerances like Sec. 6.3's 1e-12.
+ * U_io: N device buffers (I_n x R_n, dtype), read as the initial guess (orthonormal
+ * columns) and overwritten with the refined factors. G_out: device buffer of
+ * prod R_n (dtype) for the final core, or NULL. resid_out: host array of
+ * max_iters + 1 doubles (r_0 .. r_k), or NULL. stats: host, or NULL.
+ * Uses the context's workspace and stream-ordered scratch (two tensors of the
+ * largest partial projection); synchronises the stream once per cycle.
+ * TALS_EINVAL for NULL U_io entries, max_iters < 1, inner_sweeps < 1, tol < 0 or
+ * a zero tensor; TALS_ENOTSUP if a partial projection is outside the pass limits;
+ * TALS_ESINGULAR as for the ALS. */
+tals_status tals_hooi(tals_ctx* ctx, void* const* U_io, void* G_out, double tol, int max_iters,
+                      double inner_eta, int inner_sweeps, double* resid_out, tals_hooi_stats* stats);
+
+/* Singular vectors from a t-HOSVD-ALS basis (Sec. 5, after Alg. 4): for the
+ * context's tensor A and Qhat (device, I_n x R_n, dtype, orthonormal columns --
+ * U^(n) as t_hosvd returns it), the SVD Qhat^T A_(n) = U S V^T gives
+ * U_out = Qhat U (device, I_n x R_n, dtype) and sigma_out = S (host, R_n doubles,
+ * descending). Formed through the R_n x R_n Gram M = Qhat^T A_(n) A_(n)^T Qhat --
+ * one read of A by the fused sweep pass with Qhat as its basis -- and the
+ * eigendecomposition M = V diag(S^2) V^T by cyclic Jacobi rotations in FP64
+ * (U = V); S_r = sqrt(max(lambda_r, 0)), so singular values far below S_1 carry
+ * an absolute error of about 1e-16 S_1^2 / S_r (FP64 data). The sign of each column
+ * of U_out makes its entry of largest magnitude positive (the first on ties).
+ * Qhat and U_out must not alias. TALS_EINVAL for bad arguments; TALS_ENOTSUP if
+ * the Jacobi sweeps do not converge (not expected for a symmetric M).
+ * Synchronises the stream. */
+tals_status tals_singular_vectors(tals_ctx* ctx, int mode, const void* Qhat, void* U_out,
+                                  double* sigma_out);
+
 /* Free a context (its workspace, graphs and owned buffers). NULL is allowed. */
 void tals_destroy(tals_ctx* ctx);
 

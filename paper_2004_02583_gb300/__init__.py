@@ -57,6 +57,12 @@ class tals_stats(ctypes.Structure):
                 "order": list(self.order[:ndim]), "status": self.status}
 
 
+class tals_hooi_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("resid0", ctypes.c_double), ("resid", ctypes.c_double),
+                ("inner_sweeps", ctypes.c_int * MAX_NDIM)]
+
+
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
 _IP = ctypes.POINTER(ctypes.c_int)
@@ -104,6 +110,11 @@ SIGNATURES = {
                                        ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     "tals_sweep_pass_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _I64P, ctypes.c_int, _VP,
                                                ctypes.c_int, _VP, _VP, _VP]),
+    "tals_hooi": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(tals_hooi_stats)]),
+    "tals_singular_vectors": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP,
+                                             ctypes.POINTER(ctypes.c_double)]),
     "tals_destroy": (None, [_VP]),
     "tals_last_error": (ctypes.c_char_p, []),
     "tals_version": (ctypes.c_char_p, []),
@@ -327,6 +338,49 @@ class Context:
         _check(lib().als_mode_finish(self._h, int(mode), U.data_ptr(), int(bool(truncate))))
         return U
 
+
+    def hooi(self, Us, G=None, tol: float = 1e-12, max_iters: int = 50,
+             inner_eta: float = 1e-12, inner_sweeps: int = 20):
+        """HOOI refinement (Sec. 6.3) started from the factors Us (overwritten with
+        the refined ones). Returns (G, Us, info) with info = {"iters", "converged",
+        "resid" (r_0 .. r_k), "inner_sweeps"}."""
+        torch = _torch()
+        if len(Us) != self.ndim:
+            raise ValueError(f"{self.ndim} factor buffers expected, got {len(Us)}")
+        if G is None:
+            G = torch.empty(self.ranks, dtype=self.dtype, device=self.A.device)
+        _expect(G, self.ranks, self.dtype, "G")
+        for n, u in enumerate(Us):
+            _expect(u, (self.dims[n], self.ranks[n]), self.dtype, f"U[{n}]")
+        _require_cuda(G, *Us)
+        if int(max_iters) < 1:
+            raise ValueError("max_iters must be >= 1")
+        hist = (ctypes.c_double * (int(max_iters) + 1))()
+        st = tals_hooi_stats()
+        _check(lib().tals_hooi(self._h, _ptrs(Us), G.data_ptr(), float(tol), int(max_iters),
+                               float(inner_eta), int(inner_sweeps), hist, ctypes.byref(st)))
+        info = {"iters": st.iters, "converged": bool(st.converged),
+                "resid": list(hist[:st.iters + 1]),
+                "inner_sweeps": list(st.inner_sweeps[:self.ndim])}
+        return G, Us, info
+
+    def singular_vectors(self, mode: int, Qhat, U=None):
+        """Singular vectors of the mode-`mode` unfolding from the t-HOSVD-ALS basis
+        Qhat (Sec. 5): returns (U, sigma) with U = Qhat V, sigma descending."""
+        torch = _torch()
+        if not (0 <= int(mode) < self.ndim):
+            raise ValueError(f"mode {mode} outside 0..{self.ndim - 1}")
+        shape = (self.dims[mode], self.ranks[mode])
+        _expect(Qhat, shape, self.dtype, "Qhat")
+        if U is None:
+            U = torch.empty(shape, dtype=self.dtype, device=self.A.device)
+        _expect(U, shape, self.dtype, "U")
+        _require_cuda(Qhat, U)
+        if U.data_ptr() == Qhat.data_ptr():
+            raise ValueError("U must not alias Qhat")
+        sig = (ctypes.c_double * self.ranks[mode])()
+        _check(lib().tals_singular_vectors(self._h, int(mode), Qhat.data_ptr(), U.data_ptr(), sig))
+        return U, list(sig)
 
     def time_sweep(self, mode: int = 0, engine: str = "tf32", iters: int = 10):
         """Per-pass mean durations (ms) and algorithmic bytes of one sweep's product

@@ -136,6 +136,15 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
       d[m] = c->ranks[m];
     }
   }
+  // HOOI shapes (Sec. 6.3): the ALS of mode n on A x_{m != n} U_m^T and the mode
+  // products forming it (smaller views of the same modes; a view outside the pass
+  // limits only makes tals_hooi return TALS_ENOTSUP)
+  {
+    std::vector<ViewR> sw, pr;
+    hooi_views(N, c->dims, c->ranks, &sw, &pr, nullptr);
+    for (const ViewR& x : sw) need.add_mode(c->dtype, x.v, x.R, c->sms, true);
+    for (const ViewR& x : pr) need.add_mode(c->dtype, x.v, x.R, c->sms, false);
+  }
   const size_t esz = c->esz;
   cudaStream_t s = c->stream;
   auto al = [&](void** p, size_t bytes) -> cudaError_t {

@@ -3,6 +3,7 @@
 
 #include <cstdarg>
 #include <cstddef>
+#include <vector>
 
 #include "../../include/tals.h"
 #include "kernels.h"
@@ -51,6 +52,8 @@ tals_status mode_init_tail(tals_ctx* c, const ModeJob& j, bool set_norm_a, int g
 tals_status read_states(tals_ctx* c);
 tals_status run_mode(tals_ctx* c, ModeJob& j, bool set_norm_a);
 tals_status mode_loop_host(tals_ctx* c, const ModeJob& j, int max_iters);
+// TALS_ESINGULAR with a message when mode n's state reports a failed factorisation.
+tals_status mode_status(tals_ctx* c, int n);
 // Error flags of the tensor-core passes (BF16 and split-precision).
 tals_status tc_check(tals_ctx* c);
 // t-HOSVD relative error from ||A||^2 (na2), ||G||^2 (g2) and the mode states (read
@@ -60,6 +63,22 @@ tals_status tc_check(tals_ctx* c);
 // of the stored A x_N U_N^T, which does not rest on ||A||^2 - ||W||^2 of
 // tensor-core products.
 double t_hosvd_rel_err(const tals_ctx* c, double na2, double g2);
+
+// hooi.cu: HOOI refinement (Sec. 6.3) and singular vectors (Sec. 5)
+struct ViewR {
+  ModeView v;
+  int R;
+};
+// Modes other than skip (-1: all) in the order of a projection chain.
+std::vector<int> hooi_chain(int N, const long long* dims, const int* ranks, int skip);
+// The views HOOI runs on: the ALS of mode n on Y = A x_{m != n} U_m^T (sweeps), the
+// mode products forming every Y and the initial core (products), and the largest
+// product output (inter_elems).
+void hooi_views(int N, const long long* dims, const int* ranks, std::vector<ViewR>* sweeps,
+                std::vector<ViewR>* products, size_t* inter_elems);
+tals_status hooi_run(tals_ctx* c, void* const* U, void* G_out, double tol, int max_iters, double inner_eta,
+                     int inner_sweeps, double* resid_out, tals_hooi_stats* hs);
+tals_status singular_vectors_run(tals_ctx* c, int mode, const void* Qhat, void* U_out, double* sigma_out);
 
 // graph.cu: whole decompositions as one CUDA graph per context and output set
 tals_status st_hosvd_graph(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st);
