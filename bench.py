@@ -346,6 +346,30 @@ def main():
         c3[prec] = timed(lambda: c.st_hosvd(G3, U3), max(3, args.steps // 2))
         c.close()
     del A3
+    # the CP-model workload of Sec. 6.1.1 at its largest size: 100 x 100 x 10000 FP32,
+    # truncation (20, 20, 20), lambda_r in [5, 10], absolute noise 1e-4 (400 MB, larger
+    # than L2); the third mode (10000) runs the two-pass sweep
+    cpm = W.cp_model(W.CP_SEED, 100, dtype=np.float32)
+    Acp = torch.from_numpy(cpm.A).cuda()
+    rcp = (20, 20, 20)
+    Gcp = torch.empty(rcp, device="cuda")
+    Ucp = [torch.empty((d, 20), device="cuda") for d in cpm.A.shape]
+    cp = {}
+    for drv in ("st", "t"):
+        c = tals.Context(Acp, rcp, eta=1e-4, seed=1, use_graph=not args.no_graph)
+        fn = (lambda: c.st_hosvd(Gcp, Ucp)) if drv == "st" else (lambda: c.t_hosvd(Gcp, Ucp))
+        cp[drv] = timed(fn, max(3, args.steps // 2))
+        c.close()
+    del Acp, cpm
+    # HOOI refinement (Sec. 6.3) started from the 512^3 st-HOSVD-ALS factors, FP32,
+    # stop at a residual change below 1e-5 (FP32 resolves r to about 1e-5 here)
+    Uh = [u.clone() for u in Us]
+    Gh = torch.empty(RANKS, device="cuda")
+
+    def run_hooi():
+        V = [u.clone() for u in Uh]
+        return nctx.hooi(V, G=Gh, tol=1e-5, max_iters=10, inner_eta=1e-9, inner_sweeps=10)
+    hooi_ms, (_, _, hinfo) = timed(run_hooi, 3)
 
     # end to end through the C ABI with host buffers (H2D of A, D2H of G and U)
     e_ms, e_single_ms, h2d, d2h = None, None, 0, 0
@@ -471,6 +495,17 @@ def main():
                        "rel_err_gap": abs(c3["mixed_bf16"][1][2]["rel_err"] - c3["native"][1][2]["rel_err"]),
                        "mixed_sweeps": c3["mixed_bf16"][1][2]["sweeps"],
                        "fp32_plain_sweeps": c3["native"][1][2]["sweeps"]},
+                   "cp_model_100": {
+                       "workload": "CP model (Sec. 6.1.1) 100x100x10000 FP32, 20 terms, lambda in "
+                                   "[5,10], noise 1e-4, truncation (20,20,20), eta 1e-4",
+                       "st_hosvd_ms": round(cp["st"][0], 4), "t_hosvd_ms": round(cp["t"][0], 4),
+                       "st_rel_err": cp["st"][1][2]["rel_err"], "t_rel_err": cp["t"][1][2]["rel_err"],
+                       "st_sweeps": cp["st"][1][2]["sweeps"], "t_sweeps": cp["t"][1][2]["sweeps"]},
+                   "hooi": {"workload": "HOOI (Sec. 6.3) from the 512^3 st-HOSVD-ALS factors, FP32, "
+                                       "tol 1e-5, inner ALS eta 1e-9",
+                            "ms": round(hooi_ms, 4), "cycles": hinfo["iters"],
+                            "resid0": hinfo["resid"][0], "resid": hinfo["resid"][-1],
+                            "inner_sweeps": hinfo["inner_sweeps"]},
                    "t_hosvd": {"fp32_plain_ms": round(t_ms["fp32_plain"], 4),
                                "mixed_ms": round(t_ms["mixed"], 4),
                                "fp32_plain_rel_err": t_rel["fp32_plain"], "mixed_rel_err": t_rel["mixed"]},

@@ -32,10 +32,12 @@
  *   error, TALS_ESINGULAR when an R x R Gram matrix is not numerically positive
  *   definite (the truncation exceeds the numerical rank, Remark 3), TALS_ENOTSUP
  *   for shapes outside the kernels' limits. Contexts (tucker_als_init*): R_n <= 64
- *   (checked on the host) and every mode view must fit the fused pass's shared
- *   memory -- I_n up to 1920 in FP32 and 852 in FP64 at the smallest tile shapes,
- *   less for some ranks (checked per mode at init, before any sweep). The Tucker
- *   operators (reconstruct, project and their adjoints) take any sizes and ranks.
+ *   (checked on the host). A mode view whose I_n fits the fused sweep pass's
+ *   shared-memory tile (up to 1920 in FP32 and 852 in FP64 at the smallest tile
+ *   shapes, less for some ranks) reads the tensor once per sweep; a longer mode
+ *   runs the same sweep as two tiled products (W = B^T Q, then Y = B W), reading
+ *   it twice. The Tucker operators (reconstruct, project and their adjoints) take
+ *   any sizes and ranks.
  *   tals_last_error() returns a
  *   thread-local message for the last failure. Not converging within
  *   max_sweeps is TALS_OK with converged[n] = 0.

@@ -64,12 +64,22 @@ struct Need {
   size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0, qs = 0;
   void add_mode(int dtype, const ModeView& v, int R, int sms, bool sweep) {
     PassConfig pc = pass_config(dtype, v, R, sms);
-    if (!pc.ok) return;
-    if (sweep) ypart = std::max(ypart, (size_t)pc.grid_x * (size_t)v.I * (size_t)R);
-    spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
     RowPlan rp = row_plan(v.I, R, sms);
     gpart = std::max(gpart, (size_t)rp.blocks * (size_t)R * (size_t)R);
     ir = std::max(ir, (size_t)v.I * (size_t)R);
+    if (!pc.ok) {
+      // beyond the fused pass: the two-pass sweep (Y and its column-split partials
+      // in Ypart, W in a scratch tensor buffer) or the tiled mode product, both
+      // with ||.||^2 partials over a fixed grid
+      spart = std::max(spart, (size_t)kSumsqParts);
+      if (sweep) {
+        ypart = std::max(ypart, (size_t)(twopass_splits(v, R, sms) + 1) * (size_t)v.I * (size_t)R);
+        tbuf = std::max(tbuf, (size_t)(v.J() * R));
+      }
+      return;
+    }
+    if (sweep) ypart = std::max(ypart, (size_t)pc.grid_x * (size_t)v.I * (size_t)R);
+    spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
     if (sweep && dtype == TALS_F32 && t32_supported(v, R)) {
       // split-precision passes: per-CTA Y partials, W written every sweep (into a
       // scratch tensor buffer where the mode has no destination), the split basis
@@ -103,10 +113,6 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     for (int idx = 0; idx < N; ++idx) {
       const int n = c->order[idx];
       ModeView v = view_of(d, N, n);
-      PassConfig pc = pass_config(c->dtype, v, c->ranks[n], c->sms);
-      if (!pc.ok)
-        return fail(TALS_ENOTSUP, "mode %d: size %lld with rank %d exceeds the pass kernel limits",
-                    n, v.I, c->ranks[n]);
       need.add_mode(c->dtype, v, c->ranks[n], c->sms, true);
       if (idx < N - 1) need.tbuf = std::max(need.tbuf, (size_t)(v.J() * c->ranks[n]));
       d[n] = c->ranks[n];
@@ -118,10 +124,6 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     for (int m = 0; m < N; ++m) d[m] = c->dims[m];
     for (int n = 0; n < N; ++n) {
       ModeView v = view_of(d, N, n);
-      PassConfig pc = pass_config(c->dtype, v, c->ranks[n], c->sms);
-      if (!pc.ok)
-        return fail(TALS_ENOTSUP, "mode %d: size %lld with rank %d exceeds the pass kernel limits",
-                    n, v.I, c->ranks[n]);
       need.add_mode(c->dtype, v, c->ranks[n], c->sms, true);
     }
     ModeView v = view_of(d, N, N - 1);
@@ -129,8 +131,6 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     d[N - 1] = c->ranks[N - 1];
     for (int m = 0; m < N - 1; ++m) {
       ModeView w = view_of(d, N, m);
-      PassConfig pc = pass_config(c->dtype, w, c->ranks[m], c->sms);
-      if (!pc.ok) return fail(TALS_ENOTSUP, "projection of mode %d exceeds the kernel limits", m);
       need.add_mode(c->dtype, w, c->ranks[m], c->sms, false);
       need.tbuf = std::max(need.tbuf, (size_t)(w.J() * c->ranks[m]));
       d[m] = c->ranks[m];
@@ -203,7 +203,6 @@ constexpr bool kT32Auto = false;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
-  if (!j.pc.ok) return fail(TALS_ENOTSUP, "pass kernel limits exceeded (I=%lld R=%d)", j.v.I, j.R);
   j.rp = row_plan(j.v.I, j.R, c->sms);
   j.st = c->st + j.n;
   // FP32: on tensors up to a quarter of the input (and at least 16M elements) the
@@ -213,6 +212,24 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   long long tot = 1;
   for (int m = 0; m < c->N; ++m) tot *= c->dims[m];
   const long long mine = j.v.P * j.v.I * j.v.Q;
+  j.twopass = 0;
+  if (!j.pc.ok) {
+    // I_n beyond the fused pass: two tiled products per sweep, W in the destination
+    // or a scratch tensor buffer other than the input
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    const size_t ir = (size_t)j.v.I * j.R;
+    j.splits = twopass_splits(j.v, j.R, c->sms);
+    if (w == j.X || (size_t)(j.splits + 1) * ir > c->ypart_elems || ir > c->need_ir ||
+        c->spart_n < (size_t)kSumsqParts)
+      return fail(TALS_ENOTSUP, "mode %d (I=%lld, R=%d) exceeds the context's workspace", j.n, j.v.I, j.R);
+    j.twopass = 1;
+    j.t32 = 0;
+    j.resid = 0;
+    j.resid_kernel = (c->dtype == TALS_F32) && mine <= std::max(tot / 4, 16LL << 20);
+    j.Wt = w;
+    return TALS_OK;
+  }
   j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 &&
             mine <= std::max(tot / 4, 16LL << 20);
   // the same tensors with the rank split across CTAs cannot form the residual
@@ -260,6 +277,7 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
   TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
                             j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32));
+  if (j.twopass) return twopass_init_launch(c, j, set_norm_a);
   if (j.t32) {
     // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
     TALS_CK(launch_t32_ypass((const float*)j.X, j.v, R, nullptr, nullptr, (float*)c->Ypart, c->spart,
@@ -302,6 +320,7 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   const int R = j.R;
   const long long I = j.v.I;
   cudaError_t e;
+  if (j.twopass) return twopass_sweep_launch(c, j);
   if (j.t32) {
     // split-precision passes: W = B^T Q_k (written), then Y = B W with the residual
     // ||B - Q_k W^T||^2 -- e_k of the stop rule -- from the same read of B
@@ -331,7 +350,7 @@ tals_status mode_sweep_tail(tals_ctx* c, const ModeJob& j, int gx, int nsp, int 
   // e_k^2 = ||B - Q W^T||^2 from this sweep's W (written by the pass) into sW;
   // the Y partials are consumed, so their buffer holds the residual partials
   if (j.resid_kernel && test_op == 1)
-    TALS_CK(launch_mode_residual((const float*)j.X, j.v, R, (const float*)j.Wdest,
+    TALS_CK(launch_mode_residual((const float*)j.X, j.v, R, (const float*)(j.twopass ? j.Wt : j.Wdest),
                                  (const float*)c->Lt, (double*)c->Ypart, (long long)(c->ypart_elems / 2),
                                  j.st, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s, c->dtype == TALS_F32));
@@ -680,12 +699,8 @@ tals_status t_hosvd(tals_ctx* c, void* G_out, void* const* U_out, tals_stats* st
   int nsp = 0;
   for (int m = 0; m < N - 1; ++m) {
     ModeView v = view_of(d, N, m);
-    PassConfig pc = pass_config(c->dtype, v, c->ranks[m], c->sms);
     void* dest = (m == N - 2) ? G_out : c->tbuf[(m + 1) & 1];
-    cudaError_t e = launch_pass(c->dtype, pc, PASS_PROJECT, cur, v, c->ranks[m], U_out[m],
-                                nullptr, c->spart, dest, 0, nullptr, 0, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "projection pass");
-    nsp = pc.grid_x * pc.grid_y;
+    if ((st = project_mode(c, cur, v, c->ranks[m], U_out[m], dest, &nsp)) != TALS_OK) return st;
     cur = dest;
     d[m] = c->ranks[m];
   }

@@ -158,12 +158,9 @@ tals_status build(tals_ctx* c, int kind, void* G_out, void* const* U_out, GraphE
     const void* cur = c->tbuf[0];
     for (int m = 0; m < N - 1 && st == TALS_OK; ++m) {
       ModeView v = view_of(d, N, m);
-      PassConfig pc = pass_config(c->dtype, v, c->ranks[m], c->sms);
       void* dest = (m == N - 2) ? G_out : c->tbuf[(m + 1) & 1];
-      e = launch_pass(c->dtype, pc, PASS_PROJECT, cur, v, c->ranks[m], U_out[m], nullptr,
-                      c->spart, dest, 0, nullptr, 0, cs);
-      if (e != cudaSuccess) st = cuda_fail(e, "projection pass");
-      out->nsp = pc.grid_x * pc.grid_y;
+      c->stream = cs;   // project_mode launches on the context's stream
+      st = project_mode(c, cur, v, c->ranks[m], U_out[m], dest, &out->nsp);
       cur = dest;
       d[m] = c->ranks[m];
     }

@@ -27,58 +27,10 @@ namespace tals {
 
 namespace {
 
-constexpr int kSqThreads = 256;
-constexpr int kSqBlocks = 512;    // fixed: the partial sums are added in a fixed order
 constexpr int kJacThreads = 256;
 constexpr int kJacMaxSweeps = 40;
 constexpr int kMaxR = 64;
 constexpr size_t kJacSmem = 2 * kMaxR * (kMaxR + 1) * sizeof(double);
-
-// ---------------------------------------------------------------------------
-// ||x||^2 in FP64: per-block partials over a fixed grid, then one block adds
-// them in index order (deterministic for a given n).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kSqThreads) sumsq_part_kernel(const T* __restrict__ x, size_t n,
-                                                                double* __restrict__ part) {
-  __shared__ double red[kSqThreads];
-  double acc = 0.0;
-  for (size_t i = (size_t)blockIdx.x * kSqThreads + threadIdx.x; i < n; i += (size_t)gridDim.x * kSqThreads) {
-    const double v = (double)x[i];
-    acc = fma(v, v, acc);
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = kSqThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-__global__ void __launch_bounds__(kSqThreads) sum_parts_kernel(const double* __restrict__ part, int nb,
-                                                               double* __restrict__ out) {
-  __shared__ double red[kSqThreads];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += kSqThreads) acc += part[i];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = kSqThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
-}
-
-// *out = ||x||^2; part: kSqBlocks doubles of scratch.
-cudaError_t launch_sumsq(int dtype, const void* x, size_t n, double* part, double* out, cudaStream_t s) {
-  if (dtype == TALS_F32)
-    sumsq_part_kernel<float><<<kSqBlocks, kSqThreads, 0, s>>>((const float*)x, n, part);
-  else
-    sumsq_part_kernel<double><<<kSqBlocks, kSqThreads, 0, s>>>((const double*)x, n, part);
-  sum_parts_kernel<<<1, kSqThreads, 0, s>>>(part, kSqBlocks, out);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Symmetric eigendecomposition M = V diag(lam) V^T (R <= 64, FP64) by the cyclic
@@ -352,15 +304,9 @@ tals_status project_chain(tals_ctx* c, const void* X, long long* d, const std::v
   for (size_t k = 0; k < ms.size(); ++k) {
     const int m = ms[k];
     const ModeView v = view_of(d, c->N, m);
-    const PassConfig pc = pass_config(c->dtype, v, c->ranks[m], c->sms);
-    if (!pc.ok || (size_t)pc.grid_x * pc.grid_y > c->spart_n)
-      return fail(TALS_ENOTSUP, "HOOI: the mode-%d product (size %lld -> %d) exceeds the pass limits", m, v.I,
-                  c->ranks[m]);
     void* dest = (k + 1 == ms.size() && last) ? last : (cur == bufs[0] ? bufs[1] : bufs[0]);
-    cudaError_t e = launch_pass(c->dtype, pc, PASS_PROJECT, cur, v, c->ranks[m], U[m], nullptr, c->spart,
-                                dest, 0, nullptr, 0, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "HOOI mode product");
-    *nsp = pc.grid_x * pc.grid_y;
+    tals_status st = project_mode(c, cur, v, c->ranks[m], U[m], dest, nsp);
+    if (st != TALS_OK) return st;
     d[m] = c->ranks[m];
     cur = dest;
   }
@@ -399,7 +345,7 @@ tals_status hooi_run(tals_ctx* c, void* const* U, void* G_out, double tol, int m
   if (e == cudaSuccess) bufs[1] = sc.get(inter * esz, &e);
   void* G = G_out;
   if (e == cudaSuccess && !G) G = sc.get(gsize * esz, &e);
-  double* part = e == cudaSuccess ? (double*)sc.get(kSqBlocks * sizeof(double), &e) : nullptr;
+  double* part = e == cudaSuccess ? (double*)sc.get(kSumsqParts * sizeof(double), &e) : nullptr;
   double* dsc = e == cudaSuccess ? (double*)sc.get(4 * sizeof(double), &e) : nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "HOOI scratch");
   tals_hooi_stats st;
@@ -500,9 +446,20 @@ tals_status singular_vectors_run(tals_ctx* c, int mode, const void* Qhat, void* 
                              nullptr, s));
   TALS_CK(launch_copy(c->Lt, Qhat, (size_t)I * R * c->esz, s));
   // W = A_(n)^T Qhat, Y = A_(n) W; M = Qhat^T Y = (Qhat^T A_(n)) (Qhat^T A_(n))^T
-  TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, c->A, j.v, R, c->Lt, c->Ypart, c->spart, nullptr, 0, j.st, 1, s));
-  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, j.pc.grid_x, I, R, c->Y64, 2, c->L64, c->Gpart, j.rp, c->spart,
-                             j.pc.grid_x * j.pc.grid_y, 1, j.st, nullptr, s));
+  int gx = 1, nsp = 0;
+  if (j.twopass) {
+    const size_t ir = (size_t)I * R;
+    TALS_CK(launch_mode_project_any(c->dtype, c->A, j.v, c->Lt, R, j.Wt, s));
+    TALS_CK(launch_mode_adjoint_any(c->dtype, c->A, j.v, j.Wt, R, j.splits, (char*)c->Ypart + ir * c->esz,
+                                    c->Ypart, s));
+  } else {
+    TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, c->A, j.v, R, c->Lt, c->Ypart, c->spart, nullptr, 0, j.st, 1,
+                        s));
+    gx = j.pc.grid_x;
+    nsp = j.pc.grid_x * j.pc.grid_y;
+  }
+  TALS_CK(launch_reduce_rows(c->dtype, c->Ypart, gx, I, R, c->Y64, 2, c->L64, c->Gpart, j.rp, c->spart, nsp, 1,
+                             j.st, nullptr, s));
   TALS_CK(launch_gram_sum(c->Gpart, j.rp.blocks, R, c->Gfin, j.st, s));
   // M = V diag(lam) V^T; scratch in F (3 R^2 + R doubles): V, lam, info, signs
   double* V = c->F;

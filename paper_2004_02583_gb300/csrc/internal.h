@@ -24,8 +24,11 @@ struct ModeJob {
   int resid = 0;                 // sweeps measure the error from the explicit residual
   int resid_kernel = 0;          // rank split across CTAs: e_k from a residual kernel per sweep
   int t32 = 0;                   // FP32 sweeps on the split-precision (3xTF32) tensor-core passes
-  void* Wt = nullptr;            // where those passes write W every sweep (Wdest or scratch)
+  void* Wt = nullptr;            // where those passes (or the two-pass form) write W every
+                                 // sweep (Wdest or scratch)
   int g1 = 0, g2 = 0;            // their grids (W pass CTAs; Y pass column shares per chunk)
+  int twopass = 0;               // I_n beyond the fused pass: two tiled products per sweep
+  int splits = 1;                // column splits of the two-pass form's Y product
 };
 
 struct DriveState {
@@ -63,6 +66,13 @@ tals_status tc_check(tals_ctx* c);
 // of the stored A x_N U_N^T, which does not rest on ||A||^2 - ||W||^2 of
 // tensor-core products.
 double t_hosvd_rel_err(const tals_ctx* c, double na2, double g2);
+
+// twopass.cu: the mode's init and sweep for views beyond the fused pass
+tals_status twopass_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
+tals_status twopass_sweep_launch(tals_ctx* c, const ModeJob& j);
+// out = X x_n U^T (fused pass in projection mode, else the tiled mode product);
+// *nsp partial sums of ||out||^2 left in c->spart.
+tals_status project_mode(tals_ctx* c, const void* X, const ModeView& v, int R, const void* U, void* out, int* nsp);
 
 // hooi.cu: HOOI refinement (Sec. 6.3) and singular vectors (Sec. 5)
 struct ViewR {

@@ -153,6 +153,23 @@ int factor_adjoint_splits(long long P, long long I, long long Q, int R, int sms)
 template <typename T>
 cudaError_t launch_factor_adjoint_any(const T* X, long long P, long long I, long long Q, const T* V, int R,
                                       int S, T* part, T* Ubar, cudaStream_t s);
+// twopass.cu: the two-pass sweep's building blocks.
+// ||x||^2 as kSumsqParts FP64 partial sums (fixed grid), or summed into *out.
+constexpr int kSumsqParts = 512;
+cudaError_t launch_sumsq_parts(int dtype, const void* x, size_t n, double* part, cudaStream_t s);
+cudaError_t launch_sumsq(int dtype, const void* x, size_t n, double* part, double* out, cudaStream_t s);
+// S[p, r, q] = entry (p Q + q, r) of the Sec. 4 sketch drawn from `state`.
+cudaError_t launch_sketch_prq(int dtype, void* S, const ModeView& v, int R, uint64_t state, int sms,
+                              cudaStream_t s);
+// out = X x_n U^T (P x R x Q) for any view: FP32 register-tiled GEMM where it
+// applies, else plain shared-memory tiles (FP32 or FP64).
+cudaError_t launch_mode_project_any(int dtype, const void* X, const ModeView& v, const void* U, int R, void* out,
+                                    cudaStream_t s);
+// Y (I x R) = X_(n) W_(n)^T for W viewed P x R x Q, in S column splits (part: S I R
+// elements of scratch, added in order).
+int twopass_splits(const ModeView& v, int R, int sms);
+cudaError_t launch_mode_adjoint_any(int dtype, const void* X, const ModeView& v, const void* W, int R, int S,
+                                    void* part, void* Y, cudaStream_t s);
 // One CTA whose bounded mbarrier wait runs out after limit_cycles; *err = 5
 // (TALS_ETIMEOUT) afterwards. Exercises the failure path without a fault.
 cudaError_t launch_wait_timeout_probe(int* err, long long limit_cycles, cudaStream_t s);
