@@ -1,6 +1,6 @@
-"""bench.py's reference arm (the FP64 oracle timed on the host cores, a bounded
-slab of the 512^3 workload per step) prints one JSON line with the keys of the
-benchmark contract. CPU only."""
+"""bench.py's reference arm (the FP64 oracle timed on the host cores, the full
+512^3 workload per step) prints one JSON line with the keys of the benchmark
+contract. CPU only."""
 import json
 import os
 import subprocess
