@@ -1,10 +1,11 @@
 """GPU checks of the tensor-core (tcgen05, BF16) sweep pass and of the mixed-
 precision st-HOSVD-ALS against the FP64 oracle.
 
-One tensor-core pass is compared with Y = B (B^T Q) evaluated in FP64 on the
-BF16-rounded tensor and basis: W is rounded to BF16 once more between the two
-products, so Y agrees to ~2^-8 relative; ||W||^2 (FP32 accumulation of exact
-BF16 products) to 1e-5. The mixed decomposition ends with FP32 sweeps, so its
+One tensor-core pass is compared elementwise with Y = B bf16(B^T Q) evaluated
+in FP64 on the BF16-rounded tensor and basis, W rounded to BF16 between the two
+products as the pass does (bound per entry: FP32 accumulation plus at most three
+one-ulp rounding flips of W); ||W||^2 (FP32 accumulation of exact BF16 products)
+to 1e-5. The mixed decomposition ends with FP32 sweeps, so its
 result is held to the FP32 tolerances."""
 import numpy as np
 import pytest
@@ -48,10 +49,23 @@ def test_tensor_core_pass_vs_oracle(tals, dims, mode, R):
     m = O.unfold(_bf16(a), mode)
     qb = _bf16(q)
     w_ref = m.T @ qb
-    y_ref = m @ w_ref
     Y, w2 = tals.sweep_pass(A, mode, Qt, engine="tc")
     Y = Y.cpu().numpy()
-    assert np.linalg.norm(Y - y_ref) <= 1e-2 * np.linalg.norm(y_ref)
+    # elementwise: the pass rounds its FP32 W to BF16 (round to nearest) before the
+    # second product, so the reference does too; what remains is FP32 accumulation
+    # (1e-5 of the sum of |products|) and W entries whose FP32 value rounds to the
+    # other BF16 neighbour than the FP64 one (rare: within ~1e-7 of a rounding
+    # boundary), each moving Y by one BF16 ulp of |w| times |b| -- at most three per
+    # entry allowed. A wrong or missing tile moves entries by ~|Y|.
+    wb = _bf16(w_ref.astype(np.float32))
+    y_ref = m @ wb
+    acc = np.abs(m) @ np.abs(wb)
+    am = np.abs(m)
+    flip = np.stack([np.max(am * np.abs(wb[:, r])[None, :], axis=1) for r in range(wb.shape[1])], axis=1)
+    tol = 1e-5 * acc + 3 * 2.0 ** -7 * flip
+    err = np.abs(Y - y_ref)
+    assert np.all(err <= tol), (float((err / tol).max()), np.unravel_index(np.argmax(err / tol), err.shape))
+    assert np.linalg.norm(Y - y_ref) <= 1e-4 * np.linalg.norm(y_ref)
     assert abs(w2 - O.frob2(w_ref)) <= 1e-5 * O.frob2(w_ref)
     # the CUDA-core pass on the FP32 data, against FP64
     m32 = O.unfold(a.astype(np.float64), mode)
