@@ -212,7 +212,7 @@ def main():
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="c4: number of tensors (4096 is the workload; fewer for profiling)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "tucker"],
                     help="c2 (default): 512^3 FP32 st-HOSVD, the benchmark line; c1: 64^3 FP64; "
                          "c3: 128^4 FP32 mixed vs plain; c4: 4096 small tensors batched vs "
                          "per-tensor loop; c5: 1024x1024x512 forward + reconstruction-loss backward")
@@ -220,7 +220,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "c2":
-        from_extra = {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload]
+        from_extra = {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5,
+                      "tucker": run_tucker}[args.workload]
         return from_extra(args)
     global DIMS
     if args.dims:
@@ -631,6 +632,77 @@ def run_c1(args):
                              "sample": f"the full 64^3 decomposition, {n} runs"}}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_tucker(args):
+    """Sec. 6.1.2's Tucker model at the paper's sizes: I x 100 x 100 x 100 FP32,
+    I = 1000 .. 5000, truncation (I/100, 10, 10, 10), core U[5, 10], noise 1e-4,
+    eta 1e-4; st- and t-HOSVD-ALS time-to-tol per size (the long first mode runs
+    the two-pass sweep in t-HOSVD), errors against the input and the noiseless
+    base. The line's value is st-HOSVD-ALS at I = 5000 (a 20 GB tensor)."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    sizes = [int(x) for x in args.dims.split(",")] if args.dims else list(W.TUCKER_SIZES)
+    peaks, _ = _peaks()
+    clocks = Clocks(0)
+    rows, roof, clk = [], None, {}
+    for I in sizes:
+        dims, ranks = (I, 100, 100, 100), (I // 100, 10, 10, 10)
+        A = W.tucker_model_device(W.TUCKER_SEED + I, dims, ranks)
+        G = torch.empty(ranks, device="cuda")
+        Us = [torch.empty((d, r), device="cuda") for d, r in zip(dims, ranks)]
+        res = {"I": I}
+        for drv in ("st", "t"):
+            ctx = tals.Context(A, ranks, eta=1e-4, seed=1)
+            fn = (lambda: ctx.st_hosvd(G, Us)) if drv == "st" else (lambda: ctx.t_hosvd(G, Us))
+            if I == sizes[-1] and drv == "st":
+                clocks.start()
+            ms, (_, _, st) = _time_gpu(fn, args.steps, args.warmup)
+            if I == sizes[-1] and drv == "st":
+                clk = clocks.stop()
+                # the dominant kernel: the first mode's sweep pass over the whole tensor
+                m0 = st["order"][0]
+                pms, pby, _ = ctx.time_pass(mode=m0, iters=5)
+                hbm = float(peaks.get("hbm_gbs", 6800.0))
+                gbs = pby / (pms * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(gbs / hbm, 4), "traffic": None,
+                        "kernel": f"tals::pass_kernel (fused FP32 sweep, mode {m0 + 1} of the "
+                                  f"{I}x100x100x100 tensor, rank 10)",
+                        "pass_ms": round(pms, 4), "algorithmic_bytes": pby,
+                        "peak_source": f"HBM {hbm} GB/s (measured)"}
+            b = tals.reconstruct(G, Us)
+            base = W.tucker_model_device(W.TUCKER_SEED + I, dims, ranks, base_only=True)
+            e_base = float(torch.linalg.vector_norm(b - base) / torch.linalg.vector_norm(base))
+            del b, base
+            res[drv] = {"ms": round(ms, 3), "rel_err": st["rel_err"], "err_vs_noiseless": e_base,
+                        "sweeps": st["sweeps"]}
+            ctx.close()
+        rows.append(res)
+        if I == sizes[0]:
+            a_host = A.cpu().numpy().astype(np.float64)
+        del A
+        torch.cuda.empty_cache()
+    # the oracle on the host on the smallest size, as it stands
+    sec, n = _oracle_time(lambda: O.st_hosvd_als(a_host, (sizes[0] // 100, 10, 10, 10), eta=1e-4, seed=1))
+    last = rows[-1]
+    line = {"metric": "Tucker-model (Sec. 6.1.2) st-HOSVD-ALS time-to-tol",
+            "value": round(1e3 / last["st"]["ms"], 3), "unit": "st-HOSVD/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": last["st"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"Tucker model {sizes[-1]}x100x100x100 FP32, ranks "
+                                   f"({sizes[-1] // 100},10,10,10), core U[5,10], noise 1e-4, eta 1e-4",
+                       "sizes": rows, "l2": "inputs (4-20 GB) larger than L2"},
+            "roofline": roof, "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": round(1.0 / sec, 4), "unit": "st-HOSVD/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle st-HOSVD-ALS on the {sizes[0]}x100x100x100 "
+                                       f"tensor ({n} runs)"}}
+    print(json.dumps(line), flush=True)
 
 
 def _pass_rooflines(nctx, mctx, mode, sm_mhz, sms, peaks):

@@ -165,11 +165,17 @@ cudaError_t launch_sketch_prq(int dtype, void* S, const ModeView& v, int R, uint
 // applies, else plain shared-memory tiles (FP32 or FP64).
 cudaError_t launch_mode_project_any(int dtype, const void* X, const ModeView& v, const void* U, int R, void* out,
                                     cudaStream_t s);
-// Y (I x R) = X_(n) W_(n)^T for W viewed P x R x Q, in S column splits (part: S I R
-// elements of scratch, added in order).
+// Y (I x R) = X_(n) W_(n)^T for W viewed P x R x Q, in S column splits of at most
+// 2048 columns (FP32 sums stay short; at most 4096 splits), the splits added in
+// FP64 in a fixed order (part: S I R elements of scratch).
 int twopass_splits(const ModeView& v, int R, int sms);
 cudaError_t launch_mode_adjoint_any(int dtype, const void* X, const ModeView& v, const void* W, int R, int S,
                                     void* part, void* Y, cudaStream_t s);
+// The column-split partials of launch_factor_adjoint_any without their sum:
+// part[s][i][r] over the s-th of S equal column ranges (rounded up to 32).
+template <typename T>
+cudaError_t launch_factor_adjoint_parts(const T* X, long long P, long long I, long long Q, const T* V, int R,
+                                        int S, T* part, cudaStream_t s);
 // One CTA whose bounded mbarrier wait runs out after limit_cycles; *err = 5
 // (TALS_ETIMEOUT) afterwards. Exercises the failure path without a fault.
 cudaError_t launch_wait_timeout_probe(int* err, long long limit_cycles, cudaStream_t s);

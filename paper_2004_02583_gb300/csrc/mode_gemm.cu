@@ -757,6 +757,24 @@ cudaError_t launch_factor_adjoint_any(const T* X, long long P, long long I, long
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_factor_adjoint_parts(const T* X, long long P, long long I, long long Q, const T* V, int R,
+                                        int S, T* part, cudaStream_t s) {
+  if (P < 1 || I < 1 || Q < 1 || R < 1 || S < 1) return cudaErrorInvalidValue;
+  const long long J = P * Q;
+  long long jper = (J + S - 1) / S;
+  jper = (jper + 31) / 32 * 32;
+  const long long gx = (I + 31) / 32, gy = (R + 31) / 32;
+  if (gx > 0x7fffffffLL || gy > 65535 || S > 65535) return cudaErrorNotSupported;
+  factor_adjoint_any<T><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)S), 256, 0, s>>>(X, P, I, Q, V, R, jper,
+                                                                                    part);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_factor_adjoint_parts<float>(const float*, long long, long long, long long, const float*,
+                                                        int, int, float*, cudaStream_t);
+template cudaError_t launch_factor_adjoint_parts<double>(const double*, long long, long long, long long,
+                                                         const double*, int, int, double*, cudaStream_t);
 template cudaError_t launch_mode_gemm_any<float>(const float*, long long, long long, long long, const float*,
                                                  long long, long long, long long, float*, cudaStream_t);
 template cudaError_t launch_mode_gemm_any<double>(const double*, long long, long long, long long,

@@ -72,6 +72,18 @@ __global__ void __launch_bounds__(256) sketch_prq_kernel(T* __restrict__ S, long
   }
 }
 
+// out[e] = sum over s of part[s * n + e], in FP64, in order.
+template <typename T>
+__global__ void __launch_bounds__(256) sum_parts_f64_kernel(const T* __restrict__ part, int S, long long n,
+                                                            T* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += (double)part[(long long)s * n + e];
+    out[e] = (T)v;
+  }
+}
+
 unsigned elem_grid(long long n, int sms) {
   const long long want = (n + 255) / 256;
   return (unsigned)std::max<long long>(1, std::min<long long>(want, (long long)std::max(sms, 1) * 16));
@@ -115,15 +127,27 @@ cudaError_t launch_mode_project_any(int dtype, const void* X, const ModeView& v,
   return launch_mode_gemm_any((const double*)X, v.P, v.I, v.Q, (const double*)U, 1, R, R, (double*)out, s);
 }
 
-int twopass_splits(const ModeView& v, int R, int sms) { return factor_adjoint_splits(v.P, v.I, v.Q, R, sms); }
+int twopass_splits(const ModeView& v, int R, int sms) {
+  const long long by_len = (v.J() + 2047) / 2048;   // at most 2048 columns per FP32 sum
+  long long S = std::max<long long>(factor_adjoint_splits(v.P, v.I, v.Q, R, sms), by_len);
+  return (int)std::min<long long>(S, 4096);
+}
 
 cudaError_t launch_mode_adjoint_any(int dtype, const void* X, const ModeView& v, const void* W, int R, int S,
                                     void* part, void* Y, cudaStream_t s) {
-  if (dtype == TALS_F32)
-    return launch_factor_adjoint_any((const float*)X, v.P, v.I, v.Q, (const float*)W, R, S, (float*)part,
-                                     (float*)Y, s);
-  return launch_factor_adjoint_any((const double*)X, v.P, v.I, v.Q, (const double*)W, R, S, (double*)part,
-                                   (double*)Y, s);
+  cudaError_t e;
+  const long long n = v.I * R;
+  const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
+  if (dtype == TALS_F32) {
+    e = launch_factor_adjoint_parts((const float*)X, v.P, v.I, v.Q, (const float*)W, R, S, (float*)part, s);
+    if (e != cudaSuccess) return e;
+    sum_parts_f64_kernel<float><<<g, 256, 0, s>>>((const float*)part, S, n, (float*)Y);
+  } else {
+    e = launch_factor_adjoint_parts((const double*)X, v.P, v.I, v.Q, (const double*)W, R, S, (double*)part, s);
+    if (e != cudaSuccess) return e;
+    sum_parts_f64_kernel<double><<<g, 256, 0, s>>>((const double*)part, S, n, (double*)Y);
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

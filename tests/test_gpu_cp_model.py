@@ -125,3 +125,20 @@ def test_hooi_and_singular_vectors_on_a_long_mode(tals):
     for n in range(3):
         assert O.principal_angles(_np(Us[n]), ref.U[n]).max() <= 1e-7
     ctx.close()
+
+
+def test_long_mode_with_many_columns_t_hosvd(tals):
+    """The long mode's Y = B_(n) W sums 60000 columns: held to the FP32 gates, so
+    the column splits' FP32 sums must stay short (they are added in FP64)."""
+    dims, ranks = (2400, 50, 40, 30), (24, 5, 5, 5)
+    p = W.planted(W.SEED_BASE + 22, dims, ranks, "uniform510", 1e-3, dtype=np.float32)
+    a64 = p.A.astype(np.float64)
+    assert tals.pass_plan("f32", 1, 2400, 60000, 24) is None
+    ref = O.t_hosvd_als(a64, ranks, eta=1e-6, seed=6)
+    G, Us, st = tals.t_hosvd(_gpu(p.A), ranks, eta=1e-6, seed=6)
+    rel_ref = O.rel_error(a64, ref.G, ref.U)
+    rel_own = O.rel_error(a64, _np(G), [_np(u) for u in Us])
+    assert abs(rel_own - rel_ref) <= 1e-6 * max(1.0, rel_ref), (rel_own, rel_ref)
+    for n in range(4):
+        assert O.principal_angles(_np(Us[n]), ref.U[n]).max() <= 1e-4, n
+        assert abs(st["sweeps"][n] - ref.sweeps[n]) <= 1

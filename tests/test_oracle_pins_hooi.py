@@ -208,3 +208,25 @@ def test_cp_model_recipe():
     assert abs(np.std(e) - 1.0) < 0.02 and abs(np.mean(e)) < 0.02
     assert W.cp_model(7, 20).A.shape == (20, 20, 2000)
     assert len(W.cp_model(7, 20).lam) == 4
+
+
+def test_tucker_model_device_recipe():
+    """Sec. 6.1.2's Tucker model drawn with torch (here on the CPU): planted
+    multilinear rank, the projection on the leading subspaces keeps the base's
+    spectrum, absolute noise 1e-4, seeded."""
+    torch = pytest.importorskip("torch")
+    dims, ranks = (30, 9, 8, 7), (3, 2, 3, 2)
+    a = W.tucker_model_device(11, dims, ranks, device="cpu").double().numpy()
+    b = W.tucker_model_device(11, dims, ranks, device="cpu", base_only=True).double().numpy()
+    e = (a - b) / 1e-4
+    assert abs(np.std(e) - 1.0) < 0.05 and abs(np.mean(e)) < 0.05
+    for n in range(4):
+        sv = np.linalg.svd(O.unfold(b, n), compute_uv=False)
+        assert sv[ranks[n]] < 1e-5 * sv[0]
+    # the leading subspaces span the base's unfoldings
+    us = [np.linalg.svd(O.unfold(b, n), full_matrices=False)[0][:, :ranks[n]] for n in range(4)]
+    g = O.project(b, us)
+    assert np.allclose(np.sort(np.abs(np.linalg.svd(O.unfold(g, 0), compute_uv=False))),
+                       np.sort(np.linalg.svd(O.unfold(b, 0), compute_uv=False)[:3]), rtol=1e-5)
+    again = W.tucker_model_device(11, dims, ranks, device="cpu").double().numpy()
+    assert np.array_equal(a, again)

@@ -163,6 +163,43 @@ def cp_model(seed: int, I: int, R: int = None, delta: float = 1e-4, dtype=np.flo
                    delta=float(delta), seed=seed)
 
 
+def tucker_model_device(seed: int, dims: Sequence[int], ranks: Sequence[int], delta: float = 1e-4,
+                        device="cuda", base_only: bool = False):
+    """Sec. 6.1.2's Tucker model at sizes too large to draw on the host, built on a
+    torch device (FP32 result): Haar factors (QR of Gaussian, sign-fixed), core
+    i.i.d. U[5, 10], A0 = core x_1 U_1 ... x_N U_N, and A = A0 + delta E with E
+    i.i.d. N(0, 1) (absolute noise, as the paper's Sec. 6.1). The expansions run
+    in FP64 except the last (the first mode, the largest), which writes FP32; the
+    noise is added in row blocks. Seeded through torch's generator on the device:
+    the same seed gives the same tensor on one torch version. base_only: A0."""
+    import torch
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    factors = []
+    for d, r in zip(dims, ranks):
+        x = torch.randn((d, r), generator=g, device=device, dtype=torch.float64)
+        q, rr = torch.linalg.qr(x)
+        sg = torch.sign(torch.diagonal(rr))
+        sg[sg == 0] = 1.0
+        factors.append(q * sg)
+    core = torch.rand(tuple(ranks), generator=g, device=device, dtype=torch.float64) * 5.0 + 5.0
+    a = core
+    for n in range(len(dims) - 1, 0, -1):
+        a = torch.movedim(torch.tensordot(factors[n], a, dims=([1], [n])), 0, n)
+    rest = a.reshape(ranks[0], -1).float()
+    out = (factors[0].float() @ rest).reshape(dims)
+    del a, rest
+    if delta > 0 and not base_only:
+        flat = out.view(dims[0], -1)
+        step = max(1, (1 << 28) // flat.shape[1])
+        for i0 in range(0, dims[0], step):
+            blk = flat[i0:i0 + step]
+            blk.add_(torch.randn(blk.shape, generator=g, device=device, dtype=torch.float32), alpha=delta)
+    return out
+
+
 def uniform_tensor(seed: int, dims: Sequence[int], dtype=np.float32) -> np.ndarray:
     """Plain U[-1, 1) tensor (gradient and projection tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -205,6 +242,11 @@ CONFIGS = {
                         1e-6, "f32", SEED_BASE + 4),
 }
 
+
+# Sec. 6.1.2's Tucker-model sizes: I x 100 x 100 x 100, I = 1000 .. 5000 (step 1000),
+# truncation (I / 100, 10, 10, 10), core U[5, 10], delta = 1e-4
+TUCKER_SIZES = (1000, 2000, 3000, 4000, 5000)
+TUCKER_SEED = SEED_BASE + 7
 
 # Sec. 6.1.1's CP-model sizes: I = 20 .. 100 (step 20), shape I x I x 100 I,
 # truncation (0.2 I, 0.2 I, 0.2 I), delta = 1e-4; the largest is 100 x 100 x 10000
