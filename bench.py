@@ -456,9 +456,13 @@ def main():
     }
     # kernels per step: per mode 10 (initial guess chain) + the factor copy, 9 per
     # CUDA-core or BF16 sweep, 12 per split-precision sweep (basis split, W pass,
-    # ||W||^2 sum, Y pass + the 8-kernel tail), plus the BF16 conversion of each mode
-    # that runs bulk sweeps
-    launches = (sum(11 + 9 * n + 3 * t for n, t in zip(st["sweeps"], st["tc_sweeps"])) +
+    # ||W||^2 sum, Y pass + the 8-kernel tail), 4 more per FP32 sweep of a mode whose
+    # sweeps can run split (W product, W statistics, test, Y pass: each launched,
+    # each exiting at once when its sweep is not split), plus the BF16 conversion of
+    # each mode that runs bulk sweeps
+    launches = (sum(11 + 9 * n + 3 * t + (4 * (n - b) if sc else 0)
+                    for n, t, b, sc in zip(st["sweeps"], st["tc_sweeps"], st["bulk_sweeps"],
+                                           st["split_capable"])) +
                 sum(1 for b in st["bulk_sweeps"] if b > 0))
     mixed_st = st if args.precision == "mixed_bf16" else ost
     plain_st = st if args.precision == "native" else ost
@@ -473,6 +477,7 @@ def main():
         "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
                                "1e-2 noise eta 1e-6", "precision": args.precision,
                    "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
+                   "split_sweeps": st["split_sweeps"],
                    "bulk_sweeps": st["bulk_sweeps"], "tc_sweeps": st["tc_sweeps"],
                    "rel_err": st["rel_err"],
                    "mixed_vs_fp32_plain": {
@@ -481,7 +486,8 @@ def main():
                        "mixed_rel_err": mixed_st["rel_err"], "fp32_plain_rel_err": plain_st["rel_err"],
                        "rel_err_gap": abs(mixed_st["rel_err"] - plain_st["rel_err"]),
                        "fp32_plain_sweeps": plain_st["sweeps"],
-                       "fp32_plain_products": "split-precision 3xTF32 on tcgen05 (full-size modes)",
+                       "fp32_plain_products": "exact FP32 on the CUDA cores (fused sweep; a sweep "
+                                               "predicted to be the last forms W alone first)",
                        "fp32_cuda_core_ms": round(cuda_ms, 4), "fp32_cuda_core_rel_err": cst["rel_err"],
                        "fp32_cuda_core_sweeps": cst["sweeps"]},
                    "c3_128quartic": {

@@ -105,6 +105,10 @@ typedef struct {
   int converged[TALS_MAX_NDIM];         /* 1 if Eq. 5.01 fired before max_sweeps */
   int order[TALS_MAX_NDIM];             /* processing order used */
   int status;                           /* worst per-mode status */
+  int split_capable[TALS_MAX_NDIM];     /* 1 if mode n's FP32 sweeps could run split: a sweep
+                                           predicted to be the last forms W alone, takes the
+                                           Eq. 5.01 test, and forms Y only if the loop goes on */
+  int split_sweeps[TALS_MAX_NDIM];      /* sweeps of mode n that ran split */
 } tals_stats;
 
 typedef struct tals_ctx tals_ctx;

@@ -45,7 +45,8 @@ class tals_stats(ctypes.Structure):
                 ("sweeps", ctypes.c_int * MAX_NDIM), ("bulk_sweeps", ctypes.c_int * MAX_NDIM),
                 ("tc_sweeps", ctypes.c_int * MAX_NDIM),
                 ("converged", ctypes.c_int * MAX_NDIM), ("order", ctypes.c_int * MAX_NDIM),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("split_capable", ctypes.c_int * MAX_NDIM),
+                ("split_sweeps", ctypes.c_int * MAX_NDIM)]
 
     def to_dict(self, ndim: int) -> dict:
         return {"rel_err": self.rel_err, "norm_a": self.norm_a,
@@ -54,7 +55,9 @@ class tals_stats(ctypes.Structure):
                 "bulk_sweeps": list(self.bulk_sweeps[:ndim]),
                 "tc_sweeps": list(self.tc_sweeps[:ndim]),
                 "converged": [bool(x) for x in self.converged[:ndim]],
-                "order": list(self.order[:ndim]), "status": self.status}
+                "order": list(self.order[:ndim]), "status": self.status,
+                "split_capable": [bool(x) for x in self.split_capable[:ndim]],
+                "split_sweeps": list(self.split_sweeps[:ndim])}
 
 
 class tals_hooi_stats(ctypes.Structure):

@@ -80,6 +80,11 @@ struct Need {
     }
     if (sweep) ypart = std::max(ypart, (size_t)pc.grid_x * (size_t)v.I * (size_t)R);
     spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
+    if (sweep && dtype == TALS_F32) {
+      // split sweeps: the W statistics' partials after the pass's, W in a scratch buffer
+      spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y + 2 * (size_t)split_stat_blocks(v, sms));
+      tbuf = std::max(tbuf, (size_t)(v.J() * R));
+    }
     if (sweep && dtype == TALS_F32 && t32_supported(v, R)) {
       // split-precision passes: per-CTA Y partials, W written every sweep (into a
       // scratch tensor buffer where the mode has no destination), the split basis
@@ -188,6 +193,7 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
   c->host_d_n = need.spart + 16;
   c->need_ir = need.ir;
   c->ypart_elems = need.ypart;
+  c->tbuf_elems = need.tbuf;
   c->spart_n = need.spart;
   return TALS_OK;
 }
@@ -257,6 +263,23 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
       j.g2 = t32_grid(j.v, 2, c->sms);
     }
   }
+  // FP32 modes on the fused pass whose error comes from ||B||^2 - ||W||^2: a sweep
+  // predicted to be the last forms W alone (register-tiled mode product into the
+  // destination or a scratch buffer), takes the test, and forms Y only if needed
+  j.split_ok = 0;
+  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32) {
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    const int nb = split_stat_blocks(j.v, c->sms);
+    const bool room = j.Wdest != nullptr || (size_t)(j.v.J() * j.R) <= c->tbuf_elems;
+    if (w != j.X && room && (size_t)j.pc.grid_x * j.pc.grid_y + 2 * (size_t)nb <= c->spart_n &&
+        mode_gemm_gated_ok((const float*)j.X, j.v.P, j.v.I, j.v.Q, (const float*)c->Lt, 1, j.R, j.R,
+                           (float*)w)) {
+      j.split_ok = 1;
+      j.Wt = w;
+      j.nbw = nb;
+    }
+  }
   return TALS_OK;
 }
 
@@ -276,7 +299,7 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
 #define TALS_CK(x)                                   \
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
   TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
-                            j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32));
+                            j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32, j.split_ok));
   if (j.twopass) return twopass_init_launch(c, j, set_norm_a);
   if (j.t32) {
     // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
@@ -334,8 +357,20 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
     return mode_sweep_tail(c, j, j.g2, np, 1);
   }
   // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
+  // (the pass exits at once on a split sweep)
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
                       j.Wdest, 0, j.st, j.resid_kernel ? 0 : 1, s, nullptr, j.resid));
+  if (j.split_ok) {
+    // a split sweep (each kernel exits at once otherwise): W alone, its statistics
+    // and the Eq. 5.01 step, then Y = B W only if the mode goes on
+    double* wpart = c->spart + (size_t)j.pc.grid_x * j.pc.grid_y;
+    TALS_CK(launch_mode_gemm_gated((const float*)j.X, j.v.P, I, j.v.Q, (const float*)c->Lt, 1, R, R,
+                                   (float*)j.Wt, j.st, s));
+    TALS_CK(launch_split_stats((const float*)j.Wt, j.v, R, c->GfinL, j.st, wpart, j.nbw, s));
+    TALS_CK(launch_split_test(wpart, j.nbw, j.st, c->norm_a2, j.cond, j.has_cond, s));
+    TALS_CK(launch_pass(c->dtype, j.pc, PASS_GIVEN, j.X, j.v, R, nullptr, c->Ypart, c->spart, nullptr, 0, j.st,
+                        0, s, j.Wt));
+  }
   return mode_sweep_tail(c, j, j.pc.grid_x, j.pc.grid_x * j.pc.grid_y, 1);
 }
 
@@ -615,6 +650,8 @@ static void fill_mode_stats(tals_ctx* c, int n, tals_stats* st) {
   st->sweeps[n] = ms.k;
   st->bulk_sweeps[n] = ms.bulk;
   st->tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
+  st->split_capable[n] = ms.split_ok;
+  st->split_sweeps[n] = ms.nsplit;
   st->converged[n] = ms.converged;
   if (ms.status && !st->status) st->status = ms.status;
 }

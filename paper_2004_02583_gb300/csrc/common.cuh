@@ -35,7 +35,50 @@ struct ModeState {
                       // sw_tc holds ||W||^2 of the stored W
   double sw_prev;     // ||W||^2 of the previous bulk sweep
   double sw_tc;       // tensor-core modes: ||W||^2 of the W last written
+  int split_ok;       // the mode may run a sweep split (W alone, the test, then Y if needed)
+  int split;          // this sweep runs split (set for the next sweep by the TEST kernel)
+  double d_cur;       // |e_{k-1} - e_k| of the last test (negative: no comparison yet)
+  double d_prev;      // the one before
+  int nsplit;         // sweeps that ran split
 };
+
+// The Eq. 5.01 step of an FP32-phase sweep, given e_k (thread 0 of a single-CTA
+// kernel): the test on |e_{k-1} - e_k| from the second sweep of the phase on, the
+// sweep budget, and the state's counters. Returns 1 when the mode is done.
+__device__ inline int als_stop_step(ModeState* st, double e, double norm_a) {
+  int s = 0;
+  st->d_cur = -1.0;
+  if (st->kf >= 1) {
+    const double d = fabs(st->e_prev - e);
+    st->d_cur = d;
+    if (d <= st->eta * norm_a) {
+      s = 1;
+      st->converged = 1;
+    }
+  }
+  st->kf += 1;
+  if (st->k + 1 >= st->max_sweeps) s = 1;
+  st->e_prev = e;
+  st->e_cur = e;
+  st->k += 1;
+  if (s) st->done = 1;
+  return s;
+}
+
+// Whether the next sweep runs split (thread 0, after a test that did not stop):
+// the mixed path's second FP32 sweep (the first one the test can stop), a sweep
+// whose predicted change rho |e_{k-1} - e_k| (rho = the last two changes' ratio)
+// is within the tolerance, or the budget's last sweep.
+__device__ inline void als_predict_split(ModeState* st, double norm_a) {
+  int nxt = 0;
+  if (st->split_ok) {
+    if (st->bulk > 0 && st->kf == 1) nxt = 1;
+    if (st->d_cur >= 0.0 && st->d_prev > 0.0 && st->d_cur * st->d_cur <= st->eta * norm_a * st->d_prev) nxt = 1;
+    if (st->k + 1 >= st->max_sweeps) nxt = 1;
+  }
+  st->d_prev = st->d_cur;
+  st->split = nxt;
+}
 
 // splitmix64 output number c of the stream seeded with `state`:
 // mix(state + (c + 1) * 0x9E3779B97F4A7C15) (Steele, Lea, Flood 2014; Vigna).

@@ -226,6 +226,8 @@ tals_status collect(tals_ctx* c, int kind, const GraphEntry* en, tals_stats* sta
     local.sweeps[n] = ms.k;
     local.bulk_sweeps[n] = ms.bulk;
     local.tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
+    local.split_capable[n] = ms.split_ok;
+    local.split_sweeps[n] = ms.nsplit;
     local.converged[n] = ms.converged;
     if (ms.status && !local.status) local.status = ms.status;
   }

@@ -395,7 +395,7 @@ tals_status hooi_run(tals_ctx* c, void* const* U, void* G_out, double tol, int m
       if (yp > c->ypart_elems || ir > c->need_ir)
         return fail(TALS_ENOTSUP, "HOOI: mode %d exceeds the context's workspace", n);
       if ((e = launch_state_init(j.st, inner_eta, inner_sweeps, j.resid || j.resid_kernel || j.t32, s, 0,
-                                 j.t32)) != cudaSuccess)
+                                 j.t32, j.split_ok)) != cudaSuccess)
         return cuda_fail(e, "HOOI state");
       if ((e = launch_copy(c->Ypart, U[n], ir * esz, s)) != cudaSuccess) return cuda_fail(e, "HOOI warm start");
       if ((rs = mode_init_tail(c, j, false, 1, c->spart, nsp)) != TALS_OK) return rs;

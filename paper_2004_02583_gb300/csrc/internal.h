@@ -29,6 +29,8 @@ struct ModeJob {
   int g1 = 0, g2 = 0;            // their grids (W pass CTAs; Y pass column shares per chunk)
   int twopass = 0;               // I_n beyond the fused pass: two tiled products per sweep
   int splits = 1;                // column splits of the two-pass form's Y product
+  int split_ok = 0;              // sweeps predicted to be the last run split (split.cu), W in Wt
+  int nbw = 0;                   // CTAs of their W statistics
 };
 
 struct DriveState {
@@ -146,6 +148,7 @@ struct tals_ctx {
   size_t host_d_n = 0;
   size_t need_ir = 0;
   size_t ypart_elems = 0;     // capacity of Ypart (elements)
+  size_t tbuf_elems = 0;      // capacity of each tbuf (elements)
   size_t spart_n = 0;         // capacity of spart
   // als_mode_sweep / als_mode_finish drive state
   tals::DriveState drive[TALS_MAX_NDIM];

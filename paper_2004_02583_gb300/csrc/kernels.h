@@ -98,7 +98,7 @@ cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s
 // sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
 // tc: the mode's products run on the split-precision tensor-core passes.
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max = 0, int tc = 0);
+                              int bulk_max = 0, int tc = 0, int split_ok = 0);
 
 // Tensor-core (tcgen05, BF16) sweep pass; see tc_pass.cu.
 bool tc_supported(const ModeView& v, int R);
@@ -136,6 +136,21 @@ cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long lo
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
                                  const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s);
+// The register-tiled mode product of launch_mode_gemm, its CTAs exiting at once
+// unless gate's sweep is split and not done (cudaErrorNotSupported where the
+// register-tiled plan does not take the view; mode_gemm_gated_ok tells beforehand).
+bool mode_gemm_gated_ok(const float* X, long long P, long long Bin, long long Q, const float* M, long long sa,
+                        long long sb, long long Aout, float* out);
+cudaError_t launch_mode_gemm_gated(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                   long long sa, long long sb, long long Aout, float* out, const ModeState* gate,
+                                   cudaStream_t s);
+// split.cu: the split sweep's statistics of W (||W||^2 and the rounded-basis term,
+// two FP64 partials per CTA; nb = split_stat_blocks CTAs) and its Eq. 5.01 step.
+int split_stat_blocks(const ModeView& v, int sms);
+cudaError_t launch_split_stats(const float* W, const ModeView& v, int R, const double* GL, const ModeState* st,
+                               double* part, int nb, cudaStream_t s);
+cudaError_t launch_split_test(const double* part, int nb, ModeState* st, const double* norm_a2,
+                              unsigned long long cond, int has_cond, cudaStream_t s);
 // Partial sums launch_mode_resid_gemm writes for this view (0: not covered).
 long long mode_resid_gemm_parts(const float* X, long long P, long long Bin, long long Q, const float* M,
                                 long long sa, long long sb, long long Aout, const float* B);

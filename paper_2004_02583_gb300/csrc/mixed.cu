@@ -75,7 +75,7 @@ tals_status mixed_init_launch(tals_ctx* c, ModeJob& j, bool set_norm_a, int grid
                                  s, c->mixed->sq);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
   e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid || j.t32, s, c->opts.bulk_sweeps,
-                        j.t32);
+                        j.t32, j.split_ok);
   if (e == cudaSuccess)
     e = launch_tc_pass(c->mixed->shadow, j.v, j.R, nullptr, (float*)c->Ypart, c->spart,
                        c->mixed->err, grid, s, 1, sketch_state(c->opts.seed, j.n));

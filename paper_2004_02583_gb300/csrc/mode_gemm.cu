@@ -249,6 +249,7 @@ struct MgArgs {
   long long nt;         // tiles per a-tile: cols ceil(P Q / TN), rows ceil(P / TN)
   int nk;               // K chunks
   int vec;              // 16-byte output stores
+  const ModeState* gate;   // when set: run only while the mode's sweep is split and not done
 };
 
 // Tile geometry: TA a (outputs' rank side) x TN (cols: q, rows: p) = 8192
@@ -272,6 +273,7 @@ constexpr size_t mg_smem_floats() {
 // resident M slice, RESID accumulates sum (B - M X)^2 instead of storing.
 template <bool ROWS, bool MRES, bool RESID, int TA>
 __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
+  if (a.gate != nullptr && (!a.gate->split || a.gate->done)) return;   // uniform, before any barrier
   using S = MgShape<ROWS, TA>;
   constexpr int TN = S::TN, XS = S::XS, ST = S::STAGES;
   constexpr int MS = MRES ? 0 : kMgBK * TA;
@@ -601,6 +603,20 @@ cudaError_t launch_mode_resid_gemm(const float* X, long long P, long long Bin, l
   mode_resid_cols<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)P), kGThreads, 0, s>>>(X, Bin, Q, M, sa, sb,
                                                                                    Aout, B, part);
   return cudaGetLastError();
+}
+
+bool mode_gemm_gated_ok(const float* X, long long P, long long Bin, long long Q, const float* M, long long sa,
+                        long long sb, long long Aout, float* out) {
+  return mg_plan<false>(X, P, Bin, Q, M, sa, sb, Aout, out).ok;
+}
+
+cudaError_t launch_mode_gemm_gated(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                   long long sa, long long sb, long long Aout, float* out, const ModeState* gate,
+                                   cudaStream_t s) {
+  MgPlan pl = mg_plan<false>(X, P, Bin, Q, M, sa, sb, Aout, out);
+  if (!pl.ok) return cudaErrorNotSupported;
+  pl.a.gate = gate;
+  return mg_launch<false>(pl, s);
 }
 
 cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long long Q, const float* M,

@@ -7,7 +7,13 @@ namespace tals {
 
 template <typename T, int RC, int RPT, int RW, int NT, int JT, bool TR>
 __global__ void __launch_bounds__(NT, 1) pass_kernel(PassArgs<T> a) {
-  if (a.st != nullptr && a.st->done) return;   // uniform early exit, before any barrier
+  if (a.st != nullptr) {   // uniform early exits, before any barrier
+    if (a.st->done) return;
+    // split sweeps (split.cu): the fused pass yields to W alone, and the Y-only
+    // pass runs only for a split sweep whose test did not stop the mode
+    if (a.mode == PASS_SWEEP && a.st->split) return;
+    if (a.mode == PASS_GIVEN && !a.st->split) return;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* yp = a.Ypart != nullptr ? a.Ypart + (size_t)blockIdx.x * a.I * a.R : nullptr;
   const double tot =

@@ -185,8 +185,11 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
     __shared__ int stop, phase_end;
     __shared__ double red[32];
     if (tid == 0) phase_end = 0;
+    // a split sweep took its test on W alone (split_test_kernel) before Y existed;
+    // here only the prediction for the next sweep and the L-update's factor remain
+    const bool pre = op == 1 && st->split;
     double c = 0.0;
-    if (GL != nullptr) {
+    if (GL != nullptr && !pre) {
       // a thread's first four entries: their loads issued together, then summed in
       // the order of the plain loop
       double g[4], x[4];
@@ -207,7 +210,10 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
       }
     }
     const double corr = block_sum(c, red);
-    if (tid == 0) {
+    if (tid == 0 && pre) {
+      stop = st->done;
+      if (!stop) als_predict_split(st, sqrt(*norm_a2));
+    } else if (tid == 0) {
       const bool rs = st->resid && op == 1;
       st->corr = rs ? 0.0 : corr;
       const double e2 = rs ? st->sW : st->normM2 - st->sW + corr;
@@ -229,17 +235,16 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(const double* __re
         }
         st->bulk += 1;
       } else {
-        if (st->kf >= 1 && fabs(st->e_prev - e) <= st->eta * norm_a) {
-          s = 1;
-          st->converged = 1;
-        }
-        st->kf += 1;
+        s = als_stop_step(st, e, norm_a);
+        if (!s) als_predict_split(st, norm_a);
       }
-      if (k + 1 >= st->max_sweeps) s = 1;
-      st->e_prev = e;
-      st->e_cur = e;
-      st->k = k + 1;
-      if (s) st->done = 1;
+      if (op == 2) {
+        if (k + 1 >= st->max_sweeps) s = 1;
+        st->e_prev = e;
+        st->e_cur = e;
+        st->k = k + 1;
+        if (s) st->done = 1;
+      }
       stop = s;
     }
     __syncthreads();
@@ -746,9 +751,12 @@ cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
 }
 
 __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int resid,
-                                  int bulk_max, int tc) {
+                                  int bulk_max, int tc, int split_ok) {
   ModeState z = {};
   z.tc_resid = tc;
+  z.split_ok = split_ok;
+  z.d_cur = -1.0;
+  z.d_prev = -1.0;
   z.eta = eta;
   z.max_sweeps = max_sweeps;
   z.resid = resid;
@@ -758,8 +766,8 @@ __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int
 }
 
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max, int tc) {
-  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max, tc);
+                              int bulk_max, int tc, int split_ok) {
+  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max, tc, split_ok);
   return cudaGetLastError();
 }
 
