@@ -302,8 +302,10 @@ tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mo
  * It allocates nothing: its scratch (the per-CTA partial sums) is one fixed array
  * of 4 MiB + 8 KiB in device global memory, defined in the library and held by
  * every GPU that loads the library until the process exits. The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make the
- * first call on each device before any stream capture. Limit: I_mode x R <= 2^20
+ * device looks up that array's device address (cudaGetSymbolAddress) and keeps it
+ * for the life of the process, so make the first call on each device before any
+ * stream capture; a cudaDeviceReset of that device invalidates the kept address
+ * (do not call this entry point on a device after resetting it). Limit: I_mode x R <= 2^20
  * (larger shapes return TALS_EINVAL); the pass uses fewer CTAs when their partials
  * would not fit. All calls share the one array: calls whose work overlaps on the
  * GPU (two streams, or two host threads) race and must be serialised by the

@@ -86,8 +86,9 @@ extern "C" tals_status tals_sweep_pass_noalloc(const void* A, int ndim, const in
   tals_status st = scratch_on_current_device(&scratch);
   if (st != TALS_OK) return st;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t qe = cudaGetDevice(&dev);
+  if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (qe != cudaSuccess) return cuda_fail(qe, "device query");
   PassConfig pc = pass_config(TALS_F32, v, R, sms);
   if (!pc.ok) return fail(TALS_ENOTSUP, "shape outside the pass kernel limits");
   // fewer CTAs when their partials would not fit the fixed scratch

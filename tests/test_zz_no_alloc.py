@@ -54,6 +54,26 @@ def test_noalloc_matches_allocating_pass_twice(tals, dims, mode, R):
         assert abs(float(w2.item()) - w2_ref) <= 1e-5 * w2_ref
 
 
+def test_noalloc_with_its_grid_cut_to_the_scratch(tals):
+    """I x R = 512 x 64: the fixed scratch holds the Y partials of 32 CTAs only, fewer
+    than the pass plans for this view, so every CTA covers more tiles."""
+    dims, mode, R = (512, 64, 64), 0, 64
+    plan = tals.pass_plan("f32", 1, 512, 64 * 64, R, torch.cuda.get_device_properties(0).multi_processor_count)
+    assert plan is not None and plan["grid_x"] > (1 << 20) // (512 * R)
+    rng = np.random.default_rng(12)
+    A = torch.from_numpy(rng.standard_normal(dims).astype(np.float32)).cuda()
+    Q = torch.from_numpy(np.linalg.qr(rng.standard_normal((dims[mode], R)))[0]
+                         .astype(np.float32)).cuda()
+    Y_ref, w2_ref = tals.sweep_pass(A, mode, Q, engine="cuda")
+    Y = torch.full((dims[mode], R), float("nan"), dtype=torch.float64, device="cuda")
+    w2 = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    assert _noalloc(tals, A, mode, Q, Y, w2) == tals.TALS_OK
+    torch.cuda.synchronize()
+    assert torch.isfinite(Y).all()
+    assert torch.allclose(Y, Y_ref, rtol=1e-5, atol=1e-5 * float(Y_ref.abs().max()))
+    assert abs(float(w2.item()) - w2_ref) <= 1e-5 * w2_ref
+
+
 def test_noalloc_rejects_oversize(tals):
     A = torch.zeros((4096, 8, 8), device="cuda")
     Q = torch.zeros((4096, 300), device="cuda")
