@@ -36,7 +36,8 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # where no capture of the current kernel exists.
 PASS_TRAFFIC = 2 * (268599552 + 14900480)   # CUDA-core FP32 fused pass
 TC_TRAFFIC = 2 * (134338048 + 3646208)      # BF16 tensor-core fused pass
-T32_TRAFFIC = {"w": None, "y": None}        # split-precision W and Y passes
+T32_TRAFFIC = {"w": 2 * (268653568 + 12280320),   # split-precision W and Y passes
+               "y": 2 * (285491968 + 3066368)}
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
@@ -210,6 +211,10 @@ def main():
                     help="skip the other precision path (per-path launch lists under ncu)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
+    ap.add_argument("--profile-what", default="pass", choices=["pass", "tf32", "decomp"],
+                    help="with --profile-pass: pass (the fused sweep pass), tf32 (the split-precision "
+                         "W and Y passes, one timed launch each after one warm-up), decomp (one "
+                         "decomposition: its split sweep's W product and W statistics)")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="c4: number of tensors (4096 is the workload; fewer for profiling)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "tucker"],
@@ -247,7 +252,16 @@ def main():
     ctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=args.precision,
                        use_graph=not args.no_graph)
     if args.profile_pass:
-        ms_, by_, fl_ = ctx.time_pass(mode=0, iters=1)
+        if args.profile_what == "tf32":
+            ms_, by_, fl_ = ctx.time_sweep(mode=0, engine="tf32", iters=1)
+        elif args.profile_what == "decomp":
+            G = torch.empty(RANKS, device="cuda")
+            Us = [torch.empty((d, r), device="cuda") for d, r in zip(DIMS, RANKS)]
+            _, _, st_ = ctx.st_hosvd(G, Us)
+            ms_, by_, fl_ = None, None, None
+            print(json.dumps({"sweeps": st_["sweeps"], "split_sweeps": st_["split_sweeps"]}))
+        else:
+            ms_, by_, fl_ = ctx.time_pass(mode=0, iters=1)
         print(json.dumps({"profile_pass_ms": ms_, "bytes": by_, "flops": fl_}))
         ctx.close()
         return
