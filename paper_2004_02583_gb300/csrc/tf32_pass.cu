@@ -171,12 +171,16 @@ __device__ __forceinline__ double split_sum(float sh, float sl, double* red4, in
 // ---------------------------------------------------------------------------
 // Pass 1: W = B^T Q (3xTF32), ||W||^2
 //
-// Three rings decouple the stages: raw slots receive the tensor by TMA and are
-// released as soon as the split threads hold their column in registers, so a
-// raw slot recycles after one TMA round trip and many bytes stay in flight;
-// operand slots hold the stage split and transposed K-major ([128 tile columns][32 rows i], hi and lo planes)
-// until its MMAs are done; beside each operand slot, the stage's rows of the split
-// basis (released with it).
+// Three rings decouple the stages. Raw slots receive the tensor by TMA and are
+// released as soon as the split threads hold their column in registers, so a raw
+// slot recycles after one TMA round trip and many bytes stay in flight. The A
+// operand stages live in tensor memory: each split thread stores the hi and lo
+// planes of its column (row m of A) into its own lane, and the MMAs read A from
+// there -- no shared-memory operand traffic, and an MMA with A in tensor memory
+// issues in ~46 cycles against ~75 from shared memory (measured). Beside each A
+// stage, a shared-memory slot holds the stage's rows of the split basis (the B
+// operand), released with it. Ring positions are kept as counters: a 64-bit
+// division per stage cost more than the stage's MMAs.
 // ---------------------------------------------------------------------------
 // The raw stage is row-major without swizzle: one box [32 rows][128 columns]
 // (wide), or four boxes [32 rows][32 columns] (narrow views, Q % 128 != 0). Thread
@@ -189,17 +193,14 @@ __device__ __forceinline__ void t32_read_col(const unsigned char* raw, int t, bo
   for (int k = 0; k < 32; ++k) v[k] = base[k * pitch];
 }
 
-// Column m of the stage as a K-major row of the hi and lo operands (16-byte chunks:
-// four wavefronts per warp store, the minimum for 512 bytes).
-__device__ __forceinline__ void t32_write_col(unsigned char* hi, unsigned char* lo, int m,
-                                              const float (&v)[32]) {
+// Column m of the stage split into hi and lo (32 values each, as raw 32-bit words
+// for the tensor-memory stores).
+__device__ __forceinline__ void t32_split_col(const float (&v)[32], uint32_t (&hi)[32], uint32_t (&lo)[32]) {
 #pragma unroll
-  for (int kq = 0; kq < 8; ++kq) {
-    float4 x = make_float4(v[4 * kq], v[4 * kq + 1], v[4 * kq + 2], v[4 * kq + 3]);
-    const float4 l4 = split4(x);
-    const uint32_t off = (uint32_t)m * 128u + ((uint32_t)(kq ^ (m & 7)) << 4);
-    *reinterpret_cast<float4*>(hi + off) = x;
-    *reinterpret_cast<float4*>(lo + off) = l4;
+  for (int k = 0; k < 32; ++k) {
+    const float h = to_tf32(v[k]);
+    hi[k] = __float_as_uint(h);
+    lo[k] = __float_as_uint(to_tf32(v[k] - h));
   }
 }
 
@@ -211,13 +212,12 @@ __global__ void __launch_bounds__(kT32Threads, 1)
   unsigned char* base = align1024(smem_raw);
   constexpr uint32_t kQB = 2 * RP * 128;            // split basis of one stage
   unsigned char* raw = base;                                      // nr x 16 KiB
-  unsigned char* opr = raw + (size_t)nr * kStage1;                // no x (hi | lo) 32 KiB
-  unsigned char* qsr = opr + (size_t)no * 2 * kStage1;            // nq x kQB
+  unsigned char* qsr = raw + (size_t)nr * kStage1;                // no x kQB
   uint64_t* bars = reinterpret_cast<uint64_t*>(qsr + (size_t)nq * kQB);
   uint64_t* rfull = bars;                     // raw stage landed (tx)
   uint64_t* rempty = rfull + kMaxStages;      // raw stage read by the split threads (128)
-  uint64_t* ofull = rempty + kMaxStages;      // operands written (128)
-  uint64_t* oempty = ofull + kMaxStages;      // MMAs done with the operands (commit)
+  uint64_t* ofull = rempty + kMaxStages;      // A operands stored in tensor memory (128)
+  uint64_t* oempty = ofull + kMaxStages;      // MMAs done with the A stage and its basis slot (commit)
   uint64_t* qfull = oempty + kMaxStages;      // basis chunk landed (tx)
   uint64_t* dfull = qfull + kMaxStages;       // [kNB] group products ready (commit)
   uint64_t* dfree = dfull + kMaxDB;           // [kNB] group products read out (128 arrivals)
@@ -248,11 +248,14 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // Tensor memory: kNB buffers of kDS columns, one per accumulation group of
-  // a.flush K-steps in flight, each [B_hi Q_hi | B_hi Q_lo + B_lo Q_hi] started fresh.
+  // Tensor memory (all 512 columns): the A operand stages first, 64 columns each
+  // (hi plane | lo plane: lane m = tile column m, column = row i of the stage), then
+  // nb buffers of kDS columns, one per accumulation group of a.flush K-steps in
+  // flight, each [B_hi Q_hi | B_hi Q_lo + B_lo Q_hi] started fresh.
   constexpr int kDS = (2 * RP + 31) / 32 * 32;
-  constexpr int kNB = 512 / kDS < kMaxDB ? 512 / kDS : kMaxDB;
-  constexpr uint32_t kCols = kNB * kDS <= 64 ? 64 : kNB * kDS <= 128 ? 128 : kNB * kDS <= 256 ? 256 : 512;
+  constexpr uint32_t kCols = 512;
+  const uint32_t acols = (uint32_t)no * 64u;
+  const int nb = (int)((kCols - acols) / kDS) < kMaxDB ? (int)((kCols - acols) / kDS) : kMaxDB;
   if (warp == 0) tmem_alloc(su32(tmem_holder), kCols);
   fence_before();
   __syncthreads();
@@ -264,6 +267,11 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     // ---------------- producer: raw stages and basis chunks ----------------
     long long s = 0;
     bool ok = true;
+    // ring positions kept as counters (a 64-bit division per stage costs more than
+    // the stage's MMAs)
+    int rr = 0;
+    uint32_t rph = 0;
+    const int kcs = (int)(blockIdx.x % (unsigned)a.nkc);
     const bool wide = a.Q % 128 == 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const long long t = blockIdx.x + lt * gridDim.x;
@@ -284,10 +292,15 @@ __global__ void __launch_bounds__(kT32Threads, 1)
       for (int kc0 = 0; kc0 < a.nkc && ok; ++kc0, ++s) {
         // every CTA starts its tiles at a different 32-row stage, so the CTAs do not
         // all fetch the same chunk of the split basis from L2 at the same time
-        const int kc = (int)((kc0 + blockIdx.x) % a.nkc);
-        const int r = (int)(s % nr);
-        ok = TWAIT(0, mbar_wait_b(su32(&rempty[r]), (uint32_t)(((s / nr) & 1) ^ 1), vfail));
+        int kc = kc0 + kcs;
+        if (kc >= a.nkc) kc -= a.nkc;
+        const int r = rr;
+        ok = TWAIT(0, mbar_wait_b(su32(&rempty[r]), rph ^ 1u, vfail));
         if (!ok) break;
+        if (++rr == nr) {
+          rr = 0;
+          rph ^= 1u;
+        }
         if (lane == 0) {
           unsigned char* st = raw + (size_t)r * kStage1;
           mbar_expect_tx(su32(&rfull[r]), (uint32_t)kStage1);
@@ -315,26 +328,44 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     const bool wide = a.Q % 128 == 0;
     bool ok = true;
     long long nq_issued = 0;
+    int r = 0, o = 0, kc0 = 0;
+    uint32_t rph = 0, oph = 0;
+    const int kcs = (int)(blockIdx.x % (unsigned)a.nkc);
     for (long long s = 0; s < nst && ok; ++s) {
-      const int r = (int)(s % nr), o = (int)(s % no);
-      ok = TWAIT(1, mbar_wait_b(su32(&rfull[r]), (uint32_t)((s / nr) & 1), vfail));
+      ok = TWAIT(1, mbar_wait_b(su32(&rfull[r]), rph, vfail));
       if (!ok) break;
       float v[32];
       t32_read_col(raw + (size_t)r * kStage1, t, wide, v);
       mbar_arrive(su32(&rempty[r]));
-      ok = TWAIT(2, mbar_wait_b(su32(&oempty[o]), (uint32_t)(((s / no) & 1) ^ 1), vfail));
+      ok = TWAIT(2, mbar_wait_b(su32(&oempty[o]), oph ^ 1u, vfail));
       if (!ok) break;
+      fence_after();
       if (t == 0) {
-        // the stage's rows of the split basis into the operand slot's basis slot
-        const int kc = (int)(((s % a.nkc) + blockIdx.x) % a.nkc);
+        // the stage's rows of the split basis into the A stage's basis slot
+        int kc = kc0 + kcs;
+        if (kc >= a.nkc) kc -= a.nkc;
         mbar_expect_tx(su32(&qfull[o]), kQB);
         bulk_load(su32(qsr + (size_t)o * kQB), a.QS + (size_t)kc * (kQB / 4), kQB, su32(&qfull[o]));
       }
-      unsigned char* op = opr + (size_t)o * 2 * kStage1;
-      t32_write_col(op, op + kStage1, t, v);
-      fence_async_smem();
+      // hi and lo of column t into lane t of A stage o
+      uint32_t hi[32], lo[32];
+      t32_split_col(v, hi, lo);
+      const uint32_t ta = tmem + (uint32_t)o * 64u + ((uint32_t)((warp & 3) * 32) << 16);
+      tmem_st32(ta, hi);
+      tmem_st32(ta + 32u, lo);
+      tmem_wait_st();
+      fence_before();
       mbar_arrive(su32(&ofull[o]));
       ++nq_issued;
+      if (++r == nr) {
+        r = 0;
+        rph ^= 1u;
+      }
+      if (++o == no) {
+        o = 0;
+        oph ^= 1u;
+      }
+      if (++kc0 == a.nkc) kc0 = 0;
     }
     // every basis copy issued must have landed before the shared memory is released
     if (t == 0)
@@ -348,43 +379,50 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     const int F = a.flush;
     long long gseq = 0;   // accumulation groups
     bool ok = true;
+    int o = 0, b = 0, bround = 0;
+    uint32_t oph = 0;
     for (long long s = 0; s < nst && ok; ++s) {
-      const int o = (int)(s % no), q = o;
-      ok = TWAIT(3, mbar_wait_b(su32(&ofull[o]), (uint32_t)((s / no) & 1), vfail));
-      if (ok) ok = TWAIT(3, mbar_wait_b(su32(&qfull[q]), (uint32_t)((s / no) & 1), vfail));
+      const int q = o;
+      ok = TWAIT(3, mbar_wait_b(su32(&ofull[o]), oph, vfail));
+      if (ok) ok = TWAIT(3, mbar_wait_b(su32(&qfull[q]), oph, vfail));
       if (!ok) break;
       fence_after();
-      const uint32_t op = su32(opr + (size_t)o * 2 * kStage1);
+      const uint32_t aop = tmem + (uint32_t)o * 64u;   // A stage: hi at +0, lo at +32
       const uint32_t qs = su32(qsr + (size_t)q * kQB);
       // groups of F K-steps, each into a fresh buffer (the epilogue adds the groups
       // up in registers with rounding to nearest); lane 0 issues a group's MMAs back
       // to back (a fence or commit between MMAs costs issue cycles)
       for (int g = 0; g < (kKC / 8) / F && ok; ++g, ++gseq) {
-        const int b = (int)(gseq % kNB);
-        if (gseq >= kNB) {
-          ok = TWAIT(4, mbar_wait_b(su32(&dfree[b]), (uint32_t)((gseq / kNB - 1) & 1), vfail));
+        if (bround >= 1) {
+          ok = TWAIT(4, mbar_wait_b(su32(&dfree[b]), (uint32_t)((bround - 1) & 1), vfail));
           if (!ok) break;
           fence_after();
         }
         if (lane == 0) {
-          const uint32_t d = tmem + (uint32_t)(b * kDS);
+          const uint32_t d = tmem + acols + (uint32_t)(b * kDS);
           for (int k = 0; k < F; ++k) {
             const int ks = g * F + k;
-            // A: K-major (rows = the 128 tile columns, 128 B = 32 rows i), 8 i per step
-            const uint64_t ahi = desc_sw128(op + ks * 32, 16, 1024);
-            const uint64_t alo = desc_sw128(op + kStage1 + ks * 32, 16, 1024);
-            // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]
+            // B: K-major split basis, rows [Q_hi (RP) | Q_lo (RP)]; A from tensor
+            // memory, 8 rows i (columns) per step
             const uint64_t bq = desc_sw128(qs + ks * 32, 16, 1024);
-            mma_tf32(d, ahi, bq, kIdAll, k ? 1u : 0u);   // [B_hi Q_hi | B_hi Q_lo]
-            mma_tf32(d + RP, alo, bq, kIdHi, 1u);        // + B_lo Q_hi into the correction
+            mma_tf32_ts(d, aop + (uint32_t)(ks * 8), bq, kIdAll, k ? 1u : 0u);   // [B_hi Q_hi | B_hi Q_lo]
+            mma_tf32_ts(d + RP, aop + 32u + (uint32_t)(ks * 8), bq, kIdHi, 1u);  // + B_lo Q_hi
           }
           mma_commit(su32(&dfull[b]));
         }
         __syncwarp();
+        if (++b == nb) {
+          b = 0;
+          ++bround;
+        }
       }
       // operand slot and basis slot released together
       if (lane == 0) mma_commit(su32(&oempty[o]));
       __syncwarp();
+      if (++o == no) {
+        o = 0;
+        oph ^= 1u;
+      }
     }
     if (lane == 0) mma_commit(su32(alldone));
     __syncwarp();
@@ -393,22 +431,22 @@ __global__ void __launch_bounds__(kT32Threads, 1)
     bool ok = true;
     const int m = warp * 32 + lane;
     const int ngr = (kKC / 8) / a.flush;   // groups per stage
-    long long gseq = 0;
+    int b = 0;
+    uint32_t bph = 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       const long long t = blockIdx.x + lt * gridDim.x;
       float big[RP], small[RP];   // sum of B_hi Q_hi; of the two correction terms
 #pragma unroll
       for (int k = 0; k < RP; ++k) big[k] = small[k] = 0.f;
       for (int kc = 0; kc < a.nkc && ok; ++kc) {
-        for (int g = 0; g < ngr && ok; ++g, ++gseq) {
-          const int b = (int)(gseq % kNB);
-          ok = TWAIT(5, mbar_wait_b(su32(&dfull[b]), (uint32_t)((gseq / kNB) & 1), vfail));
+        for (int g = 0; g < ngr && ok; ++g) {
+          ok = TWAIT(5, mbar_wait_b(su32(&dfull[b]), bph, vfail));
           if (!ok) break;
           fence_after();
 #pragma unroll
           for (int cb = 0; cb < kDS; cb += 64) {
             uint32_t r0[32], r1[32];
-            const uint32_t ta = tmem + (uint32_t)(b * kDS + cb) + ((uint32_t)(warp * 32) << 16);
+            const uint32_t ta = tmem + acols + (uint32_t)(b * kDS + cb) + ((uint32_t)(warp * 32) << 16);
             tmem_ld32_nw(ta, r0);
             if (cb + 32 < kDS) tmem_ld32_nw(ta + 32u, r1);
             tmem_wait_ld();
@@ -423,6 +461,10 @@ __global__ void __launch_bounds__(kT32Threads, 1)
           }
           fence_before();
           mbar_arrive(su32(&dfree[b]));
+          if (++b == nb) {
+            b = 0;
+            bph ^= 1u;
+          }
         }
       }
       if (!ok) break;
@@ -488,8 +530,8 @@ __device__ __forceinline__ bool t32_prep_w(const T32Args& a, unsigned char* ring
                                            long long lt, long long col, long long ncol, uint64_t* full,
                                            uint64_t* wrdy, int t, volatile int* vfail, bool resid) {
   constexpr uint32_t kW2 = 2u * RP * 128u;
-  const int slot = (int)(lt % ns);
-  const uint32_t ph = (uint32_t)((lt / ns) & 1);
+  const int slot = (int)((uint32_t)lt % (uint32_t)ns);   // 32-bit: stages per CTA < 2^32
+  const uint32_t ph = ((uint32_t)lt / (uint32_t)ns) & 1u;
   if (!mbar_wait_b(su32(&full[slot]), ph, vfail)) return false;
   const long long j0 = (col + lt * ncol) * 32;
   unsigned char* w2 = ring + (size_t)slot * kSB + 2 * kStage2;
@@ -599,8 +641,8 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
       const long long j = (col + lt * ncol) * 32;
       const long long p = j / a.Q, q = j - p * a.Q;
-      const int slot = (int)(seq % ns);
-      const uint32_t ph = (uint32_t)((seq / ns) & 1);
+      const int slot = (int)((uint32_t)seq % (uint32_t)ns);
+      const uint32_t ph = ((uint32_t)seq / (uint32_t)ns) & 1u;
       ok = TWAIT(0, mbar_wait_b(su32(&empty[slot]), ph ^ 1u, vfail));
       if (!ok) break;
       if (lane == 0) {
@@ -641,8 +683,8 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     long long gseq = 0;
     for (long long lt = 0; lt < nt && ok; ++lt) {
       for (int g = 0; g < ngr && ok; ++g, ++gseq) {
-        const int b = (int)(gseq % kYB);
-        ok = TWAIT(2, mbar_wait_b(su32(&yfull[b]), (uint32_t)((gseq / kYB) & 1), vfail));
+        const int b = (int)((uint32_t)gseq % (uint32_t)kYB);
+        ok = TWAIT(2, mbar_wait_b(su32(&yfull[b]), ((uint32_t)gseq / (uint32_t)kYB) & 1u, vfail));
         if (!ok) break;
         fence_after();
 #pragma unroll
@@ -688,8 +730,8 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     bool ok = true;
     float sh = 0.f, sl = 0.f;   // residual sum (init: ||B||^2)
     for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
-      const int slot = (int)(seq % ns);
-      const uint32_t ph = (uint32_t)((seq / ns) & 1);
+      const int slot = (int)((uint32_t)seq % (uint32_t)ns);
+      const uint32_t ph = ((uint32_t)seq / (uint32_t)ns) & 1u;
       ok = TWAIT(3, mbar_wait_b(su32(&full[slot]), ph, vfail));
       if (!ok) break;
       float pv[32];
@@ -745,8 +787,8 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     const int F = a.flush;
     // stage lt's P product (after its W block is prepared)
     auto issue_p = [&](long long lt) -> bool {
-      const int slot = (int)(lt % ns);
-      if (!TWAIT(5, mbar_wait_b(su32(&wrdy[slot]), (uint32_t)((lt / ns) & 1), vfail))) return false;
+      const int slot = (int)((uint32_t)lt % (uint32_t)ns);
+      if (!TWAIT(5, mbar_wait_b(su32(&wrdy[slot]), ((uint32_t)lt / (uint32_t)ns) & 1u, vfail))) return false;
       fence_after();
       if (!resid) return true;
       // P = Q_c W^T: [Q_hi W_hi^T | Q_hi W_lo^T] (N = 64) and Q_lo W_hi^T into the first half
@@ -775,15 +817,15 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     long long gseq = 0;
     // stage lt's Y product (after its residual and split), in groups of F K-steps
     auto issue_y = [&](long long lt) -> bool {
-      const int slot = (int)(lt % ns);
-      if (!TWAIT(7, mbar_wait_b(su32(&splt[slot]), (uint32_t)((lt / ns) & 1), vfail))) return false;
+      const int slot = (int)((uint32_t)lt % (uint32_t)ns);
+      if (!TWAIT(7, mbar_wait_b(su32(&splt[slot]), ((uint32_t)lt / (uint32_t)ns) & 1u, vfail))) return false;
       fence_after();
       const uint32_t st = su32(ring + (size_t)slot * kSB);
       const uint32_t w2 = st + 2 * kStage2;
       for (int g = 0; g < 4 / F; ++g, ++gseq) {
-        const int b = (int)(gseq % kYB);
+        const int b = (int)((uint32_t)gseq % (uint32_t)kYB);
         if (gseq >= kYB) {
-          if (!TWAIT(8, mbar_wait_b(su32(&yfree[b]), (uint32_t)((gseq / kYB - 1) & 1), vfail))) return false;
+          if (!TWAIT(8, mbar_wait_b(su32(&yfree[b]), ((uint32_t)gseq / (uint32_t)kYB - 1u) & 1u, vfail))) return false;
           fence_after();
         }
         if (lane == 0) {
@@ -852,7 +894,7 @@ struct Ring1 { int nr, no, nq; };
 
 template <int RP>
 size_t smem1(const Ring1& g) {
-  return 1024 + (size_t)g.nr * kStage1 + (size_t)g.no * 2 * kStage1 + (size_t)g.nq * (2 * RP * 128) +
+  return 1024 + (size_t)g.nr * kStage1 + (size_t)g.no * (2 * RP * 128) +
          (5 * kMaxStages + 2 * kMaxDB + 1) * 8 + 16;
 }
 
