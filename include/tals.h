@@ -85,9 +85,12 @@ typedef struct {
   int bulk_sweeps;       /* mixed precision: most BF16 sweeps per mode (default 8) */
   int use_graph;         /* 1 (default): run each mode's sweep loop as one CUDA graph whose
                             device-side while-node evaluates the stop rule; 0: host loop */
-  int fp32_engine;       /* FP32 products: 0 (default, auto) the faster engine per mode -- at
-                            present exact FP32 on CUDA cores everywhere; 1 CUDA cores for every
-                            mode; 2 split-precision 3xTF32 on the tcgen05 tensor cores for
+  int fp32_engine;       /* FP32 products: 0 (default, auto) the faster engine per mode -- the
+                            split-precision tensor-core passes for the modes of rank above 32
+                            that read the full-size tensor (where they measured faster than
+                            the CUDA-core fused pass), exact FP32 on CUDA cores elsewhere;
+                            1 CUDA cores for every mode; 2 split-precision 3xTF32 on the
+                            tcgen05 tensor cores for
                             every mode whose view qualifies (two passes per sweep; views with
                             Q % 32 == 0, I <= 1024, R <= 64), the stop rule's e_k and the
                             reported error taken from the explicit residual ||B_(n) - Q W^T||

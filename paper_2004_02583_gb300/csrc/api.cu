@@ -202,10 +202,12 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
 // Per-mode ALS (Alg. 3) on a given tensor view
 // ---------------------------------------------------------------------------
 
-// Whether fp32_engine 0 (auto) puts the full-size FP32 modes on the split-precision
-// tensor-core passes: off while they are slower than the exact-FP32 CUDA-core pass
-// on the benchmark view (0.35 + 0.53 ms against 0.49 ms per sweep at 512^3, R = 32).
-constexpr bool kT32Auto = false;
+// fp32_engine 0 (auto) puts the full-size FP32 modes of rank above 32 on the
+// split-precision tensor-core passes: measured at 512^3, W + Y pass 0.221 + 0.447 ms
+// (R = 48) and 0.235 + 0.498 ms (R = 64) against 0.951 ms for the CUDA-core fused
+// pass, which runs two rank chunks there; at R <= 32 the fused pass is faster
+// (0.489 ms against 0.210 + 0.407 ms at R = 32).
+constexpr int kT32AutoMinRank = 33;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
@@ -249,7 +251,7 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // explicit residual instead of the per-sweep one)
   j.t32 = 0;
   const int eng = c->opts.fp32_engine;
-  const bool want = eng == 2 || (eng == 0 && kT32Auto && !j.resid && !j.resid_kernel);
+  const bool want = eng == 2 || (eng == 0 && j.R >= kT32AutoMinRank && !j.resid && !j.resid_kernel);
   if (c->dtype == TALS_F32 && want && c->QS != nullptr && t32_supported(j.v, j.R) &&
       (uintptr_t)j.X % 16 == 0) {
     void* w = j.Wdest;

@@ -534,7 +534,7 @@ __device__ __forceinline__ bool t32_prep_w(const T32Args& a, unsigned char* ring
   const uint32_t ph = ((uint32_t)lt / (uint32_t)ns) & 1u;
   if (!mbar_wait_b(su32(&full[slot]), ph, vfail)) return false;
   const long long j0 = (col + lt * ncol) * 32;
-  unsigned char* w2 = ring + (size_t)slot * kSB + 2 * kStage2;
+  unsigned char* w2 = ring + (size_t)slot * kSB + kStage2;
   unsigned char* w3 = w2 + kW2;
   for (int e = t; e < 32 * a.R; e += 64) {
     const int r = e >> 5, q = e & 31;
@@ -565,15 +565,16 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
   constexpr uint32_t kQP = 128u * KB * 128u;          // one plane of Q_c: K-major, 128 rows
   constexpr uint32_t kW2 = 2u * RP * 128u;            // W block, Y product: rows [W_hi | W_lo]
   constexpr uint32_t kW3 = 64u * KB * 128u;           // W block, P product: rows [q hi | q lo]
-  constexpr uint32_t kSB = 2u * kStage2 + kW2 + kW3;  // stage: B hi | B lo | W2 | W3
+  constexpr uint32_t kSB = kStage2 + kW2 + kW3;       // stage: B | W2 | W3
   unsigned char* qhi = base;
   unsigned char* qlo = qhi + kQP;
   unsigned char* ring = qlo + kQP;
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)ns * kSB);
   uint64_t* full = bars;                      // B (and W) landed (tx)
   uint64_t* wrdy = full + kMaxStages;         // W block prepared (128 arrivals)
-  uint64_t* splt = wrdy + kMaxStages;         // residual taken, B split (128 arrivals)
-  uint64_t* empty = splt + kMaxStages;        // MMAs done with the stage (commit)
+  uint64_t* afull = wrdy + kMaxStages;        // [nA] B split into an A stage of tensor memory (128)
+  uint64_t* aempty = afull + kMaxDB;          // [nA] MMAs done with the A stage (commit)
+  uint64_t* empty = aempty + kMaxDB;          // MMAs done with the stage (commit)
   uint64_t* pready = empty + kMaxStages;      // [2] P in tensor memory (commit)
   uint64_t* pfree = pready + 2;               // [2] P read out (128 arrivals)
   uint64_t* yfull = pfree + 2;                // [kYB] K-step products of Y ready (commit)
@@ -595,8 +596,11 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     for (int k = 0; k < kMaxStages; ++k) {
       mbar_init(su32(&full[k]), 1);
       mbar_init(su32(&wrdy[k]), 64);
-      mbar_init(su32(&splt[k]), 128);
       mbar_init(su32(&empty[k]), 1);
+    }
+    for (int k = 0; k < kMaxDB; ++k) {
+      mbar_init(su32(&afull[k]), 128);
+      mbar_init(su32(&aempty[k]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(su32(&pready[b]), 1);
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
   // W blocks: rows beyond R (and the K columns beyond R of the P operand) are read
   // by the MMAs and never written: zero every stage's W regions once
   for (int sl = 0; sl < ns; ++sl) {
-    uint4* w = reinterpret_cast<uint4*>(ring + (size_t)sl * kSB + 2 * kStage2);
+    uint4* w = reinterpret_cast<uint4*>(ring + (size_t)sl * kSB + kStage2);
     for (int e = tid; e < (int)((kW2 + kW3) / 16); e += kT32Threads2) w[e] = make_uint4(0u, 0u, 0u, 0u);
   }
   fence_async_smem();
@@ -624,10 +628,15 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
   // tensor memory over a whole pass, that bias varies from row to row and tilts the
   // weakest directions of the basis), summed in registers by warps 0-3; P buffers
   // at 384 and 448.
+  // The A operand of the Y product (the stage's B split into hi | lo: lane = row,
+  // column = block column) lives in tensor memory too, in nA stages of 64 columns
+  // just below the P buffers.
   constexpr int kYS = (2 * RP + 31) / 32 * 32;
-  constexpr int kYB = 384 / kYS < kMaxDB ? 384 / kYS : kMaxDB;
-  constexpr uint32_t kCols = 512;
+  constexpr int nA = (RP <= 32 || RP == 64) ? 2 : 3;
   constexpr uint32_t kPCol = 384;
+  constexpr uint32_t kACol = kPCol - 64u * nA;
+  constexpr int kYB = (int)kACol / kYS < kMaxDB ? (int)kACol / kYS : kMaxDB;
+  constexpr uint32_t kCols = 512;
   if (warp == 0) tmem_alloc(su32(tmem_holder), kCols);
   fence_before();
   __syncthreads();
@@ -649,7 +658,7 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
         unsigned char* st = ring + (size_t)slot * kSB;
         mbar_expect_tx(su32(&full[slot]), (uint32_t)kStage2 + (resid ? (uint32_t)a.R * 128u : 0u));
         tma_load_3d(su32(st), &bmap, su32(&full[slot]), (int)q, chunk * kRows2, (int)p);
-        if (resid) tma_load_3d(su32(st + 2 * kStage2), &wmap, su32(&full[slot]), (int)q, 0, (int)p);
+        if (resid) tma_load_3d(su32(st + kStage2), &wmap, su32(&full[slot]), (int)q, 0, (int)p);
       }
       __syncwarp();
     }
@@ -729,6 +738,8 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
     long long seq = 0;
     bool ok = true;
     float sh = 0.f, sl = 0.f;   // residual sum (init: ||B||^2)
+    int ai = 0;
+    uint32_t aph = 0;
     for (long long lt = 0; lt < nt && ok; ++lt, ++seq) {
       const int slot = (int)((uint32_t)seq % (uint32_t)ns);
       const uint32_t ph = ((uint32_t)seq / (uint32_t)ns) & 1u;
@@ -752,6 +763,7 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
       }
       unsigned char* st = ring + (size_t)slot * kSB;
       unsigned char* row = st + t * 128;
+      uint32_t hi[32], lo[32];
 #pragma unroll
       for (int c4 = 0; c4 < 8; ++c4) {
         // chunk c4 of the row holds columns 4 c4 .. 4 c4 + 3
@@ -769,11 +781,29 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
           acc_sq(x.w, sh, sl);
         }
         const float4 l = split4(x);
-        *reinterpret_cast<float4*>(row + off) = x;
-        *reinterpret_cast<float4*>(row + kStage2 + off) = l;
+        hi[4 * c4] = __float_as_uint(x.x);
+        hi[4 * c4 + 1] = __float_as_uint(x.y);
+        hi[4 * c4 + 2] = __float_as_uint(x.z);
+        hi[4 * c4 + 3] = __float_as_uint(x.w);
+        lo[4 * c4] = __float_as_uint(l.x);
+        lo[4 * c4 + 1] = __float_as_uint(l.y);
+        lo[4 * c4 + 2] = __float_as_uint(l.z);
+        lo[4 * c4 + 3] = __float_as_uint(l.w);
       }
-      fence_async_smem();
-      mbar_arrive(su32(&splt[slot]));
+      // the row's hi and lo into its lane of A stage ai, once the MMAs are done with it
+      ok = TWAIT(9, mbar_wait_b(su32(&aempty[ai]), aph ^ 1u, vfail));
+      if (!ok) break;
+      fence_after();
+      const uint32_t ta = tmem + kACol + (uint32_t)ai * 64u + ((uint32_t)((warp & 3) * 32) << 16);
+      tmem_st32(ta, hi);
+      tmem_st32(ta + 32u, lo);
+      tmem_wait_st();
+      fence_before();
+      mbar_arrive(su32(&afull[ai]));
+      if (++ai == nA) {
+        ai = 0;
+        aph ^= 1u;
+      }
     }
     const double tot = split_sum(sh, sl, red4, t);
     if (t == 0) a.spart[(size_t)col * gridDim.x + chunk] = tot;
@@ -797,7 +827,7 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
         return false;
       fence_after();
       if (lane == 0) {
-        const uint32_t w3 = su32(ring + (size_t)slot * kSB) + 2 * kStage2 + kW2;
+        const uint32_t w3 = su32(ring + (size_t)slot * kSB) + kStage2 + kW2;
         const uint32_t d = tmem + kPCol + (uint32_t)(pb * 64);
 #pragma unroll
         for (int ks = 0; ks < RP / 8; ++ks) {
@@ -815,13 +845,16 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
       return true;
     };
     long long gseq = 0;
+    int ai = 0;
+    uint32_t aph = 0;
     // stage lt's Y product (after its residual and split), in groups of F K-steps
     auto issue_y = [&](long long lt) -> bool {
       const int slot = (int)((uint32_t)lt % (uint32_t)ns);
-      if (!TWAIT(7, mbar_wait_b(su32(&splt[slot]), ((uint32_t)lt / (uint32_t)ns) & 1u, vfail))) return false;
+      if (!TWAIT(7, mbar_wait_b(su32(&afull[ai]), aph, vfail))) return false;
       fence_after();
       const uint32_t st = su32(ring + (size_t)slot * kSB);
-      const uint32_t w2 = st + 2 * kStage2;
+      const uint32_t w2 = st + kStage2;
+      const uint32_t aop = tmem + kACol + (uint32_t)ai * 64u;   // A stage: hi at +0, lo at +32
       for (int g = 0; g < 4 / F; ++g, ++gseq) {
         const int b = (int)((uint32_t)gseq % (uint32_t)kYB);
         if (gseq >= kYB) {
@@ -832,18 +865,23 @@ __global__ void __launch_bounds__(kT32Threads2, 1)
           const uint32_t d = tmem + (uint32_t)(b * kYS);
           for (int k = 0; k < F; ++k) {
             const int ks = g * F + k;
-            const uint64_t ahi = desc_sw128(st + ks * 32, 16, 1024);
-            const uint64_t alo = desc_sw128(st + kStage2 + ks * 32, 16, 1024);
             const uint64_t bw = desc_sw128(w2 + ks * 32, 16, 1024);
-            mma_tf32(d, ahi, bw, kIdY2, k ? 1u : 0u);   // [B_hi W_hi | B_hi W_lo]
-            mma_tf32(d + RP, alo, bw, kIdY1, 1u);       // + B_lo W_hi into the correction
+            mma_tf32_ts(d, aop + (uint32_t)(ks * 8), bw, kIdY2, k ? 1u : 0u);        // [B_hi W_hi | B_hi W_lo]
+            mma_tf32_ts(d + RP, aop + 32u + (uint32_t)(ks * 8), bw, kIdY1, 1u);      // + B_lo W_hi
           }
           mma_commit(su32(&yfull[b]));
         }
         __syncwarp();
       }
-      if (lane == 0) mma_commit(su32(&empty[slot]));
+      if (lane == 0) {
+        mma_commit(su32(&empty[slot]));
+        mma_commit(su32(&aempty[ai]));
+      }
       __syncwarp();
+      if (++ai == nA) {
+        ai = 0;
+        aph ^= 1u;
+      }
       return true;
     };
     // software pipeline: the next stage's P product goes ahead of this stage's Y
@@ -901,8 +939,8 @@ size_t smem1(const Ring1& g) {
 template <int RP>
 size_t smem2(int ns) {
   constexpr size_t KB = (RP + 31) / 32;
-  const size_t stage = 2 * (size_t)kStage2 + 2 * RP * 128 + 64 * KB * 128;
-  return 1024 + 2 * (128 * KB * 128) + (size_t)ns * stage + (4 * kMaxStages + 6 + 2 * kMaxDB) * 8 + 16;
+  const size_t stage = (size_t)kStage2 + 2 * RP * 128 + 64 * KB * 128;
+  return 1024 + 2 * (128 * KB * 128) + (size_t)ns * stage + (3 * kMaxStages + 6 + 4 * kMaxDB) * 8 + 16;
 }
 
 // K-steps (of 8) per accumulation group: four, i.e. one group per 32-row stage.
