@@ -211,10 +211,11 @@ def main():
                     help="skip the other precision path (per-path launch lists under ncu)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="only launch the mode-1 sweep pass twice (for an ncu capture)")
-    ap.add_argument("--profile-what", default="pass", choices=["pass", "tf32", "decomp"],
+    ap.add_argument("--profile-what", default="pass", choices=["pass", "tf32", "products", "decomp"],
                     help="with --profile-pass: pass (the fused sweep pass), tf32 (the split-precision "
-                         "W and Y passes, one timed launch each after one warm-up), decomp (one "
-                         "decomposition: its split sweep's W product and W statistics)")
+                         "W and Y passes, one timed launch each after one warm-up), products (the "
+                         "two-product form's mode product and split-K Y product, likewise), decomp "
+                         "(one decomposition: its split sweep's W product and W statistics)")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="c4: number of tensors (4096 is the workload; fewer for profiling)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "tucker"],
@@ -252,8 +253,8 @@ def main():
     ctx = tals.Context(A, RANKS, eta=ETA, seed=1, precision=args.precision,
                        use_graph=not args.no_graph)
     if args.profile_pass:
-        if args.profile_what == "tf32":
-            ms_, by_, fl_ = ctx.time_sweep(mode=0, engine="tf32", iters=1)
+        if args.profile_what in ("tf32", "products"):
+            ms_, by_, fl_ = ctx.time_sweep(mode=0, engine=args.profile_what, iters=1)
         elif args.profile_what == "decomp":
             G = torch.empty(RANKS, device="cuda")
             Us = [torch.empty((d, r), device="cuda") for d, r in zip(DIMS, RANKS)]
@@ -471,13 +472,18 @@ def main():
     }
     # kernels per step: per mode 10 (initial guess chain) + the factor copy, 9 per
     # CUDA-core or BF16 sweep, 12 per split-precision sweep (basis split, W pass,
-    # ||W||^2 sum, Y pass + the 8-kernel tail), 4 more per FP32 sweep of a mode whose
-    # sweeps can run split (W product, W statistics, test, Y pass: each launched,
-    # each exiting at once when its sweep is not split), plus the BF16 conversion of
-    # each mode that runs bulk sweeps
-    launches = (sum(11 + 9 * n + 3 * t + (4 * (n - b) if sc else 0)
-                    for n, t, b, sc in zip(st["sweeps"], st["tc_sweeps"], st["bulk_sweeps"],
-                                           st["split_capable"])) +
+    # ||W||^2 sum, Y pass + the 8-kernel tail), 10 per FP32 sweep on the two-product
+    # form (mode product, split-K Y product + the tail); per FP32 sweep of a mode whose
+    # sweeps can run split, 4 more on the fused pass (W product, W statistics, test,
+    # Y pass) or 2 more on the two-product form (W statistics, test), each exiting at
+    # once when its sweep is not split; plus the BF16 conversion of each mode that
+    # runs bulk sweeps
+    def _extra(prod, sc):
+        return (1 + (2 if sc else 0)) if prod else (4 if sc else 0)
+
+    launches = (sum(11 + 9 * n + 3 * t + (n - b) * _extra(pr, sc)
+                    for n, t, b, sc, pr in zip(st["sweeps"], st["tc_sweeps"], st["bulk_sweeps"],
+                                               st["split_capable"], st["two_product"])) +
                 sum(1 for b in st["bulk_sweeps"] if b > 0))
     mixed_st = st if args.precision == "mixed_bf16" else ost
     plain_st = st if args.precision == "native" else ost
@@ -492,7 +498,7 @@ def main():
         "config": {"workload": "st-HOSVD-ALS 512x512x512 FP32 rank (32,32,32) 1/k spectrum "
                                "1e-2 noise eta 1e-6", "precision": args.precision,
                    "time_to_tol_ms": round(ms, 4), "sweeps": st["sweeps"],
-                   "split_sweeps": st["split_sweeps"],
+                   "split_sweeps": st["split_sweeps"], "two_product": st["two_product"],
                    "bulk_sweeps": st["bulk_sweeps"], "tc_sweeps": st["tc_sweeps"],
                    "rel_err": st["rel_err"],
                    "mixed_vs_fp32_plain": {

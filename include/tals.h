@@ -87,14 +87,20 @@ typedef struct {
                             device-side while-node evaluates the stop rule; 0: host loop */
   int fp32_engine;       /* FP32 products: 0 (default, auto) the faster engine per mode -- the
                             split-precision tensor-core passes for the modes of rank above 32
-                            that read the full-size tensor (where they measured faster than
-                            the CUDA-core fused pass), exact FP32 on CUDA cores elsewhere;
-                            1 CUDA cores for every mode; 2 split-precision 3xTF32 on the
-                            tcgen05 tensor cores for
-                            every mode whose view qualifies (two passes per sweep; views with
-                            Q % 32 == 0, I <= 1024, R <= 64), the stop rule's e_k and the
-                            reported error taken from the explicit residual ||B_(n) - Q W^T||
-                            formed in the second pass. */
+                            that read the full-size tensor, the two-product form (engine 3)
+                            for the modes of rank up to 32 whose view has at least 2^26
+                            elements (each where it measured faster than the fused pass),
+                            the fused CUDA-core pass elsewhere; 1 the fused CUDA-core pass
+                            for every mode; 2 split-precision 3xTF32 on the tcgen05 tensor
+                            cores for every mode whose view qualifies (two passes per sweep;
+                            views with Q % 32 == 0, I <= 1024, R <= 64), the stop rule's e_k
+                            and the reported error taken from the explicit residual
+                            ||B_(n) - Q W^T|| formed in the second pass; 3 the two-product
+                            form on CUDA cores (exact FP32 arithmetic) for every mode whose
+                            view qualifies (R <= 64, Q % 16 == 0, 16-byte aligned data):
+                            W = B x_n Q^T by the register-tiled mode product, then
+                            Y = B_(n) W split over column ranges -- two reads of B per
+                            sweep. */
 } tals_opts;
 
 typedef struct {
@@ -112,6 +118,8 @@ typedef struct {
                                            predicted to be the last forms W alone, takes the
                                            Eq. 5.01 test, and forms Y only if the loop goes on */
   int split_sweeps[TALS_MAX_NDIM];      /* sweeps of mode n that ran split */
+  int two_product[TALS_MAX_NDIM];       /* 1 if mode n's FP32 sweeps ran as two products (the
+                                           mode product W, then the split-K Y = B_(n) W) */
 } tals_stats;
 
 typedef struct tals_ctx tals_ctx;
@@ -262,9 +270,10 @@ tals_status tals_time_pass(tals_ctx* ctx, int mode, int iters, double* ms, doubl
  * sweep of `mode` on the context's tensor A, `iters` times after one warm-up, with
  * CUDA events recorded on the context's stream around each launch. engine 0: the
  * fused FP32 CUDA-core pass; 1: the fused BF16 tensor-core pass (mixed-precision
- * contexts only); 2: the two split-precision 3xTF32 tensor-core passes.
+ * contexts only); 2: the two split-precision 3xTF32 tensor-core passes; 3: the
+ * two-product form (FP32 mode product W, then the split-K product Y = B_(n) W).
  * ms_out[0], bytes_out[0]: mean duration and algorithmic bytes of the first (or
- * only) pass; ms_out[1], bytes_out[1]: the second pass of engine 2, else 0 (both
+ * only) pass; ms_out[1], bytes_out[1]: the second pass of engines 2 and 3, else 0 (both
  * host arrays of 2). *flops: FP32-equivalent flops of the sweep (4 R_n prod(I)).
  * TALS_ENOTSUP when the mode's view is outside the engine's limits. Synchronises
  * the stream. */
@@ -290,8 +299,13 @@ tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, in
  * FP32 accumulation) on a BF16 copy of A; needs I_mode % 128 == 0, I_mode <= 512,
  * prod of the later sizes % 128 == 0 and R <= 64. engine 2: the two split-precision
  * (3xTF32) tensor-core passes on A itself; needs prod of the later sizes % 32 == 0,
- * I_mode <= 1024, R <= 64 and a 16-byte aligned A. Shapes outside an engine's limits
- * return TALS_ENOTSUP. Uses stream-ordered scratch and synchronises the stream. */
+ * I_mode <= 1024, R <= 64 and a 16-byte aligned A. engines 3 and 4 (diagnostics):
+ * one of engine 2's passes replaced by the CUDA-core pass (3: tensor-core W; 4:
+ * tensor-core Y). engine 5: the two-product form on CUDA cores (W = B^T Q by the
+ * register-tiled mode product, then Y = B W split over column ranges); needs
+ * R <= 64, prod of the later sizes % 16 == 0 and a 16-byte aligned A. Shapes outside
+ * an engine's limits return TALS_ENOTSUP. Uses stream-ordered scratch and
+ * synchronises the stream. */
 tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* dims, int mode, const void* Q,
                             int R, int engine, double* Y_out, double* wnorm2, void* stream);
 

@@ -46,7 +46,8 @@ class tals_stats(ctypes.Structure):
                 ("tc_sweeps", ctypes.c_int * MAX_NDIM),
                 ("converged", ctypes.c_int * MAX_NDIM), ("order", ctypes.c_int * MAX_NDIM),
                 ("status", ctypes.c_int), ("split_capable", ctypes.c_int * MAX_NDIM),
-                ("split_sweeps", ctypes.c_int * MAX_NDIM)]
+                ("split_sweeps", ctypes.c_int * MAX_NDIM),
+                ("two_product", ctypes.c_int * MAX_NDIM)]
 
     def to_dict(self, ndim: int) -> dict:
         return {"rel_err": self.rel_err, "norm_a": self.norm_a,
@@ -57,7 +58,8 @@ class tals_stats(ctypes.Structure):
                 "converged": [bool(x) for x in self.converged[:ndim]],
                 "order": list(self.order[:ndim]), "status": self.status,
                 "split_capable": [bool(x) for x in self.split_capable[:ndim]],
-                "split_sweeps": list(self.split_sweeps[:ndim])}
+                "split_sweeps": list(self.split_sweeps[:ndim]),
+                "two_product": [bool(x) for x in self.two_product[:ndim]]}
 
 
 class tals_hooi_stats(ctypes.Structure):
@@ -193,7 +195,7 @@ def default_opts(**kw) -> tals_opts:
             o.order[i] = int(n)
     eng = kw.pop("fp32_engine", None)
     if eng is not None:
-        o.fp32_engine = {"auto": 0, "cuda": 1, "tensor": 2}.get(eng, eng)
+        o.fp32_engine = {"auto": 0, "cuda": 1, "fused": 1, "tensor": 2, "products": 3}.get(eng, eng)
     prec = kw.pop("precision", None)
     if prec is not None:
         o.precision = {"native": PREC_NATIVE, "mixed_bf16": PREC_MIXED_BF16}.get(prec, prec)
@@ -387,12 +389,12 @@ class Context:
 
     def time_sweep(self, mode: int = 0, engine: str = "tf32", iters: int = 10):
         """Per-pass mean durations (ms) and algorithmic bytes of one sweep's product
-        passes, and the sweep's FP32-equivalent flops. engine: "cuda", "tc" or "tf32"
-        (two passes: W, then Y)."""
+        passes, and the sweep's FP32-equivalent flops. engine: "cuda", "tc", "tf32"
+        or "products" (the last two: two passes, W then Y)."""
         ms = (ctypes.c_double * 2)()
         by = (ctypes.c_double * 2)()
         fl = ctypes.c_double()
-        code = {"cuda": 0, "tc": 1, "tf32": 2}[engine]
+        code = {"cuda": 0, "tc": 1, "tf32": 2, "products": 3}[engine]
         _check(lib().tals_time_sweep(self._h, int(mode), code, int(iters), ms, by, ctypes.byref(fl)))
         return list(ms), list(by), fl.value
 
@@ -678,9 +680,10 @@ def sweep_pass(A, mode, Q, engine="cuda", stream=None):
     for the mode-`mode` unfolding B of the FP32 tensor A. engine: "cuda" (fused pass,
     FP32 CUDA cores), "tc" (fused pass, tcgen05 BF16 on a BF16 copy) or "tf32" (two
     passes, tcgen05 split-precision 3xTF32 on the FP32 tensor); "tf32_w" / "tf32_y"
-    replace the Y or the W pass of "tf32" by the CUDA-core pass (diagnostics)."""
+    replace the Y or the W pass of "tf32" by the CUDA-core pass (diagnostics);
+    "products" (FP32 CUDA cores: the mode product W, then the split-K Y = B W)."""
     torch = _torch()
-    if engine not in ("cuda", "tc", "tf32", "tf32_w", "tf32_y"):
+    if engine not in ("cuda", "tc", "tf32", "tf32_w", "tf32_y", "products"):
         raise ValueError(f"unknown engine {engine!r}")
     if A.dtype != torch.float32 or Q.dtype != torch.float32:
         raise ValueError("sweep_pass needs FP32 A and Q")
@@ -695,7 +698,8 @@ def sweep_pass(A, mode, Q, engine="cuda", stream=None):
     Y = torch.empty((int(A.shape[mode]), R), dtype=torch.float64, device=A.device)
     w2 = ctypes.c_double()
     _check(lib().tals_sweep_pass(A.data_ptr(), ndim, dims, int(mode), Q.data_ptr(), R,
-                                 {"cuda": 0, "tc": 1, "tf32": 2, "tf32_w": 3, "tf32_y": 4}[engine],
+                                 {"cuda": 0, "tc": 1, "tf32": 2, "tf32_w": 3, "tf32_y": 4,
+                                  "products": 5}[engine],
                                  Y.data_ptr(), ctypes.byref(w2),
                                  _stream_ptr(stream)))
     return Y, w2.value

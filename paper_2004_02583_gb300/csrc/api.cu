@@ -84,6 +84,12 @@ struct Need {
       // split sweeps: the W statistics' partials after the pass's, W in a scratch buffer
       spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y + 2 * (size_t)split_stat_blocks(v, sms));
       tbuf = std::max(tbuf, (size_t)(v.J() * R));
+      if (R <= 64 && v.Q % 16 == 0) {
+        // the two-product form: the split-K Y product's partials and ||W||^2 partials
+        const size_t S = (size_t)adjoint_rows_splits(v, R, sms);
+        ypart = std::max(ypart, S * (size_t)v.I * (size_t)R);
+        spart = std::max(spart, S + 2 * (size_t)split_stat_blocks(v, sms));
+      }
     }
     if (sweep && dtype == TALS_F32 && t32_supported(v, R)) {
       // split-precision passes: per-CTA Y partials, W written every sweep (into a
@@ -208,6 +214,11 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
 // pass, which runs two rank chunks there; at R <= 32 the fused pass is faster
 // (0.489 ms against 0.210 + 0.407 ms at R = 32).
 constexpr int kT32AutoMinRank = 33;
+// fp32_engine 0 (auto) runs the full-size FP32 modes of rank up to 32 whose view
+// has at least this many elements on the two-product form: W by the register-tiled
+// mode product, Y = B W by the split-K adjoint (adjoint.cu).
+constexpr int kProdAutoMaxRank = 32;
+constexpr long long kProdAutoMinElems = 64LL << 20;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
@@ -265,21 +276,45 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
       j.g2 = t32_grid(j.v, 2, c->sms);
     }
   }
-  // FP32 modes on the fused pass whose error comes from ||B||^2 - ||W||^2: a sweep
-  // predicted to be the last forms W alone (register-tiled mode product into the
-  // destination or a scratch buffer), takes the test, and forms Y only if needed
+  // Full-size FP32 modes of rank <= 32 (engine 3: every mode whose view qualifies)
+  // on two products per sweep, W = B x_n Q_k^T (register-tiled mode product) into
+  // the destination or a scratch buffer, then Y = B W (split-K adjoint, which also
+  // sums ||W||^2): two reads of B, each product at a higher FMA rate than the
+  // fused pass reaches with both
+  j.prod = 0;
+  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32 &&
+      (eng == 3 || (eng == 0 && j.R <= kProdAutoMaxRank && mine >= kProdAutoMinElems))) {
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    const bool room = j.Wdest != nullptr || (size_t)(j.v.J() * j.R) <= c->tbuf_elems;
+    const size_t ir = (size_t)j.v.I * j.R;
+    const long long S = std::min<long long>(adjoint_rows_splits(j.v, j.R, c->sms),
+                                            (long long)std::min<size_t>(c->ypart_elems / ir, c->spart_n));
+    if (w != j.X && room && S >= 1 && adjoint_rows_ok(j.v, j.R, j.X, w) &&
+        mode_gemm_gated_ok((const float*)j.X, j.v.P, j.v.I, j.v.Q, (const float*)c->Lt, 1, j.R, j.R,
+                           (float*)w)) {
+      j.prod = 1;
+      j.Wt = w;
+      j.ys = (int)S;
+    }
+  }
+  // FP32 modes whose error comes from ||B||^2 - ||W||^2: a sweep predicted to be
+  // the last forms W alone (the register-tiled mode product into the destination
+  // or a scratch buffer), takes the test, and forms Y only if needed
   j.split_ok = 0;
   if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32) {
-    void* w = j.Wdest;
+    void* w = j.prod ? j.Wt : j.Wdest;
     if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
     const int nb = split_stat_blocks(j.v, c->sms);
     const bool room = j.Wdest != nullptr || (size_t)(j.v.J() * j.R) <= c->tbuf_elems;
-    if (w != j.X && room && (size_t)j.pc.grid_x * j.pc.grid_y + 2 * (size_t)nb <= c->spart_n &&
+    const size_t wpo = j.prod ? (size_t)j.ys : (size_t)j.pc.grid_x * j.pc.grid_y;
+    if (w != j.X && room && wpo + 2 * (size_t)nb <= c->spart_n &&
         mode_gemm_gated_ok((const float*)j.X, j.v.P, j.v.I, j.v.Q, (const float*)c->Lt, 1, j.R, j.R,
                            (float*)w)) {
       j.split_ok = 1;
       j.Wt = w;
       j.nbw = nb;
+      j.wpo = wpo;
     }
   }
   return TALS_OK;
@@ -301,7 +336,7 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
 #define TALS_CK(x)                                   \
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
   TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
-                            j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32, j.split_ok));
+                            j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32, j.split_ok, j.prod));
   if (j.twopass) return twopass_init_launch(c, j, set_norm_a);
   if (j.t32) {
     // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
@@ -358,6 +393,21 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
                              (float*)c->Ypart, c->spart, c->t32_err, j.g2, s, 0, 0, j.st));
     return mode_sweep_tail(c, j, j.g2, np, 1);
   }
+  if (j.prod) {
+    // W = B^T Q_k (Alg. 3 R-update) by the mode product; on a split sweep its
+    // statistics and the Eq. 5.01 step (both exit at once otherwise); then Y = B W
+    // (Alg. 3 L-update) and the ||W||^2 partials unless the test stopped the mode
+    TALS_CK(launch_mode_gemm_gated((const float*)j.X, j.v.P, I, j.v.Q, (const float*)c->Lt, 1, R, R,
+                                   (float*)j.Wt, j.st, s, 1));
+    if (j.split_ok) {
+      double* wpart = c->spart + j.wpo;
+      TALS_CK(launch_split_stats((const float*)j.Wt, j.v, R, c->GfinL, j.st, wpart, j.nbw, s));
+      TALS_CK(launch_split_test(wpart, j.nbw, j.st, c->norm_a2, j.cond, j.has_cond, s));
+    }
+    TALS_CK(launch_adjoint_rows((const float*)j.X, j.v, (const float*)j.Wt, R, j.ys, (float*)c->Ypart,
+                                c->spart, j.st, s));
+    return mode_sweep_tail(c, j, j.ys, j.ys, 1);
+  }
   // one read of B: W = B^T Q_k (LS optimum for Q_k, Alg. 3 R-update), Y = B W
   // (the pass exits at once on a split sweep)
   TALS_CK(launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, R, c->Lt, c->Ypart, c->spart,
@@ -365,7 +415,7 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   if (j.split_ok) {
     // a split sweep (each kernel exits at once otherwise): W alone, its statistics
     // and the Eq. 5.01 step, then Y = B W only if the mode goes on
-    double* wpart = c->spart + (size_t)j.pc.grid_x * j.pc.grid_y;
+    double* wpart = c->spart + j.wpo;
     TALS_CK(launch_mode_gemm_gated((const float*)j.X, j.v.P, I, j.v.Q, (const float*)c->Lt, 1, R, R,
                                    (float*)j.Wt, j.st, s));
     TALS_CK(launch_split_stats((const float*)j.Wt, j.v, R, c->GfinL, j.st, wpart, j.nbw, s));
@@ -654,6 +704,7 @@ static void fill_mode_stats(tals_ctx* c, int n, tals_stats* st) {
   st->tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
   st->split_capable[n] = ms.split_ok;
   st->split_sweeps[n] = ms.nsplit;
+  st->two_product[n] = ms.prod;
   st->converged[n] = ms.converged;
   if (ms.status && !st->status) st->status = ms.status;
 }
@@ -958,7 +1009,7 @@ tals_status tals_pass_plan(int dtype, int64_t P, int64_t I, int64_t Q, int R, in
 
 tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double* ms_out,
                             double* bytes_out, double* flops) {
-  if (!c || mode < 0 || mode >= c->N || iters < 1 || engine < 0 || engine > 2 || !ms_out || !bytes_out)
+  if (!c || mode < 0 || mode >= c->N || iters < 1 || engine < 0 || engine > 3 || !ms_out || !bytes_out)
     return fail(TALS_EINVAL, "bad arguments");
   ModeJob j;
   j.n = mode;
@@ -979,6 +1030,15 @@ tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double
   if (engine == 2 && !(c->dtype == TALS_F32 && c->QS && t32_supported(j.v, j.R) &&
                        (uintptr_t)j.X % 16 == 0))
     return fail(TALS_ENOTSUP, "view outside the split-precision pass limits");
+  if (engine == 3 &&
+      !(c->dtype == TALS_F32 && adjoint_rows_ok(j.v, j.R, j.X, c->tbuf[1]) &&
+        mode_gemm_gated_ok((const float*)j.X, j.v.P, j.v.I, j.v.Q, (const float*)c->Lt, 1, j.R, j.R,
+                           (float*)c->tbuf[1]) &&
+        (size_t)(j.v.J() * j.R) <= c->tbuf_elems && c->tbuf[1] != c->A))
+    return fail(TALS_ENOTSUP, "view outside the two-product form's limits");
+  const int ys = engine == 3 ? (int)std::min<long long>(adjoint_rows_splits(j.v, j.R, c->sms),
+                                                        (long long)(c->ypart_elems / ((size_t)j.v.I * j.R)))
+                             : 0;
   cudaStream_t s = c->stream;
   float* W = (float*)c->tbuf[1];
   cudaEvent_t ev[3];
@@ -994,6 +1054,12 @@ tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double
       e = launch_pass(c->dtype, j.pc, PASS_SWEEP, j.X, j.v, j.R, c->Lt, c->Ypart, c->spart, c->tbuf[0],
                       0, nullptr, 0, s);
       cudaEventRecord(ev[1], s);
+    } else if (engine == 3) {
+      e = launch_mode_gemm((const float*)j.X, j.v.P, j.v.I, j.v.Q, (const float*)c->Lt, 1, j.R, j.R, W, s);
+      cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess)
+        e = launch_adjoint_rows((const float*)j.X, j.v, W, j.R, ys, (float*)c->Ypart, c->spart, nullptr, s);
+      cudaEventRecord(ev[2], s);
     } else {
       e = launch_t32_wpass((const float*)j.X, j.v, j.R, c->QS, W, c->spart + np, c->t32_err, g1, s);
       cudaEventRecord(ev[1], s);
@@ -1005,7 +1071,7 @@ tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double
     if (e == cudaSuccess) e = cudaEventSynchronize(engine == 0 ? ev[1] : ev[2]);
     float t0 = 0.f, t1 = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
-    if (e == cudaSuccess && engine == 2) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    if (e == cudaSuccess && engine >= 2) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
     if (it >= 0) {
       acc[0] += t0;
       acc[1] += t1;
@@ -1016,10 +1082,10 @@ tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double
   if ((st = tc_check(c)) != TALS_OK) return st;
   ms_out[0] = acc[0] / iters;
   bytes_out[0] = T * c->esz + JR * c->esz;   // tensor read + W written
-  if (engine == 2) {
+  if (engine >= 2) {
     ms_out[1] = acc[1] / iters;
     bytes_out[1] = T * 4.0 + JR * 4.0;       // tensor read + W read (once; its other chunk
-                                             // CTAs find it in L2)
+                                             // or row-tile CTAs find it in L2)
   }
   return TALS_OK;
 }

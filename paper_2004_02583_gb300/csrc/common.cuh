@@ -40,6 +40,7 @@ struct ModeState {
   double d_cur;       // |e_{k-1} - e_k| of the last test (negative: no comparison yet)
   double d_prev;      // the one before
   int nsplit;         // sweeps that ran split
+  int prod;           // FP32 sweeps as two products (mode product W, split-K Y)
 };
 
 // The Eq. 5.01 step of an FP32-phase sweep, given e_k (thread 0 of a single-CTA

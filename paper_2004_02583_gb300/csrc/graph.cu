@@ -228,6 +228,7 @@ tals_status collect(tals_ctx* c, int kind, const GraphEntry* en, tals_stats* sta
     local.tc_sweeps[n] = ms.tc_resid ? ms.k - ms.bulk : 0;
     local.split_capable[n] = ms.split_ok;
     local.split_sweeps[n] = ms.nsplit;
+    local.two_product[n] = ms.prod;
     local.converged[n] = ms.converged;
     if (ms.status && !local.status) local.status = ms.status;
   }

@@ -391,11 +391,11 @@ tals_status hooi_run(tals_ctx* c, void* const* U, void* G_out, double tol, int m
       j.Wdest = (n == N - 1) ? G : nullptr;
       if ((rs = mode_setup(c, j)) != TALS_OK) return rs;
       const size_t ir = (size_t)j.v.I * j.R;
-      const size_t yp = (size_t)(j.t32 ? j.g2 : j.pc.grid_x) * ir;
+      const size_t yp = (size_t)(j.t32 ? j.g2 : j.prod ? j.ys : j.pc.grid_x) * ir;
       if (yp > c->ypart_elems || ir > c->need_ir)
         return fail(TALS_ENOTSUP, "HOOI: mode %d exceeds the context's workspace", n);
       if ((e = launch_state_init(j.st, inner_eta, inner_sweeps, j.resid || j.resid_kernel || j.t32, s, 0,
-                                 j.t32, j.split_ok)) != cudaSuccess)
+                                 j.t32, j.split_ok, j.prod)) != cudaSuccess)
         return cuda_fail(e, "HOOI state");
       if ((e = launch_copy(c->Ypart, U[n], ir * esz, s)) != cudaSuccess) return cuda_fail(e, "HOOI warm start");
       if ((rs = mode_init_tail(c, j, false, 1, c->spart, nsp)) != TALS_OK) return rs;

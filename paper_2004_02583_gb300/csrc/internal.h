@@ -31,6 +31,9 @@ struct ModeJob {
   int splits = 1;                // column splits of the two-pass form's Y product
   int split_ok = 0;              // sweeps predicted to be the last run split (split.cu), W in Wt
   int nbw = 0;                   // CTAs of their W statistics
+  size_t wpo = 0;                // offset of those statistics' partials in spart
+  int prod = 0;                  // FP32 sweeps as two products (mode product W, split-K Y)
+  int ys = 0;                    // column splits of that Y product
 };
 
 struct DriveState {

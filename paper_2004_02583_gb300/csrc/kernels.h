@@ -96,9 +96,10 @@ cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s
 
 // Initialise a ModeState (k = 0, flags cleared) on the device. resid: the
 // sweeps accumulate ||B - Q W^T||^2 directly (see PassArgs::resid).
-// tc: the mode's products run on the split-precision tensor-core passes.
+// tc: the mode's products run on the split-precision tensor-core passes;
+// split_ok: sweeps may run split; prod: sweeps run as two products (adjoint.cu).
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max = 0, int tc = 0, int split_ok = 0);
+                              int bulk_max = 0, int tc = 0, int split_ok = 0, int prod = 0);
 
 // Tensor-core (tcgen05, BF16) sweep pass; see tc_pass.cu.
 bool tc_supported(const ModeView& v, int R);
@@ -137,13 +138,14 @@ cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const
                                  const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s);
 // The register-tiled mode product of launch_mode_gemm, its CTAs exiting at once
-// unless gate's sweep is split and not done (cudaErrorNotSupported where the
-// register-tiled plan does not take the view; mode_gemm_gated_ok tells beforehand).
+// unless gate's sweep is split and not done (every = 1: unless the mode is done)
+// (cudaErrorNotSupported where the register-tiled plan does not take the view;
+// mode_gemm_gated_ok tells beforehand).
 bool mode_gemm_gated_ok(const float* X, long long P, long long Bin, long long Q, const float* M, long long sa,
                         long long sb, long long Aout, float* out);
 cudaError_t launch_mode_gemm_gated(const float* X, long long P, long long Bin, long long Q, const float* M,
                                    long long sa, long long sb, long long Aout, float* out, const ModeState* gate,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int every = 0);
 // split.cu: the split sweep's statistics of W (||W||^2 and the rounded-basis term,
 // two FP64 partials per CTA; nb = split_stat_blocks CTAs) and its Eq. 5.01 step.
 int split_stat_blocks(const ModeView& v, int sms);
@@ -151,6 +153,14 @@ cudaError_t launch_split_stats(const float* W, const ModeView& v, int R, const d
                                double* part, int nb, cudaStream_t s);
 cudaError_t launch_split_test(const double* part, int nb, ModeState* st, const double* norm_a2,
                               unsigned long long cond, int has_cond, cudaStream_t s);
+// adjoint.cu: Ypart[s] (I x R) = B_(n) W over the s-th of S column ranges (FP32,
+// R <= 64, Q % 16 == 0, 16-byte aligned X and W; adjoint_rows_ok tells), and, when
+// wsq is set, wsq[s] = ||W||^2 over that range. CTAs exit at once when gate is
+// set and its mode is done.
+bool adjoint_rows_ok(const ModeView& v, int R, const void* X, const void* W);
+int adjoint_rows_splits(const ModeView& v, int R, int sms);
+cudaError_t launch_adjoint_rows(const float* X, const ModeView& v, const float* W, int R, int S, float* part,
+                                double* wsq, const ModeState* gate, cudaStream_t s);
 // Partial sums launch_mode_resid_gemm writes for this view (0: not covered).
 long long mode_resid_gemm_parts(const float* X, long long P, long long Bin, long long Q, const float* M,
                                 long long sa, long long sb, long long Aout, const float* B);

@@ -75,7 +75,7 @@ tals_status mixed_init_launch(tals_ctx* c, ModeJob& j, bool set_norm_a, int grid
                                  s, c->mixed->sq);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 conversion");
   e = launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps, j.resid || j.t32, s, c->opts.bulk_sweeps,
-                        j.t32, j.split_ok);
+                        j.t32, j.split_ok, j.prod);
   if (e == cudaSuccess)
     e = launch_tc_pass(c->mixed->shadow, j.v, j.R, nullptr, (float*)c->Ypart, c->spart,
                        c->mixed->err, grid, s, 1, sketch_state(c->opts.seed, j.n));
@@ -170,7 +170,7 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
                                        const void* Q, int R, int engine, double* Y_out,
                                        double* wnorm2, void* stream) {
   if (!A || !dims || !Q || !Y_out || ndim < 1 || ndim > TALS_MAX_NDIM || mode < 0 || mode >= ndim ||
-      R < 1 || engine < 0 || engine > 4)
+      R < 1 || engine < 0 || engine > 5)
     return fail(TALS_EINVAL, "bad arguments");
   long long d[TALS_MAX_NDIM];
   size_t n = 1;
@@ -203,6 +203,22 @@ extern "C" tals_status tals_sweep_pass(const void* A, int ndim, const int64_t* d
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, nsp * sizeof(double), s);
     if (e == cudaSuccess)
       e = launch_pass(TALS_F32, pc, PASS_SWEEP, A, v, R, Q, ypart, spart, nullptr, 0, nullptr, 0, s);
+  } else if (engine == 5) {
+    // the two-product form: W = B^T Q by the register-tiled mode product, then
+    // Y = B W over column ranges with the ||W||^2 partials
+    const size_t wn = (size_t)v.J() * R;
+    if (!adjoint_rows_ok(v, R, A, A) ||
+        !mode_gemm_gated_ok((const float*)A, v.P, v.I, v.Q, (const float*)Q, 1, R, R, (float*)A))
+      return fail(TALS_ENOTSUP, "shape outside the two-product form's limits");
+    gx = adjoint_rows_splits(v, R, sms);
+    nsp = gx;
+    e = cudaMallocAsync(&ypart, (size_t)gx * v.I * R * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&spart, nsp * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&wbuf, wn * 4, s);
+    if (e == cudaSuccess)
+      e = launch_mode_gemm((const float*)A, v.P, v.I, v.Q, (const float*)Q, 1, R, R, (float*)wbuf, s);
+    if (e == cudaSuccess)
+      e = launch_adjoint_rows((const float*)A, v, (const float*)wbuf, R, gx, (float*)ypart, spart, nullptr, s);
   } else if (engine >= 2) {
     if (!t32_supported(v, R)) return fail(TALS_ENOTSUP, "shape outside the split-TF32 pass limits");
     // engine 3 / 4 (diagnostics): one of the two passes replaced by the CUDA-core

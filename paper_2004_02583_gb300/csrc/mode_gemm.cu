@@ -250,6 +250,7 @@ struct MgArgs {
   int nk;               // K chunks
   int vec;              // 16-byte output stores
   const ModeState* gate;   // when set: run only while the mode's sweep is split and not done
+  int every;               // with gate: run on every sweep until the mode is done
 };
 
 // Tile geometry: TA a (outputs' rank side) x TN (cols: q, rows: p) = 8192
@@ -273,7 +274,7 @@ constexpr size_t mg_smem_floats() {
 // resident M slice, RESID accumulates sum (B - M X)^2 instead of storing.
 template <bool ROWS, bool MRES, bool RESID, int TA>
 __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
-  if (a.gate != nullptr && (!a.gate->split || a.gate->done)) return;   // uniform, before any barrier
+  if (a.gate != nullptr && ((!a.every && !a.gate->split) || a.gate->done)) return;   // uniform, before any barrier
   using S = MgShape<ROWS, TA>;
   constexpr int TN = S::TN, XS = S::XS, ST = S::STAGES;
   constexpr int MS = MRES ? 0 : kMgBK * TA;
@@ -612,10 +613,11 @@ bool mode_gemm_gated_ok(const float* X, long long P, long long Bin, long long Q,
 
 cudaError_t launch_mode_gemm_gated(const float* X, long long P, long long Bin, long long Q, const float* M,
                                    long long sa, long long sb, long long Aout, float* out, const ModeState* gate,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int every) {
   MgPlan pl = mg_plan<false>(X, P, Bin, Q, M, sa, sb, Aout, out);
   if (!pl.ok) return cudaErrorNotSupported;
   pl.a.gate = gate;
+  pl.a.every = every;
   return mg_launch<false>(pl, s);
 }
 

@@ -751,10 +751,11 @@ cudaError_t launch_gram_sum(const double* Gpart, int nb, int R, double* Gfin,
 }
 
 __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int resid,
-                                  int bulk_max, int tc, int split_ok) {
+                                  int bulk_max, int tc, int split_ok, int prod) {
   ModeState z = {};
   z.tc_resid = tc;
   z.split_ok = split_ok;
+  z.prod = prod;
   z.d_cur = -1.0;
   z.d_prev = -1.0;
   z.eta = eta;
@@ -766,8 +767,8 @@ __global__ void state_init_kernel(ModeState* st, double eta, int max_sweeps, int
 }
 
 cudaError_t launch_state_init(ModeState* st, double eta, int max_sweeps, int resid, cudaStream_t s,
-                              int bulk_max, int tc, int split_ok) {
-  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max, tc, split_ok);
+                              int bulk_max, int tc, int split_ok, int prod) {
+  state_init_kernel<<<1, 1, 0, s>>>(st, eta, max_sweeps, resid, bulk_max, tc, split_ok, prod);
   return cudaGetLastError();
 }
 
