@@ -31,8 +31,16 @@
  *   (checked on the host before any launch), TALS_ECUDA for a CUDA runtime
  *   error, TALS_ESINGULAR when an R x R Gram matrix is not numerically positive
  *   definite (the truncation exceeds the numerical rank, Remark 3), TALS_ENOTSUP
- *   for shapes outside the kernels' limits. Contexts (tucker_als_init*): R_n <= 64
- *   (checked on the host). A mode view whose I_n fits the fused sweep pass's
+ *   for shapes outside the kernels' limits. Contexts (tucker_als_init*): R_n <= 1024
+ *   (checked on the host). Modes of rank up to 64 run the sweeps described
+ *   below with their R x R algebra in single-CTA kernels; a mode of rank above 64
+ *   (the dense test of Sec. 6.4, ranks (500, 500, 5)) forms its products as
+ *   GEMMs (W = B^T Q, then Y = B W over column ranges of at most 2048 added in
+ *   FP64) and its R x R algebra (Grams, Cholesky factors, triangular solves,
+ *   CholeskyQR) as blocked FP64 GEMM algorithms; such a context runs every mode
+ *   loop host-driven (use_graph is ignored: the host reads the stop flag after
+ *   each sweep's test), and tals_hooi / tals_singular_vectors refuse it
+ *   (TALS_ENOTSUP). A mode view whose I_n fits the fused sweep pass's
  *   shared-memory tile (up to 1920 in FP32 and 852 in FP64 at the smallest tile
  *   shapes, less for some ranks) reads the tensor once per sweep; a longer mode
  *   runs the same sweep as two tiled products (W = B^T Q, then Y = B W), reading

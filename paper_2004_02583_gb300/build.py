@@ -57,7 +57,8 @@ def build(verbose: bool = False, extra=()) -> str:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
     if True:   # always relink: a library copied from another machine may be foreign
         tmp = LIB + ".tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-lcublas", "-Xlinker", "-rpath", "-Xlinker",
+               os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -63,6 +63,21 @@ namespace {
 struct Need {
   size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0, qs = 0;
   void add_mode(int dtype, const ModeView& v, int R, int sms, bool sweep) {
+    if (bigr_rank(R)) {
+      // large ranks (bigr.cu): Y and its column-range partials in Ypart, W in a
+      // scratch tensor buffer, ||.||^2 partials over the fixed grid; no Gram
+      // partials (the R x R products are GEMMs)
+      ir = std::max(ir, (size_t)v.I * (size_t)R);
+      spart = std::max(spart, (size_t)kSumsqParts);
+      if (sweep) {
+        ypart = std::max(ypart, (size_t)(twopass_splits(v, R, sms) + 1) * (size_t)v.I * (size_t)R);
+        tbuf = std::max(tbuf, (size_t)(v.J() * R));
+      } else {
+        PassConfig pc = pass_config(dtype, v, R, sms);
+        if (pc.ok) spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
+      }
+      return;
+    }
     PassConfig pc = pass_config(dtype, v, R, sms);
     RowPlan rp = row_plan(v.I, R, sms);
     gpart = std::max(gpart, (size_t)rp.blocks * (size_t)R * (size_t)R);
@@ -184,6 +199,7 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
   if ((e = cudaMemsetAsync(c->Lt, 0, need.ir * esz, s)) != cudaSuccess)
     return cuda_fail(e, "workspace clear");
   TALS_AL(c->st, (size_t)TALS_MAX_NDIM * sizeof(ModeState));
+  if (bigr_ws_doubles(rmax) > 0) TALS_AL(c->bw, bigr_ws_doubles(rmax) * sizeof(double));
   TALS_AL(c->norm_a2, 8 * sizeof(double));
   if (need.qs > 0) {
     TALS_AL(c->QS, need.qs * sizeof(float));
@@ -221,9 +237,22 @@ constexpr int kProdAutoMaxRank = 32;
 constexpr long long kProdAutoMinElems = 64LL << 20;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
+  j.st = c->st + j.n;
+  if (bigr_rank(j.R)) {
+    // large rank: GEMM products, W in the destination or a scratch tensor buffer
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    const size_t ir = (size_t)j.v.I * j.R;
+    j.splits = twopass_splits(j.v, j.R, c->sms);
+    if (w == j.X || (size_t)(j.splits + 1) * ir > c->ypart_elems || ir > c->need_ir || c->blas == nullptr ||
+        c->spart_n < (size_t)kSumsqParts || (j.Wdest == nullptr && (size_t)(j.v.J() * j.R) > c->tbuf_elems))
+      return fail(TALS_ENOTSUP, "mode %d (I=%lld, R=%d) exceeds the context's workspace", j.n, j.v.I, j.R);
+    j.bigr = 1;
+    j.Wt = w;
+    return TALS_OK;
+  }
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
   j.rp = row_plan(j.v.I, j.R, c->sms);
-  j.st = c->st + j.n;
   // FP32: on tensors up to a quarter of the input (and at least 16M elements) the
   // sweeps measure e_k from the residual ||B - Q W^T||^2 directly; ||B||^2 - ||W||^2
   // cancels too many FP32 digits there (small e on small tensors). Costs one more
@@ -337,6 +366,7 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x);
   TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
                             j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32, j.split_ok, j.prod));
+  if (j.bigr) return bigr_init_launch(c, j, set_norm_a);
   if (j.twopass) return twopass_init_launch(c, j, set_norm_a);
   if (j.t32) {
     // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
@@ -380,6 +410,7 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   const int R = j.R;
   const long long I = j.v.I;
   cudaError_t e;
+  if (j.bigr) return bigr_sweep_launch(c, j);
   if (j.twopass) return twopass_sweep_launch(c, j);
   if (j.t32) {
     // split-precision passes: W = B^T Q_k (written), then Y = B W with the residual
@@ -577,9 +608,8 @@ static tals_status validate(int dtype, int ndim, const int64_t* dims, const int*
     if (ranks[n] > other)
       return fail(TALS_EINVAL, "ranks[%d] = %d exceeds the product of the other ranks (%lld)", n,
                   ranks[n], other);
-    if (ranks[n] > 64)
-      return fail(TALS_ENOTSUP, "ranks[%d] = %d: the R x R factorizations run in one CTA, R <= 64", n,
-                  ranks[n]);
+    if (ranks[n] > kBigRankMax)
+      return fail(TALS_ENOTSUP, "ranks[%d] = %d above the largest supported rank %d", n, ranks[n], kBigRankMax);
   }
   return TALS_OK;
 }
@@ -631,7 +661,11 @@ static tals_status ctx_create(tals_ctx** out, const void* A, bool owned, int dty
     delete c;
     return fail(TALS_ECUDA, "no CUDA device available");
   }
+  for (int n = 0; n < ndim; ++n) c->has_bigr = c->has_bigr || bigr_rank(ranks[n]);
+  // a rank above 64: those modes read their stop flag on the host every sweep
+  if (c->has_bigr) c->opts.use_graph = 0;
   st = ctx_plan_and_alloc(c);
+  if (st == TALS_OK && c->has_bigr) st = bigr_open(c);
   if (st == TALS_OK && owned) {
     size_t n = 1;
     for (int m = 0; m < ndim; ++m) n *= (size_t)dims[m];
@@ -669,9 +703,10 @@ void tals_destroy(tals_ctx* c) {
   graphs_destroy(c);
   mixed_free(c);
   if (c->upload) cudaStreamSynchronize(c->upload);
+  bigr_close(c);
   void* bufs[] = {c->GpartL, c->GfinL, c->tbuf[0], c->tbuf[1], c->Ypart, c->spart, c->Gpart, c->Gfin, c->F,
                   c->Y64,     c->L64,     c->Z64,   c->Lt,    c->st,    c->norm_a2, c->A_owned,
-                  c->A_owned2, c->hostio_G, c->pipe_G[0], c->pipe_G[1]};
+                  c->A_owned2, c->hostio_G, c->pipe_G[0], c->pipe_G[1], c->bw};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, s);
   for (int m = 0; m < TALS_MAX_NDIM; ++m)
@@ -981,8 +1016,12 @@ tals_status als_mode_finish(tals_ctx* c, int mode, void* U_out, int truncate) {
     // W of the last sweep is B x_n Q^T only when that sweep ended the mode; a
     // mode interrupted by the caller is truncated with its latest iterate
     if (!ms.done) {
-      cudaError_t e = launch_pass(c->dtype, ds.job.pc, PASS_PROJECT, ds.job.X, ds.job.v, ds.job.R,
-                                  c->Lt, nullptr, c->spart, ds.job.Wdest, 0, nullptr, 0, c->stream);
+      // the fused pass in projection mode, or the tiled mode product for the
+      // modes beyond it (long modes, large ranks)
+      cudaError_t e = ds.job.pc.ok ? launch_pass(c->dtype, ds.job.pc, PASS_PROJECT, ds.job.X, ds.job.v, ds.job.R,
+                                                 c->Lt, nullptr, c->spart, ds.job.Wdest, 0, nullptr, 0, c->stream)
+                                   : launch_mode_project_any(c->dtype, ds.job.X, ds.job.v, c->Lt, ds.job.R,
+                                                             ds.job.Wdest, c->stream);
       if (e != cudaSuccess) return cuda_fail(e, "projection pass");
     }
     c->cur = ds.job.Wdest;

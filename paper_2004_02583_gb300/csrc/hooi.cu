@@ -505,6 +505,7 @@ tals_status tals_hooi(tals_ctx* c, void* const* U_io, void* G_out, double tol, i
   if (max_iters < 1) return fail(TALS_EINVAL, "max_iters must be >= 1");
   if (inner_sweeps < 1) return fail(TALS_EINVAL, "inner_sweeps must be >= 1");
   if (!(tol >= 0.0)) return fail(TALS_EINVAL, "tol must be >= 0");
+  if (c->has_bigr) return fail(TALS_ENOTSUP, "HOOI takes ranks up to %d", kBigRankMin);
   return hooi_run(c, U_io, G_out, tol, max_iters, inner_eta, inner_sweeps, resid_out, stats);
 }
 
@@ -513,6 +514,7 @@ tals_status tals_singular_vectors(tals_ctx* c, int mode, const void* Qhat, void*
   if (!c || !Qhat || !U_out) return fail(TALS_EINVAL, "ctx, Qhat and U_out must not be NULL");
   if (mode < 0 || mode >= c->N) return fail(TALS_EINVAL, "mode %d outside [0, %d)", mode, c->N);
   if (U_out == Qhat) return fail(TALS_EINVAL, "U_out must not alias Qhat");
+  if (c->ranks[mode] > kBigRankMin) return fail(TALS_ENOTSUP, "singular vectors take ranks up to %d", kBigRankMin);
   return singular_vectors_run(c, mode, Qhat, U_out, sigma_out);
 }
 

@@ -34,6 +34,7 @@ struct ModeJob {
   size_t wpo = 0;                // offset of those statistics' partials in spart
   int prod = 0;                  // FP32 sweeps as two products (mode product W, split-K Y)
   int ys = 0;                    // column splits of that Y product
+  int bigr = 0;                  // R above kBigRankMin: bigr.cu (GEMM products, blocked FP64 algebra)
 };
 
 struct DriveState {
@@ -78,6 +79,16 @@ tals_status twopass_sweep_launch(tals_ctx* c, const ModeJob& j);
 // out = X x_n U^T (fused pass in projection mode, else the tiled mode product);
 // *nsp partial sums of ||out||^2 left in c->spart.
 tals_status project_mode(tals_ctx* c, const void* X, const ModeView& v, int R, const void* U, void* out, int* nsp);
+// bigr.cu: modes of rank above kBigRankMin (largest rank kBigRankMax). Their loop
+// is host-driven: a sweep reads the stop flag before its L-update.
+constexpr int kBigRankMin = 64;
+constexpr int kBigRankMax = 1024;
+bool bigr_rank(int R);
+size_t bigr_ws_doubles(int rmax);
+tals_status bigr_open(tals_ctx* c);
+void bigr_close(tals_ctx* c);
+tals_status bigr_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
+tals_status bigr_sweep_launch(tals_ctx* c, const ModeJob& j);
 
 // hooi.cu: HOOI refinement (Sec. 6.3) and singular vectors (Sec. 5)
 struct ViewR {
@@ -174,4 +185,7 @@ struct tals_ctx {
   tals::MixedState* mixed = nullptr;
   float* QS = nullptr;        // split basis of the split-precision W pass
   int* t32_err = nullptr;     // error flag of the split-precision passes
+  void* blas = nullptr;       // cuBLAS handle of the large-rank modes (bigr.cu)
+  double* bw = nullptr;       // their R x R scratch (bigr_ws_doubles)
+  bool has_bigr = false;      // some rank above kBigRankMin: host-driven mode loops
 };

@@ -79,5 +79,5 @@ def test_host_validation_without_a_gpu(lib):
     assert init(pkg.TALS_F32, (10, 9, 8), (5, 2, 2)) == pkg.TALS_EINVAL      # R_0 > R_1 R_2
     assert init(pkg.TALS_F32, (10,), (2,)) == pkg.TALS_EINVAL                # ndim < 2
     assert init(7, (10, 9, 8), (2, 2, 2)) == pkg.TALS_EINVAL                 # dtype
-    assert init(pkg.TALS_F32, (100, 90, 80), (65, 65, 65)) == pkg.TALS_ENOTSUP   # R > 64
-    assert b"R <= 64" in lib.tals_last_error()
+    assert init(pkg.TALS_F32, (1100, 40, 40), (1030, 40, 40)) == pkg.TALS_ENOTSUP   # R > 1024
+    assert b"largest supported rank 1024" in lib.tals_last_error()

@@ -1,0 +1,158 @@
+"""GPU parity of the large-rank modes (R_n > 64: GEMM products, blocked FP64
+Cholesky / triangular solves / CholeskyQR) against the FP64 oracle on the same
+seeded inputs, at the tolerances of the small-rank parity tests: FP64 -- errors
+within 1e-10, factors within 1e-8; FP32 -- relative error of (G, U) within 1e-6
+of the oracle's, the GPU's estimate within 1e-5, e_n^2 within 2e-7 ||A||^2,
+angles below 1e-4, and at fixed sweep counts factors within 1e-3 and the core
+within 1e-3 max|G|.
+
+The shapes cover each product form of the path -- P = 1 views (one GEMM per
+product), Q = 1 views (the last mode: GEMMs on the transposed unfolding) and
+general views (the tiled mode product and factor adjoint) -- and Cholesky factors
+of two and three 64-column blocks with a ragged last block (R = 72, 80, 130), a
+full-rank mode (R = I), the singular case of Remark 3 and the refusals.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import tucker_oracle as O
+
+
+@pytest.fixture(scope="module")
+def tals():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2004_02583_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _cmp(res_gpu, ref, a64, dtype, fixed=True):
+    G, Us, st = res_gpu
+    f64 = dtype == np.float64
+    rel_ref = O.rel_error(a64, ref.G, ref.U)
+    rel_own = O.rel_error(a64, G.double().cpu().numpy(), [u.double().cpu().numpy() for u in Us])
+    assert abs(rel_own - rel_ref) <= (1e-10 if f64 else 1e-6), (rel_own, rel_ref)
+    assert abs(st["rel_err"] - rel_ref) <= (1e-10 if f64 else 1e-5), (st["rel_err"], rel_ref)
+    norm_a2 = O.frob2(a64)
+    for n in range(a64.ndim):
+        u = Us[n].double().cpu().numpy()
+        assert O.principal_angles(u, ref.U[n]).max() <= (1e-8 if f64 else 1e-4), n
+        assert abs(st["err_per_mode"][n] ** 2 - ref.err_per_mode[n] ** 2) <= (1e-12 if f64 else 2e-7) * norm_a2, n
+        if fixed:
+            assert st["sweeps"][n] == ref.sweeps[n]
+            assert np.abs(u - ref.U[n]).max() <= (1e-8 if f64 else 1e-3), n
+    if fixed:
+        g = G.double().cpu().numpy()
+        assert np.abs(g - ref.G).max() <= (1e-8 if f64 else 1e-3) * np.abs(ref.G).max()
+
+
+# (dims, ranks): st order ascending R, so the large-rank modes come last
+CASES = [
+    ((320, 288, 10), (80, 72, 8)),    # mode 1 general view (P 320, Q 8), mode 0 P = 1; 2 blocks each
+    ((40, 30, 300), (8, 10, 70)),     # mode 2 (R 70) on the Q = 1 view
+    ((400, 150, 9), (130, 20, 9)),    # R = 130: three Cholesky blocks (64, 64, 2)
+    ((70, 96, 12), (70, 66, 12)),     # R = I = 70 (square factor), R = 66 on a general view
+]
+
+
+@pytest.mark.parametrize("dims,ranks", CASES)
+@pytest.mark.parametrize("driver", ["st", "t"])
+def test_big_rank_fixed_sweeps_f32(tals, dims, ranks, driver):
+    p = W.planted(W.SEED_BASE + 61, dims, ranks, "gauss", 1e-2, dtype=np.float32)
+    a64 = p.A.astype(np.float64)
+    f = O.st_hosvd_als if driver == "st" else O.t_hosvd_als
+    ref = f(a64, ranks, eta=-1.0, seed=5, max_sweeps=3)
+    g = tals.st_hosvd if driver == "st" else tals.t_hosvd
+    res = g(_gpu(p.A), ranks, eta=-1.0, seed=5, max_sweeps=3)
+    _cmp(res, ref, a64, np.float32, fixed=True)
+
+
+@pytest.mark.parametrize("dims,ranks", CASES[:3])
+@pytest.mark.parametrize("driver", ["st", "t"])
+def test_big_rank_fixed_sweeps_f64(tals, dims, ranks, driver):
+    p = W.planted(W.SEED_BASE + 62, dims, ranks, "gauss", 1e-2, dtype=np.float64)
+    f = O.st_hosvd_als if driver == "st" else O.t_hosvd_als
+    ref = f(p.A, ranks, eta=-1.0, seed=9, max_sweeps=4)
+    g = tals.st_hosvd if driver == "st" else tals.t_hosvd
+    res = g(_gpu(p.A), ranks, eta=-1.0, seed=9, max_sweeps=4)
+    _cmp(res, ref, p.A, np.float64, fixed=True)
+
+
+@pytest.mark.parametrize("precision", ["native", "mixed_bf16"])
+def test_big_rank_tolerance_run(tals, precision):
+    """eta = 1e-6, the stop rule read by the host after each sweep's test; the
+    graph request is ignored for such a context (same results either way); in
+    mixed precision the small-rank mode runs its BF16 bulk sweeps, the large-rank
+    modes exact FP32."""
+    dims, ranks = CASES[0]
+    p = W.planted(W.SEED_BASE + 63, dims, ranks, "gauss", 1e-2, dtype=np.float32)
+    a64 = p.A.astype(np.float64)
+    ref = O.st_hosvd_als(a64, ranks, eta=1e-6, seed=1)
+    for use_graph in (True, False):
+        G, Us, st = tals.st_hosvd(_gpu(p.A), ranks, eta=1e-6, seed=1, use_graph=use_graph, precision=precision)
+        for n in range(3):
+            assert abs(st["sweeps"][n] - ref.sweeps[n]) <= 1, (n, st["sweeps"], ref.sweeps)
+        _cmp((G, Us, st), ref, a64, np.float32, fixed=False)
+
+
+def test_big_rank_user_driven_sweeps(tals):
+    """als_mode_sweep / als_mode_finish on a large-rank mode: after the stop rule
+    the mode's error is that of the returned pair."""
+    dims, ranks = CASES[0]
+    p = W.planted(W.SEED_BASE + 64, dims, ranks, "gauss", 1e-2, dtype=np.float64)
+    ctx = tals.Context(_gpu(p.A), ranks, eta=1e-9, seed=2)
+    try:
+        e0, conv = ctx.mode_sweep(0, 50)
+        U0 = ctx.mode_finish(0, truncate=True).double().cpu().numpy()
+    finally:
+        ctx.close()
+    assert conv
+    m = O.unfold(p.A, 0)
+    resid = m - U0 @ (U0.T @ m)
+    assert abs(e0 ** 2 - O.frob2(resid)) <= 1e-10 * O.frob2(p.A)
+    assert np.abs(U0.T @ U0 - np.eye(ranks[0])).max() <= 1e-12
+
+
+def test_big_rank_singular(tals):
+    """Remark 3: a Gram that is not numerically positive definite (a zero tensor;
+    a NaN entry) gives TALS_ESINGULAR from the large-rank mode's Cholesky."""
+    z = torch.zeros((100, 90, 8), device="cuda")
+    with pytest.raises(tals.TalsError) as ex:
+        tals.st_hosvd(z, (70, 10, 8), order=[0, 1, 2])
+    assert ex.value.status == tals.TALS_ESINGULAR
+    b = torch.randn((100, 90, 8), device="cuda")
+    b[3, 4, 5] = float("nan")
+    with pytest.raises(tals.TalsError) as ex:
+        tals.st_hosvd(b, (70, 10, 8), order=[0, 1, 2])
+    assert ex.value.status == tals.TALS_ESINGULAR
+
+
+def test_big_rank_refusals(tals):
+    """HOOI and the singular-vector recovery take ranks up to 64; ranks above 1024
+    are refused at context creation."""
+    p = W.planted(W.SEED_BASE + 66, (100, 90, 8), (70, 10, 8), "gauss", 1e-2, dtype=np.float32)
+    A = _gpu(p.A)
+    ctx = tals.Context(A, (70, 10, 8), eta=1e-6, seed=1)
+    try:
+        G, Us, st = ctx.st_hosvd()
+        with pytest.raises(tals.TalsError) as ex:
+            ctx.hooi(Us)
+        assert ex.value.status == 6
+        with pytest.raises(tals.TalsError) as ex:
+            ctx.singular_vectors(0, Us[0])
+        assert ex.value.status == 6
+    finally:
+        ctx.close()
+    big = torch.zeros((1100, 40, 40), device="cuda")
+    with pytest.raises(tals.TalsError) as ex:
+        tals.st_hosvd(big, (1030, 40, 40))
+    assert ex.value.status == 6
