@@ -218,16 +218,17 @@ def main():
                          "(one decomposition: its split sweep's W product and W statistics)")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="c4: number of tensors (4096 is the workload; fewer for profiling)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "tucker"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "tucker", "rank500"],
                     help="c2 (default): 512^3 FP32 st-HOSVD, the benchmark line; c1: 64^3 FP64; "
                          "c3: 128^4 FP32 mixed vs plain; c4: 4096 small tensors batched vs "
-                         "per-tensor loop; c5: 1024x1024x512 forward + reconstruction-loss backward")
+                         "per-tensor loop; c5: 1024x1024x512 forward + reconstruction-loss backward; "
+                         "tucker: the Sec. 6.1.2 Tucker model; rank500: the Sec. 6.4 dense test")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "c2":
         from_extra = {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5,
-                      "tucker": run_tucker}[args.workload]
+                      "tucker": run_tucker, "rank500": run_rank500}[args.workload]
         return from_extra(args)
     global DIMS
     if args.dims:
@@ -729,6 +730,103 @@ def run_tucker(args):
                              "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                              "sample": f"FP64 NumPy oracle st-HOSVD-ALS on the {sizes[0]}x100x100x100 "
                                        f"tensor ({n} runs)"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_rank500(args):
+    """Sec. 6.4's dense test: a 5000 x 5000 x 50 FP32 Tucker tensor of multilinear
+    rank (500, 500, 5) (the device-built Tucker model, noise 1e-2 of the base in
+    norm), st-HOSVD-ALS (and one t-HOSVD-ALS run) at eta 1e-4 with the large-rank
+    path for the two rank-500 modes; properties of the result (orthonormal
+    factors, angles to the planted factors, error against the noiseless base).
+    --dims I,J,K runs the same recipe at ranks (I/10, J/10, 5)."""
+    import numpy as np
+    import torch
+    import paper_2004_02583_gb300 as tals
+    import workloads as W
+    from oracle import tucker_oracle as O
+    dims = tuple(int(x) for x in args.dims.split(",")) if args.dims else W.RANK500_DIMS
+    ranks = (dims[0] // 10, dims[1] // 10, 5) if args.dims else W.RANK500_RANKS
+    delta = W.tucker_delta(dims, ranks, W.RANK500_NOISE)
+    A, F = W.tucker_model_device(W.RANK500_SEED, dims, ranks, delta=delta, return_factors=True)
+    peaks, _ = _peaks()
+    clocks = Clocks(0)
+    G = torch.empty(ranks, device="cuda")
+    Us = [torch.empty((d, r), device="cuda") for d, r in zip(dims, ranks)]
+    ctx = tals.Context(A, ranks, eta=1e-4, seed=1)
+    clocks.start()
+    ms, (_, _, st) = _time_gpu(lambda: ctx.st_hosvd(G, Us), args.steps, args.warmup)
+    clk = clocks.stop()
+
+    def props(G, Us):
+        orth = max(float((u.double().T @ u.double() - torch.eye(u.shape[1], device="cuda",
+                                                                  dtype=torch.float64)).abs().max()) for u in Us)
+        sines = []
+        for u, f in zip(Us, F):
+            c = torch.linalg.svdvals((u.double().T @ f).cpu())
+            sines.append(float(torch.sqrt(torch.clamp(1.0 - c.min() ** 2, min=0.0))))
+        b = tals.reconstruct(G, Us)
+        base = W.tucker_model_device(W.RANK500_SEED, dims, ranks, delta=delta, base_only=True)
+        e_base = float(torch.linalg.vector_norm(b - base) / torch.linalg.vector_norm(base))
+        e_in = float(torch.linalg.vector_norm(b - A) / torch.linalg.vector_norm(A))
+        del b, base
+        return {"max_orthonormality_defect": orth, "sin_max_angle_to_planted": sines,
+                "rel_err_direct": e_in, "err_vs_noiseless": e_base}
+
+    st_props = props(G, Us)
+    # the rank-500 mode's products (mode 1 of the paper's numbering: the first
+    # large-rank mode st-HOSVD reaches, on the tensor after the rank-5 mode)
+    pm, pb, pf = ctx.time_sweep(mode=0, engine="cuda", iters=3)
+    ctx.close()
+    t_line = None
+    if not args.no_compare:
+        ctx = tals.Context(A, ranks, eta=1e-4, seed=1)
+        tms, (_, _, tst) = _time_gpu(lambda: ctx.t_hosvd(G, Us), 1, 1)
+        t_line = {"ms": round(tms, 3), "rel_err": tst["rel_err"], "sweeps": tst["sweeps"], **props(G, Us)}
+        ctx.close()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu, _ = _alu_peaks(152, sm_mhz)
+    # mode 0 of the full tensor: the SGEMM pair of one sweep (2 I J R flops each)
+    tf = [pf / 2.0 / (m * 1e-3) / 1e12 for m in pm]
+    roof = {"bound": "alu", "achieved": round(tf[1], 2), "peak": round(alu, 2), "unit": "TFLOP/s",
+            "frac": round(tf[1] / alu, 4), "traffic": None,
+            "kernel": "cuBLAS SGEMM (pedantic FP32) of Y = B_(1) W over 2048-column ranges, mode 1 of the "
+                      f"{'x'.join(map(str, dims))} tensor at rank {ranks[0]}",
+            "w_product_ms": round(pm[0], 4), "y_product_ms": round(pm[1], 4),
+            "w_product_tflops": round(tf[0], 2),
+            "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 flops x median SM clock {sm_mhz} MHz (derived)"}
+    # the oracle as it stands, on the same recipe at 1/5 of each large mode
+    sdims, sranks = (dims[0] // 5, dims[1] // 5, dims[2]), (ranks[0] // 5, ranks[1] // 5, ranks[2])
+    a_small = W.tucker_model_device(W.RANK500_SEED, sdims, sranks,
+                                    delta=W.tucker_delta(sdims, sranks, W.RANK500_NOISE)).cpu().numpy()
+    sec, n = _oracle_time(lambda: O.st_hosvd_als(a_small.astype(np.float64), sranks, eta=1e-4, seed=1))
+
+    def work(d, r):
+        # sum over the st-HOSVD modes (ascending rank) of I_n J_n R_n of the current tensor
+        d = list(d)
+        tot = 0.0
+        for m in sorted(range(3), key=lambda m: (r[m], m)):
+            tot += float(np.prod(d)) * r[m]
+            d[m] = r[m]
+        return tot
+
+    scale = work(dims, ranks) / work(sdims, sranks)
+    line = {"metric": "Sec. 6.4 dense test st-HOSVD-ALS time-to-tol (ranks (500, 500, 5))",
+            "value": round(1e3 / ms, 4), "unit": "st-HOSVD/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Tucker tensor {'x'.join(map(str, dims))} FP32, multilinear rank "
+                                   f"{ranks}, core U[5,10], noise 1e-2 of the base, eta 1e-4",
+                       "rel_err": st["rel_err"], "sweeps": st["sweeps"], "order": st["order"],
+                       **st_props, "t_hosvd": t_line,
+                       "l2": f"input ({A.numel() * 4 / 2**30:.1f} GiB) larger than L2"},
+            "roofline": roof, "clocks": _clock_line(clk),
+            "cpu_baseline": {"value": round(1.0 / (sec * scale), 6), "unit": "st-HOSVD/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"FP64 NumPy oracle st-HOSVD-ALS on the same recipe at "
+                                       f"{'x'.join(map(str, sdims))}, ranks {sranks} ({n} runs of "
+                                       f"{sec:.2f} s), scaled by {scale:.1f}, the ratio of the ALS "
+                                       f"product work sum_n I_n J_n R_n"}}
     print(json.dumps(line), flush=True)
 
 

@@ -1061,6 +1061,7 @@ tals_status tals_time_sweep(tals_ctx* c, int mode, int engine, int iters, double
   const double JR = (double)j.v.J() * j.R;
   ms_out[0] = ms_out[1] = bytes_out[0] = bytes_out[1] = 0.0;
   if (flops) *flops = 4.0 * j.R * T;
+  if (j.bigr) return bigr_time_products(c, j, iters, ms_out, bytes_out);
   if (engine == 1) {
     if (!(c->mixed && c->dtype == TALS_F32 && tc_supported(j.v, j.R)))
       return fail(TALS_ENOTSUP, "the BF16 tensor-core pass needs a mixed-precision context and its shapes");

@@ -152,15 +152,27 @@ __global__ void sum_to_f64_kernel(const T* __restrict__ part, int S, long long n
   }
 }
 
-// The stored basis: Lt = L64 rounded to the tensor's type, Lr = Lt in FP64 (the
-// basis the next products actually use, for its Gram).
+// The stored basis: Lt = L64 rounded to the tensor's type and, for FP32, its
+// rounding error D = Lt - L64 (exact in FP32 to its own rounding: |D| is near
+// 2^-24 |L64|).
 template <typename T>
 __global__ void store_basis_kernel(const double* __restrict__ L64, long long n, T* __restrict__ Lt,
-                                   double* __restrict__ Lr) {
+                                   float* __restrict__ D) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const T q = (T)L64[e];
     Lt[e] = q;
-    Lr[e] = (double)q;
+    if (D != nullptr) D[e] = (float)((double)q - L64[e]);
+  }
+}
+
+// GL = I + H + H^T (H = D^T Lt, R x R FP32; null: GL = I).
+__global__ void basis_gram_kernel(const float* __restrict__ H, int R, double* __restrict__ GL) {
+  const long long n = (long long)R * R;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / R), j = (int)(e % R);
+    double g = i == j ? 1.0 : 0.0;
+    if (H != nullptr) g += (double)H[e] + (double)H[(long long)j * R + i];
+    GL[e] = g;
   }
 }
 
@@ -357,17 +369,32 @@ tals_status big_cholqr(tals_ctx* c, const ModeJob& j, double* M, double* out, in
   return big_solve_fwd(c, j, M, out);
 }
 
-// L64 holds the new basis: store its rounding Lt and the Gram of the stored basis
-// (GfinL, the rounded-basis term of the next test).
+// L64 holds the new basis (orthonormal to FP64 rounding): store its rounding Lt
+// and the Gram GL = Lt^T Lt of the stored basis (GfinL, the rounded-basis term of
+// the next test). With Lt = L64 + D, GL = I + D^T L64 + L64^T D + D^T D +
+// (L64^T L64 - I); the last two terms are at FP64 rounding level, and D^T L64 =
+// D^T Lt - D^T D, so GL = I + H + H^T with H = D^T Lt to that level: one FP32 GEMM
+// (D is ~2^-24 |L|, so H's FP32 rounding is far below the term itself) instead of
+// an FP64 Gram. FP64 tensors: Lt = L64, GL = I.
 tals_status big_store_basis(tals_ctx* c, const ModeJob& j) {
-  const long long n = j.v.I * j.R;
+  const int R = j.R;
+  const long long n = j.v.I * R;
   cudaError_t e;
-  if (c->dtype == TALS_F32)
-    store_basis_kernel<float><<<grid_of(n, c->sms), 256, 0, c->stream>>>(c->L64, n, (float*)c->Lt, c->Z64);
-  else
-    store_basis_kernel<double><<<grid_of(n, c->sms), 256, 0, c->stream>>>(c->L64, n, (double*)c->Lt, c->Z64);
+  float* H = reinterpret_cast<float*>(c->F);   // R x R FP32 (F holds 3 R^2 + R doubles)
+  if (c->dtype == TALS_F32) {
+    float* D = reinterpret_cast<float*>(c->Z64);
+    store_basis_kernel<float><<<grid_of(n, c->sms), 256, 0, c->stream>>>(c->L64, n, (float*)c->Lt, D);
+    TALS_CK(cudaGetLastError());
+    TALS_BL(gemm_rm((cublasHandle_t)c->blas, true, false, R, R, j.v.I, 1.f, D, R, (const float*)c->Lt, R, 0.f, H,
+                    R));
+  } else {
+    store_basis_kernel<double><<<grid_of(n, c->sms), 256, 0, c->stream>>>(c->L64, n, (double*)c->Lt, nullptr);
+    TALS_CK(cudaGetLastError());
+    H = nullptr;
+  }
+  basis_gram_kernel<<<grid_of((long long)R * R, c->sms), 256, 0, c->stream>>>(H, R, c->GfinL);
   TALS_CK(cudaGetLastError());
-  return big_gram(c, j, c->Z64, c->GfinL);
+  return TALS_OK;
 }
 
 // Y64 = B_(n) V for V in the P x R x Q layout (the sketch or W), the column
@@ -493,6 +520,42 @@ tals_status bigr_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
 
 tals_status bigr_sweep_launch(tals_ctx* c, const ModeJob& j) {
   return c->dtype == TALS_F32 ? big_sweep_t<float>(c, j) : big_sweep_t<double>(c, j);
+}
+
+tals_status bigr_time_products(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes) {
+  cudaStream_t s = c->stream;
+  cudaEvent_t ev[3];
+  for (auto& x : ev) cudaEventCreate(&x);
+  double acc[2] = {0.0, 0.0};
+  tals_status st = TALS_OK;
+  cudaError_t e = cudaSuccess;
+  for (int it = -1; it < iters && st == TALS_OK && e == cudaSuccess; ++it) {   // it = -1: warm-up
+    cudaEventRecord(ev[0], s);
+    st = c->dtype == TALS_F32 ? big_project<float>(c, j, (const float*)j.X, (const float*)c->Lt, (float*)j.Wt)
+                              : big_project<double>(c, j, (const double*)j.X, (const double*)c->Lt, (double*)j.Wt);
+    cudaEventRecord(ev[1], s);
+    if (st == TALS_OK)
+      st = c->dtype == TALS_F32 ? big_adjoint<float>(c, j, (const float*)j.X, (const float*)j.Wt)
+                                : big_adjoint<double>(c, j, (const double*)j.X, (const double*)j.Wt);
+    cudaEventRecord(ev[2], s);
+    e = cudaEventSynchronize(ev[2]);
+    float t0 = 0.f, t1 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    if (it >= 0) {
+      acc[0] += t0;
+      acc[1] += t1;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (st != TALS_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "timed products");
+  const double T = (double)j.v.P * j.v.I * j.v.Q, JR = (double)j.v.J() * j.R;
+  ms[0] = acc[0] / iters;
+  ms[1] = acc[1] / iters;
+  bytes[0] = (T + JR) * c->esz;   // tensor read + W written
+  bytes[1] = (T + JR) * c->esz;   // tensor read + W read
+  return TALS_OK;
 }
 
 tals_status bigr_open(tals_ctx* c) {

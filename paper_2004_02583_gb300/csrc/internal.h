@@ -89,6 +89,9 @@ tals_status bigr_open(tals_ctx* c);
 void bigr_close(tals_ctx* c);
 tals_status bigr_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
 tals_status bigr_sweep_launch(tals_ctx* c, const ModeJob& j);
+// Mean durations (ms) and algorithmic bytes of a large-rank mode's two products
+// (W = B^T Q, then Y = B W with its FP64 range sums), timed on the current basis.
+tals_status bigr_time_products(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes);
 
 // hooi.cu: HOOI refinement (Sec. 6.3) and singular vectors (Sec. 5)
 struct ViewR {

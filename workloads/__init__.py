@@ -164,14 +164,16 @@ def cp_model(seed: int, I: int, R: int = None, delta: float = 1e-4, dtype=np.flo
 
 
 def tucker_model_device(seed: int, dims: Sequence[int], ranks: Sequence[int], delta: float = 1e-4,
-                        device="cuda", base_only: bool = False):
+                        device="cuda", base_only: bool = False, return_factors: bool = False):
     """Sec. 6.1.2's Tucker model at sizes too large to draw on the host, built on a
-    torch device (FP32 result): Haar factors (QR of Gaussian, sign-fixed), core
+    torch device (FP32 result): Haar factors (QR of Gaussian, sign-fixed; the QR on
+    the host), core
     i.i.d. U[5, 10], A0 = core x_1 U_1 ... x_N U_N, and A = A0 + delta E with E
     i.i.d. N(0, 1) (absolute noise, as the paper's Sec. 6.1). The expansions run
     in FP64 except the last (the first mode, the largest), which writes FP32; the
     noise is added in row blocks. Seeded through torch's generator on the device:
-    the same seed gives the same tensor on one torch version. base_only: A0."""
+    the same seed gives the same tensor on one torch version. base_only: A0.
+    return_factors: (A, [U_n]) with the planted FP64 factors."""
     import torch
     dims = [int(d) for d in dims]
     ranks = [int(r) for r in ranks]
@@ -179,11 +181,12 @@ def tucker_model_device(seed: int, dims: Sequence[int], ranks: Sequence[int], de
     g.manual_seed(int(seed))
     factors = []
     for d, r in zip(dims, ranks):
-        x = torch.randn((d, r), generator=g, device=device, dtype=torch.float64)
+        # the Gaussian draw on the device, its QR on the host (FP64)
+        x = torch.randn((d, r), generator=g, device=device, dtype=torch.float64).cpu()
         q, rr = torch.linalg.qr(x)
         sg = torch.sign(torch.diagonal(rr))
         sg[sg == 0] = 1.0
-        factors.append(q * sg)
+        factors.append((q * sg).to(device))
     core = torch.rand(tuple(ranks), generator=g, device=device, dtype=torch.float64) * 5.0 + 5.0
     a = core
     for n in range(len(dims) - 1, 0, -1):
@@ -197,7 +200,15 @@ def tucker_model_device(seed: int, dims: Sequence[int], ranks: Sequence[int], de
         for i0 in range(0, dims[0], step):
             blk = flat[i0:i0 + step]
             blk.add_(torch.randn(blk.shape, generator=g, device=device, dtype=torch.float32), alpha=delta)
-    return out
+    return (out, factors) if return_factors else out
+
+
+def tucker_delta(dims: Sequence[int], ranks: Sequence[int], rel: float) -> float:
+    """The absolute noise level delta of tucker_model_device that makes the noise
+    about `rel` of the base tensor in norm: ||A0||^2 = ||core||^2 (orthonormal
+    factors), E c^2 = 175/3 for c ~ U[5, 10], E ||E||^2 = prod(dims)."""
+    return float(rel * np.sqrt(np.prod([float(r) for r in ranks]) * (175.0 / 3.0) /
+                               np.prod([float(d) for d in dims])))
 
 
 def uniform_tensor(seed: int, dims: Sequence[int], dtype=np.float32) -> np.ndarray:
@@ -247,6 +258,14 @@ CONFIGS = {
 # truncation (I / 100, 10, 10, 10), core U[5, 10], delta = 1e-4
 TUCKER_SIZES = (1000, 2000, 3000, 4000, 5000)
 TUCKER_SEED = SEED_BASE + 7
+# Sec. 6.4's dense test: a 5000 x 5000 x 50 Tucker tensor of multilinear rank
+# (500, 500, 5) (the paper draws it with the Tensor Toolbox's ttensor), here the
+# device-built Tucker model with noise 1e-2 of the base tensor in norm (so that
+# e_k, and with it the stop rule, is well above FP32 rounding)
+RANK500_DIMS = (5000, 5000, 50)
+RANK500_RANKS = (500, 500, 5)
+RANK500_SEED = SEED_BASE + 8
+RANK500_NOISE = 1e-2
 
 # Sec. 6.1.1's CP-model sizes: I = 20 .. 100 (step 20), shape I x I x 100 I,
 # truncation (0.2 I, 0.2 I, 0.2 I), delta = 1e-4; the largest is 100 x 100 x 10000
