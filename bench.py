@@ -36,8 +36,9 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # where no capture of the current kernel exists.
 PASS_TRAFFIC = 2 * (268599552 + 14900480)   # CUDA-core FP32 fused pass
 TC_TRAFFIC = 2 * (134338048 + 3646208)      # BF16 tensor-core fused pass
-T32_TRAFFIC = {"w": 2 * (268653568 + 12280320),   # split-precision W and Y passes
-               "y": 2 * (285491968 + 3066368)}
+T32_TRAFFIC = {"w": None, "y": None}        # split-precision W and Y passes (changed since)
+PROD_TRAFFIC = {"w": 2 * (268647424 + 8675840),    # two-product form: register-tiled W product
+                "y": 2 * (285284096 + 6981632)}    # and the split-K Y = B W kernel
 DIMS = (512, 512, 512)
 RANKS = (32, 32, 32)
 ETA = 1e-6
@@ -347,6 +348,9 @@ def main():
     # the exact-FP32 CUDA-core fused pass and the BF16 tensor-core pass, same view
     pass_ms, pass_bytes, pass_flops = nctx.time_pass(mode=mode0, iters=5)
     tc_ms, tc_bytes, tc_flops = mctx.time_pass(mode=mode0, iters=10)
+    # the two-product form the FP32 sweeps of the first mode run on in both paths:
+    # the register-tiled W product and the split-K Y kernel, each timed alone
+    pr_ms, pr_bytes, pr_flops = nctx.time_sweep(mode=mode0, engine="products", iters=10)
     octx_close = octx.close
     cctx.close()
     # the metric's own mixed-vs-plain comparison at equal error on the 128^4 workload
@@ -449,8 +453,8 @@ def main():
     roofline_cuda = {
         "bound": "alu", "achieved": round(achieved_tflops, 2), "peak": round(alu_peak, 2),
         "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 4), "traffic": PASS_TRAFFIC,
-        "kernel": "tals::pass_kernel<float,32,4,16,256> (exact-FP32 CUDA-core fused sweep: the FP32 "
-                  "sweeps of both timed paths; the largest share of both steps)",
+        "kernel": "tals::pass_kernel<float,32,4,16,256> (exact-FP32 CUDA-core fused sweep: the later "
+                  "modes' sweeps, and every FP32 sweep with fp32_engine = cuda)",
         "view": "mode-1 view 1 x 512 x 262144, rank 32",
         "algorithmic_bytes": pass_bytes, "algorithmic_flops": pass_flops,
         "hbm_gbs_achieved": round(achieved_gbs, 1), "hbm_frac": round(achieved_gbs / hbm, 4),
@@ -458,6 +462,25 @@ def main():
         "peak_source": f"FP32 FMA peak from {sms} SMs x 128 lanes x 2 flops x median SM clock "
                        f"{sm_mhz} MHz (derived)",
     }
+    # the two-product form: each product 2 T R flops over T (+ W) elements
+    prod = {}
+    pnames = {"w": "tals::mg_pipe<0,0,0,32> (register-tiled mode product W = B x_1 Q^T of the "
+                   "two-product FP32 sweep)",
+              "y": "tals::adjoint_rows_kernel<32> (split-K Y = B_(1) W of the two-product FP32 sweep)"}
+    for k, i in (("w", 0), ("y", 1)):
+        tf = pr_flops / 2.0 / (pr_ms[i] * 1e-3) / 1e12
+        prod[k] = {"bound": "alu", "achieved": round(tf, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                   "frac": round(tf / alu_peak, 4), "traffic": PROD_TRAFFIC[k], "kernel": pnames[k],
+                   "algorithmic_flops": pr_flops / 2.0, "algorithmic_bytes": pr_bytes[i],
+                   "hbm_gbs_achieved": round(pr_bytes[i] / (pr_ms[i] * 1e-3) / 1e9, 1),
+                   "pass_ms": round(pr_ms[i], 4),
+                   "peak_source": f"FP32 FMA peak from {sms} SMs x 128 lanes x 2 flops x median SM clock "
+                                  f"{sm_mhz} MHz (derived)"}
+    roofline = dict(prod["w"])
+    roofline["kernel"] += ("; the largest share among the step's product kernels in both paths (the "
+                           "R x R small algebra, a chain of latency-bound one-CTA kernels, is 43% of "
+                           "the mixed launch list, small_kernel alone 20%)")
+    roofline["view"] = "mode-1 view 1 x 512 x 262144, rank 32"
     tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
     tc_tflops = tc_flops / (tc_ms * 1e-3) / 1e12
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -539,7 +562,9 @@ def main():
                    "l2": "inputs (512 MiB) larger than L2",
                    "driver": "host loop" if args.no_graph else "CUDA graph with device-side while",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roofline_cuda,
+        "roofline": roofline,
+        "roofline_adjoint": prod["y"],
+        "roofline_fused": roofline_cuda,
         "roofline_tc": roofline_tc,
         "roofline_tf32": roofline_tf32,
         "e2e": None if e_ms is None else
