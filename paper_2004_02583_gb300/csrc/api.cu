@@ -238,6 +238,14 @@ constexpr long long kProdAutoMinElems = 64LL << 20;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.st = c->st + j.n;
+  // FP32: on tensors up to a quarter of the input (and at least 16M elements) the
+  // sweeps measure e_k from the residual ||B - Q W^T||^2 directly; ||B||^2 - ||W||^2
+  // cancels too many FP32 digits there (small e on small tensors). Costs one more
+  // rank-R product per element on those small tensors only.
+  long long tot = 1;
+  for (int m = 0; m < c->N; ++m) tot *= c->dims[m];
+  const long long mine = j.v.P * j.v.I * j.v.Q;
+  const bool small_t = mine <= std::max(tot / 4, 16LL << 20);
   if (bigr_rank(j.R)) {
     // large rank: GEMM products, W in the destination or a scratch tensor buffer
     void* w = j.Wdest;
@@ -249,17 +257,11 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
       return fail(TALS_ENOTSUP, "mode %d (I=%lld, R=%d) exceeds the context's workspace", j.n, j.v.I, j.R);
     j.bigr = 1;
     j.Wt = w;
+    j.resid_kernel = c->dtype == TALS_F32 && small_t;
     return TALS_OK;
   }
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
   j.rp = row_plan(j.v.I, j.R, c->sms);
-  // FP32: on tensors up to a quarter of the input (and at least 16M elements) the
-  // sweeps measure e_k from the residual ||B - Q W^T||^2 directly; ||B||^2 - ||W||^2
-  // cancels too many FP32 digits there (small e on small tensors). Costs one more
-  // rank-R product per element on those small tensors only.
-  long long tot = 1;
-  for (int m = 0; m < c->N; ++m) tot *= c->dims[m];
-  const long long mine = j.v.P * j.v.I * j.v.Q;
   j.twopass = 0;
   if (!j.pc.ok) {
     // I_n beyond the fused pass: two tiled products per sweep, W in the destination
@@ -274,16 +276,14 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
     j.twopass = 1;
     j.t32 = 0;
     j.resid = 0;
-    j.resid_kernel = (c->dtype == TALS_F32) && mine <= std::max(tot / 4, 16LL << 20);
+    j.resid_kernel = (c->dtype == TALS_F32) && small_t;
     j.Wt = w;
     return TALS_OK;
   }
-  j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 &&
-            mine <= std::max(tot / 4, 16LL << 20);
+  j.resid = (c->dtype == TALS_F32) && j.pc.grid_y == 1 && small_t;
   // the same tensors with the rank split across CTAs cannot form the residual
   // inside the pass: the sweep writes W and a residual kernel takes it
-  j.resid_kernel = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr &&
-                   mine <= std::max(tot / 4, 16LL << 20);
+  j.resid_kernel = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr && small_t;
   // the full-size FP32 modes: products on the split-precision tensor-core passes,
   // W written every sweep (the Y pass reads it) to the destination or a scratch
   // buffer that no other part of the mode uses

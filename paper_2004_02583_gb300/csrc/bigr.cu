@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(kBlkThreads) bigr_norm_kernel(ModeState* st, c
 }
 
 // The Eq. 5.01 step: ||W||^2 from its partials, the rounded-basis term
-// tr((GL - I) X), e_k^2 = ||B||^2 - ||W||^2 + that term.
+// tr((GL - I) X), e_k^2 = ||B||^2 - ||W||^2 + that term; or, for a mode that
+// measures the residual (st->resid), e_k^2 = the sW the residual kernel wrote.
 __global__ void __launch_bounds__(kBlkThreads) bigr_test_kernel(ModeState* st, const double* __restrict__ spart,
                                                                 int nsp, const double* __restrict__ X,
                                                                 const double* __restrict__ GL, int R,
@@ -218,9 +219,15 @@ __global__ void __launch_bounds__(kBlkThreads) bigr_test_kernel(ModeState* st, c
   const double sW = block_sum_256(a, red);
   const double corr = block_sum_256(c, red);
   if (threadIdx.x == 0) {
-    st->sW = sW;
-    st->corr = corr;
-    const double e2 = st->normM2 - sW + corr;
+    double e2;
+    if (st->resid) {
+      st->corr = 0.0;
+      e2 = st->sW;
+    } else {
+      st->sW = sW;
+      st->corr = corr;
+      e2 = st->normM2 - sW + corr;
+    }
     als_stop_step(st, sqrt(e2 > 0.0 ? e2 : 0.0), sqrt(*norm_a2));
   }
 }
@@ -487,7 +494,15 @@ tals_status big_sweep_t(tals_ctx* c, const ModeJob& j) {
   if (c->st_host[j.n].done) return TALS_OK;
   // R-update W = B^T Q_k (as B x_n Q_k^T), ||W||^2, then Y = B W and X = Q_k^T Y
   if ((st = big_project<T>(c, j, (const T*)j.X, (const T*)c->Lt, (T*)j.Wt)) != TALS_OK) return st;
-  TALS_CK(launch_sumsq_parts(c->dtype, j.Wt, (size_t)(j.v.P * j.v.Q) * R, c->spart, s));
+  if (j.resid_kernel) {
+    // FP32 on a small tensor: e_k^2 = ||B - Q' W^T||^2 directly into the state (the
+    // Y partials' buffer serves as the residual's scratch before Y is formed)
+    if constexpr (sizeof(T) == 4)
+      TALS_CK(launch_mode_residual((const float*)j.X, j.v, R, (const float*)j.Wt, (const float*)c->Lt,
+                                   (double*)c->Ypart, (long long)(c->ypart_elems / 2), j.st, s));
+  } else {
+    TALS_CK(launch_sumsq_parts(c->dtype, j.Wt, (size_t)(j.v.P * j.v.Q) * R, c->spart, s));
+  }
   if ((st = big_adjoint<T>(c, j, (const T*)j.X, (const T*)j.Wt)) != TALS_OK) return st;
   TALS_BL(gemm_rm((cublasHandle_t)c->blas, true, false, R, R, j.v.I, 1.0, c->L64, R, c->Y64, R, 0.0, c->Gfin, R));
   bigr_test_kernel<<<1, kBlkThreads, 0, s>>>(j.st, c->spart, kSumsqParts, c->Gfin, c->GfinL, R, c->norm_a2);

@@ -916,6 +916,10 @@ cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const
   const long long tiles = (v.J() + 31) / 32;
   const int grid = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(cap, 1024), tiles));
   const size_t sm = (size_t)32 * (R + 1) * sizeof(float);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(mode_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
   mode_residual_kernel<<<grid, 256, sm, s>>>(X, v.P, v.I, v.Q, R, W, L, part, st);
   mode_residual_finish<<<1, 256, 0, s>>>(part, grid, st);
   return cudaGetLastError();

@@ -257,3 +257,37 @@ def test_gradients_vs_oracle_midsize(tals):
     A = torch.from_numpy(p.A).cuda()
     _, Us, _ = tals.st_hosvd(A, (32, 32, 16), eta=1e-6, seed=1)
     _gradient_parity(tals, p.A, _perturbed(Us, 18), 24)
+
+
+def test_rank500_dense_test_fullsize(tals):
+    """Sec. 6.4's dense test at its full size: 5000 x 5000 x 50 FP32 of multilinear
+    rank (500, 500, 5) plus noise 1e-2, st-HOSVD-ALS at eta 1e-4 (the large-rank path
+    for modes 1 and 2). Properties, every reference in FP64 on the device with torch
+    (independent of the library's kernels): orthonormal factors; each factor within
+    the noise-level angle of the planted one (sin <= 1e-2; ~4e-3 measured); the core
+    equal to A x_n U_n^T; the reported error equal to ||A - G x U|| / ||A|| (1e-5)."""
+    dims, ranks = W.RANK500_DIMS, W.RANK500_RANKS
+    A, F = W.tucker_model_device(W.RANK500_SEED, dims, ranks,
+                                 delta=W.tucker_delta(dims, ranks, W.RANK500_NOISE), return_factors=True)
+    G, Us, st = tals.st_hosvd(A, ranks, eta=1e-4, seed=1)
+    u = [x.double() for x in Us]
+    for n in range(3):
+        assert float((u[n].T @ u[n] - torch.eye(ranks[n], dtype=torch.float64, device="cuda")).abs().max()) <= 1e-6
+        c = torch.linalg.svdvals((u[n].T @ F[n]).cpu())
+        assert float(torch.sqrt(torch.clamp(1.0 - c.min() ** 2, min=0.0))) <= 1e-2, n
+    # core = A x_1 U_1^T x_2 U_2^T x_3 U_3^T and ||A - G x U||, 500 rows of A at a time
+    g = G.double()
+    t = torch.einsum("abc,kc->abk", g, u[2])
+    t = torch.einsum("abk,jb->ajk", t, u[1])                      # G x_2 U_2 x_3 U_3 (500 x 5000 x 50)
+    proj = torch.zeros(ranks, dtype=torch.float64, device="cuda")
+    res2, na2 = 0.0, 0.0
+    for i0 in range(0, dims[0], 500):
+        a = A[i0:i0 + 500].double()
+        proj += torch.einsum("ijk,ia,jb,kc->abc", a, u[0][i0:i0 + 500], u[1], u[2])
+        b = torch.einsum("ajk,ia->ijk", t, u[0][i0:i0 + 500])
+        res2 += float(((a - b) ** 2).sum())
+        na2 += float((a ** 2).sum())
+    assert float((g - proj).abs().max()) <= 1e-4 * float(proj.abs().max())
+    direct = (res2 / na2) ** 0.5
+    assert abs(st["rel_err"] - direct) <= 1e-5, (st["rel_err"], direct)
+    assert 0.009 <= direct <= 0.011
