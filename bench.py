@@ -36,7 +36,8 @@ METRIC = "st-HOSVD-ALS time-to-tol & HBM GB/s (% peak), mixed vs FP32 plain at e
 # where no capture of the current kernel exists.
 PASS_TRAFFIC = 2 * (268599552 + 14900480)   # CUDA-core FP32 fused pass
 TC_TRAFFIC = 2 * (134338048 + 3646208)      # BF16 tensor-core fused pass
-T32_TRAFFIC = {"w": None, "y": None}        # split-precision W and Y passes (changed since)
+T32_TRAFFIC = {"w": 2 * (268631040 + 12190976),   # split-precision W and Y passes
+               "y": 2 * (285368320 + 3259648)}
 PROD_TRAFFIC = {"w": 2 * (268647424 + 8675840),    # two-product form: register-tiled W product
                 "y": 2 * (285284096 + 6981632)}    # and the split-K Y = B W kernel
 DIMS = (512, 512, 512)
