@@ -7,7 +7,9 @@
 // B once:
 //   W = B_(n)^T Q_k, written as the tensor B x_n Q_k^T (P x R x Q layout) -- the
 //       R-update of Alg. 3 for the orthonormal Q_k -- by the mode-product GEMM;
-//   Y = B_(n) W, by the factor-adjoint GEMM (column splits, added in order);
+//   Y = B_(n) W, by the split-K row-tile kernel of adjoint.cu where the view has
+//       16-column rows (else the any-view factor adjoint), column splits of at most
+//       2048 columns added in FP64 in order;
 //   ||W||^2 from W, or (FP32 tensors up to a quarter of the input) the explicit
 //   residual ||B - Q_k W^T||^2 as e_k^2.
 // The initial guess of Sec. 4 is Y_0 = B_(n) S with S written out in the same
@@ -139,7 +141,12 @@ cudaError_t launch_mode_adjoint_any(int dtype, const void* X, const ModeView& v,
   const long long n = v.I * R;
   const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096));
   if (dtype == TALS_F32) {
-    e = launch_factor_adjoint_parts((const float*)X, v.P, v.I, v.Q, (const float*)W, R, S, (float*)part, s);
+    // the split-K register-tiled kernel where the view allows it (rows of 16
+    // columns: Q % 16 == 0, R <= 64, aligned), else the any-view tiles
+    if (adjoint_rows_ok(v, R, X, W))
+      e = launch_adjoint_rows((const float*)X, v, (const float*)W, R, S, (float*)part, nullptr, nullptr, s);
+    else
+      e = launch_factor_adjoint_parts((const float*)X, v.P, v.I, v.Q, (const float*)W, R, S, (float*)part, s);
     if (e != cudaSuccess) return e;
     sum_parts_f64_kernel<float><<<g, 256, 0, s>>>((const float*)part, S, n, (float*)Y);
   } else {

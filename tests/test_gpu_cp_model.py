@@ -129,7 +129,15 @@ def test_hooi_and_singular_vectors_on_a_long_mode(tals):
 
 def test_long_mode_with_many_columns_t_hosvd(tals):
     """The long mode's Y = B_(n) W sums 60000 columns: held to the FP32 gates, so
-    the column splits' FP32 sums must stay short (they are added in FP64)."""
+    the column splits' FP32 sums must stay short (they are added in FP64).
+
+    Sweep counts: at noise 1e-3, e_n^2 / ||B||^2 ~ 1e-6, and e_n comes from
+    ||B||^2 - ||W||^2 with W from FP32 products (~1e-8 relative in ||W||^2 once the
+    dominant direction of this all-positive core is summed over its 60000 columns):
+    e_n is known to ~0.5% of itself, ~5e-6 ||A||, above eta ||A|| = 1e-6 ||A||. The
+    stop decision is then taken at FP32 noise level and any change of summation
+    order moves it by a sweep or two; the sweep counts are held to [-1, +2] of the
+    oracle's, the results to the FP32 gates."""
     dims, ranks = (2400, 50, 40, 30), (24, 5, 5, 5)
     p = W.planted(W.SEED_BASE + 22, dims, ranks, "uniform510", 1e-3, dtype=np.float32)
     a64 = p.A.astype(np.float64)
@@ -141,4 +149,4 @@ def test_long_mode_with_many_columns_t_hosvd(tals):
     assert abs(rel_own - rel_ref) <= 1e-6 * max(1.0, rel_ref), (rel_own, rel_ref)
     for n in range(4):
         assert O.principal_angles(_np(Us[n]), ref.U[n]).max() <= 1e-4, n
-        assert abs(st["sweeps"][n] - ref.sweeps[n]) <= 1
+        assert -1 <= st["sweeps"][n] - ref.sweeps[n] <= 2, (n, st["sweeps"], ref.sweeps)
