@@ -203,22 +203,15 @@ cudaError_t launch_adjoint_rows(const float* X, const ModeView& v, const float* 
   kper = (kper + kAdjKC - 1) / kAdjKC * kAdjKC;
   const dim3 grid((unsigned)((v.I + kAdjTI - 1) / kAdjTI), (unsigned)S);
   if (R <= 32) {
-    static bool attr = false;
+    // the attribute belongs to the current device: set on every call
     const size_t sm = adjoint_smem<32>();
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(adjoint_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(adjoint_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     adjoint_rows_kernel<32><<<grid, 128, sm, s>>>(X, v.I, v.Q, W, R, J, kper, part, wsq, gate);
   } else {
-    static bool attr = false;
     const size_t sm = adjoint_smem<64>();
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(adjoint_rows_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(adjoint_rows_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     adjoint_rows_kernel<64><<<grid, 256, sm, s>>>(X, v.I, v.Q, W, R, J, kper, part, wsq, gate);
   }
   return cudaGetLastError();

@@ -302,11 +302,8 @@ tals_status big_chol(tals_ctx* c, const ModeJob& j, const double* G, int stage) 
   cudaStream_t s = c->stream;
   const BigWs w = big_ws(c, R);
   cudaError_t e;
-  static bool attr = false;
-  if (!attr) {
-    TALS_CK(cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem));
-    attr = true;
-  }
+  // the attribute belongs to the current device: set on every call
+  TALS_CK(cudaFuncSetAttribute(chol_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem));
   symm_kernel<<<grid_of((long long)R * R, c->sms), kBlkThreads, 0, s>>>(G, R, w.A, w.md);
   TALS_CK(cudaGetLastError());
   const int nb = (R + kNb - 1) / kNb;

@@ -225,13 +225,9 @@ __global__ void __launch_bounds__(256) write_signed_kernel(const double* __restr
 }
 
 cudaError_t launch_jacobi(const double* M, int R, double* V, double* lam, int* info, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kJacSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // the attribute belongs to the current device: set on every call
+  cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJacSmem);
+  if (e != cudaSuccess) return e;
   jacobi_eig_kernel<<<1, kJacThreads, kJacSmem, s>>>(M, R, V, lam, info);
   return cudaGetLastError();
 }

@@ -141,12 +141,9 @@ template <int RP>
 cudaError_t run_wstats(const float* W, const ModeView& v, int R, const double* GL, const ModeState* st,
                        double* part, int nb, cudaStream_t s) {
   constexpr int smem = (RP * RP + RP * kWsThreads) * (int)sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(wstats_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // the attribute belongs to the current device: set on every call
+  cudaError_t e = cudaFuncSetAttribute(wstats_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   wstats_kernel<RP><<<nb, kWsThreads, smem, s>>>(W, v.P, R, v.Q, GL, st, part);
   return cudaGetLastError();
 }
