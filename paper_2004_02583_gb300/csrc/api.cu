@@ -99,6 +99,11 @@ struct Need {
       // split sweeps: the W statistics' partials after the pass's, W in a scratch buffer
       spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y + 2 * (size_t)split_stat_blocks(v, sms));
       tbuf = std::max(tbuf, (size_t)(v.J() * R));
+      if (v.Q == 1) {
+        // thin last modes as a GEMM pair: the row-range Y partials, ||W||^2 partials
+        ypart = std::max(ypart, (size_t)thin_splits(v) * (size_t)v.I * (size_t)R);
+        spart = std::max(spart, (size_t)kSumsqParts);
+      }
       if (R <= 64 && v.Q % 16 == 0) {
         // the two-product form: the split-K Y product's partials and ||W||^2 partials
         const size_t S = (size_t)adjoint_rows_splits(v, R, sms);
@@ -235,6 +240,8 @@ constexpr int kT32AutoMinRank = 33;
 // mode product, Y = B W by the split-K adjoint (adjoint.cu).
 constexpr int kProdAutoMaxRank = 32;
 constexpr long long kProdAutoMinElems = 64LL << 20;
+// Thin last modes run as a GEMM pair (bigr.cu) from this many elements on.
+constexpr long long kThinMinElems = 16LL << 20;
 
 tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   j.st = c->st + j.n;
@@ -284,6 +291,21 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // the same tensors with the rank split across CTAs cannot form the residual
   // inside the pass: the sweep writes W and a residual kernel takes it
   j.resid_kernel = (c->dtype == TALS_F32) && j.pc.grid_y > 1 && j.Wdest != nullptr && small_t;
+  // a Q = 1 view without the transposed tile, in a context that holds cuBLAS (one
+  // with a large-rank mode, whose loops are host-driven): the sweep as a GEMM pair
+  // (bigr.cu), the fused pass's per-tile overhead avoided
+  j.thin = 0;
+  if (c->blas != nullptr && c->dtype == TALS_F32 && c->opts.fp32_engine == 0 && j.v.Q == 1 && !j.pc.tr &&
+      !j.resid && !j.resid_kernel && mine >= kThinMinElems) {
+    void* w = j.Wdest;
+    if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
+    const bool room = j.Wdest != nullptr || (size_t)(j.v.J() * j.R) <= c->tbuf_elems;
+    if (w != j.X && room && (size_t)thin_splits(j.v) * j.v.I * j.R <= c->ypart_elems &&
+        c->spart_n >= (size_t)kSumsqParts) {
+      j.thin = 1;
+      j.Wt = w;
+    }
+  }
   // the full-size FP32 modes: products on the split-precision tensor-core passes,
   // W written every sweep (the Y pass reads it) to the destination or a scratch
   // buffer that no other part of the mode uses
@@ -291,7 +313,7 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // explicit residual instead of the per-sweep one)
   j.t32 = 0;
   const int eng = c->opts.fp32_engine;
-  const bool want = eng == 2 || (eng == 0 && j.R >= kT32AutoMinRank && !j.resid && !j.resid_kernel);
+  const bool want = !j.thin && (eng == 2 || (eng == 0 && j.R >= kT32AutoMinRank && !j.resid && !j.resid_kernel));
   if (c->dtype == TALS_F32 && want && c->QS != nullptr && t32_supported(j.v, j.R) &&
       (uintptr_t)j.X % 16 == 0) {
     void* w = j.Wdest;
@@ -311,7 +333,7 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // sums ||W||^2): two reads of B, each product at a higher FMA rate than the
   // fused pass reaches with both
   j.prod = 0;
-  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32 &&
+  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32 && !j.thin &&
       (eng == 3 || (eng == 0 && j.R <= kProdAutoMaxRank && mine >= kProdAutoMinElems))) {
     void* w = j.Wdest;
     if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
@@ -331,7 +353,7 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
   // the last forms W alone (the register-tiled mode product into the destination
   // or a scratch buffer), takes the test, and forms Y only if needed
   j.split_ok = 0;
-  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32) {
+  if (c->dtype == TALS_F32 && !j.resid && !j.resid_kernel && !j.t32 && !j.thin) {
     void* w = j.prod ? j.Wt : j.Wdest;
     if (w == nullptr) w = (j.X == c->tbuf[1]) ? c->tbuf[0] : c->tbuf[1];
     const int nb = split_stat_blocks(j.v, c->sms);
@@ -367,6 +389,7 @@ tals_status mode_init_launch_bulk(tals_ctx* c, const ModeJob& j, bool set_norm_a
   TALS_CK(launch_state_init(j.st, c->opts.eta, c->opts.max_sweeps,
                             j.resid || j.resid_kernel || j.t32, s, bulk_max, j.t32, j.split_ok, j.prod));
   if (j.bigr) return bigr_init_launch(c, j, set_norm_a);
+  if (j.thin) return thin_init_launch(c, j, set_norm_a);
   if (j.twopass) return twopass_init_launch(c, j, set_norm_a);
   if (j.t32) {
     // Sec. 4 on the tensor cores: Y0 = B_(n) S (split-precision) and ||B_(n)||^2
@@ -411,6 +434,7 @@ tals_status mode_sweep_launch(tals_ctx* c, const ModeJob& j) {
   const long long I = j.v.I;
   cudaError_t e;
   if (j.bigr) return bigr_sweep_launch(c, j);
+  if (j.thin) return thin_sweep_launch(c, j);
   if (j.twopass) return twopass_sweep_launch(c, j);
   if (j.t32) {
     // split-precision passes: W = B^T Q_k (written), then Y = B W with the residual

@@ -514,9 +514,6 @@ tals_status big_sweep_t(tals_ctx* c, const ModeJob& j) {
   return big_store_basis(c, j);
 }
 
-#undef TALS_BL
-#undef TALS_CK
-
 }  // namespace
 
 bool bigr_rank(int R) { return R > kBigRankMin; }
@@ -570,6 +567,68 @@ tals_status bigr_time_products(tals_ctx* c, const ModeJob& j, int iters, double*
   return TALS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Thin last modes: a Q = 1 view (B_(n) = X^T for X the P x I row-major tensor)
+// whose I_n is not a multiple of 4 has no transposed tile in the fused pass, whose
+// untransposed tiles of I_n rows are then dominated by per-tile overhead (the
+// rank-5 third mode of Sec. 6.4's dense test, I_n = 50: 12.5 ms per sweep on the
+// 4.7 GiB tensor). Where the context holds a cuBLAS handle the sweep is two GEMMs
+// instead: W = X Q_k (P x R, the R-update written as B x_n Q_k^T) and the Y
+// partials X[range]^T W[range] over row ranges of at most max(2048, P / 1024) rows
+// (each an FP32 sum no longer than the fused pass's own per-CTA sums), followed by
+// the fused path's reduction, stop test and L-update over those partials; the
+// initial guess likewise with the sketch S written out in place of W.
+// ---------------------------------------------------------------------------
+namespace {
+
+long long thin_chunk(const ModeView& v) { return std::max<long long>(kChunk, (v.P + 1023) / 1024); }
+
+// Ypart[s] = X[range s]^T V[range s] (I x R), V P x R.
+tals_status thin_y_parts(tals_ctx* c, const ModeJob& j, const float* X, const float* V) {
+  cublasHandle_t h = (cublasHandle_t)c->blas;
+  const long long I = j.v.I, P = j.v.P, R = j.R, n = I * R;
+  const long long chunk = thin_chunk(j.v);
+  const int full = (int)(P / chunk);
+  const long long tail = P - (long long)full * chunk;
+  float* part = (float*)c->Ypart;
+  if (full > 0)
+    TALS_BL(gemm_rm_batched(h, true, false, I, R, chunk, X, I, chunk * I, V, R, chunk * R, part, R, n, full));
+  if (tail > 0)
+    TALS_BL(gemm_rm(h, true, false, I, R, tail, 1.f, X + (size_t)full * chunk * I, I, V + (size_t)full * chunk * R,
+                    R, 0.f, part + (size_t)full * n, R));
+  return TALS_OK;
+}
+
+}  // namespace
+
+int thin_splits(const ModeView& v) {
+  const long long chunk = thin_chunk(v);
+  return (int)((v.P + chunk - 1) / chunk);
+}
+
+tals_status thin_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  tals_status st;
+  // Sec. 4: Y0 = B_(n) S (S written out as P x R with the fused pass's entries), ||B||^2
+  TALS_CK(launch_sketch_prq(c->dtype, j.Wt, j.v, j.R, sketch_state(c->opts.seed, j.n), c->sms, s));
+  if ((st = thin_y_parts(c, j, (const float*)j.X, (const float*)j.Wt)) != TALS_OK) return st;
+  TALS_CK(launch_sumsq_parts(c->dtype, j.X, (size_t)(j.v.P * j.v.I), c->spart, s));
+  return mode_init_tail(c, j, set_norm_a, thin_splits(j.v), c->spart, kSumsqParts);
+}
+
+tals_status thin_sweep_launch(tals_ctx* c, const ModeJob& j) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  tals_status st;
+  // W = B^T Q_k = X Q_k (P x R), ||W||^2, the Y partials; then the fused path's tail
+  TALS_BL(gemm_rm((cublasHandle_t)c->blas, false, false, j.v.P, j.R, j.v.I, 1.f, (const float*)j.X, j.v.I,
+                  (const float*)c->Lt, j.R, 0.f, (float*)j.Wt, j.R));
+  TALS_CK(launch_sumsq_parts(c->dtype, j.Wt, (size_t)j.v.P * j.R, c->spart, s));
+  if ((st = thin_y_parts(c, j, (const float*)j.X, (const float*)j.Wt)) != TALS_OK) return st;
+  return mode_sweep_tail(c, j, thin_splits(j.v), kSumsqParts, 1);
+}
+
 tals_status bigr_open(tals_ctx* c) {
   if (c->blas != nullptr) return TALS_OK;
   cublasHandle_t h = nullptr;
@@ -587,5 +646,8 @@ void bigr_close(tals_ctx* c) {
   if (c->blas != nullptr) cublasDestroy((cublasHandle_t)c->blas);
   c->blas = nullptr;
 }
+
+#undef TALS_BL
+#undef TALS_CK
 
 }  // namespace tals

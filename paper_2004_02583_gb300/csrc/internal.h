@@ -35,6 +35,7 @@ struct ModeJob {
   int prod = 0;                  // FP32 sweeps as two products (mode product W, split-K Y)
   int ys = 0;                    // column splits of that Y product
   int bigr = 0;                  // R above kBigRankMin: bigr.cu (GEMM products, blocked FP64 algebra)
+  int thin = 0;                  // Q = 1 view without the fused pass's transposed tile, as a GEMM pair
 };
 
 struct DriveState {
@@ -92,6 +93,13 @@ tals_status bigr_sweep_launch(tals_ctx* c, const ModeJob& j);
 // Mean durations (ms) and algorithmic bytes of a large-rank mode's two products
 // (W = B^T Q, then Y = B W with its FP64 range sums), timed on the current basis.
 tals_status bigr_time_products(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes);
+// Thin last modes (bigr.cu): FP32 views with Q = 1 whose I_n rules out the fused
+// pass's transposed tile, in contexts holding a cuBLAS handle: W = X Q and the
+// row-range partials of Y = X^T W as GEMMs, then the fused path's tail over those
+// partials. thin_splits: the number of row ranges (Y partials).
+int thin_splits(const ModeView& v);
+tals_status thin_init_launch(tals_ctx* c, const ModeJob& j, bool set_norm_a);
+tals_status thin_sweep_launch(tals_ctx* c, const ModeJob& j);
 
 // hooi.cu: HOOI refinement (Sec. 6.3) and singular vectors (Sec. 5)
 struct ViewR {
