@@ -61,7 +61,7 @@ int device_sms() {
 namespace {
 
 struct Need {
-  size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0, qs = 0;
+  size_t ypart = 0, spart = 0, gpart = 0, ir = 0, tbuf = 0, qs = 0, unf = 0;
   void add_mode(int dtype, const ModeView& v, int R, int sms, bool sweep) {
     if (bigr_rank(R)) {
       // large ranks (bigr.cu): Y and its column-range partials in Ypart, W in a
@@ -72,6 +72,8 @@ struct Need {
       if (sweep) {
         ypart = std::max(ypart, (size_t)(twopass_splits(v, R, sms) + 1) * (size_t)v.I * (size_t)R);
         tbuf = std::max(tbuf, (size_t)(v.J() * R));
+        // general views: the written-out unfolding and its R x J product
+        if (v.P > 1 && v.Q > 1) unf = std::max(unf, (size_t)(v.P * v.I * v.Q) + (size_t)(v.J() * R));
       } else {
         PassConfig pc = pass_config(dtype, v, R, sms);
         if (pc.ok) spart = std::max(spart, (size_t)pc.grid_x * pc.grid_y);
@@ -205,6 +207,8 @@ tals_status ctx_plan_and_alloc(tals_ctx* c) {
     return cuda_fail(e, "workspace clear");
   TALS_AL(c->st, (size_t)TALS_MAX_NDIM * sizeof(ModeState));
   if (bigr_ws_doubles(rmax) > 0) TALS_AL(c->bw, bigr_ws_doubles(rmax) * sizeof(double));
+  if (need.unf > 0) TALS_AL(c->ubuf, need.unf * esz);
+  c->ubuf_elems = need.unf;
   TALS_AL(c->norm_a2, 8 * sizeof(double));
   if (need.qs > 0) {
     TALS_AL(c->QS, need.qs * sizeof(float));
@@ -265,6 +269,9 @@ tals_status mode_setup(tals_ctx* c, ModeJob& j) {
     j.bigr = 1;
     j.Wt = w;
     j.resid_kernel = c->dtype == TALS_F32 && small_t;
+    // general views on the written-out unfolding (plain GEMMs), where it fits
+    j.unf = j.v.P > 1 && j.v.Q > 1 &&
+            (size_t)(j.v.P * j.v.I * j.v.Q) + (size_t)(j.v.J() * j.R) <= c->ubuf_elems;
     return TALS_OK;
   }
   j.pc = pass_config(c->dtype, j.v, j.R, c->sms);
@@ -730,7 +737,7 @@ void tals_destroy(tals_ctx* c) {
   bigr_close(c);
   void* bufs[] = {c->GpartL, c->GfinL, c->tbuf[0], c->tbuf[1], c->Ypart, c->spart, c->Gpart, c->Gfin, c->F,
                   c->Y64,     c->L64,     c->Z64,   c->Lt,    c->st,    c->norm_a2, c->A_owned,
-                  c->A_owned2, c->hostio_G, c->pipe_G[0], c->pipe_G[1], c->bw};
+                  c->A_owned2, c->hostio_G, c->pipe_G[0], c->pipe_G[1], c->bw, c->ubuf};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, s);
   for (int m = 0; m < TALS_MAX_NDIM; ++m)

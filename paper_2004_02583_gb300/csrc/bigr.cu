@@ -152,6 +152,28 @@ __global__ void sum_to_f64_kernel(const T* __restrict__ part, int S, long long n
   }
 }
 
+// U[i][p Q + q] = X[p][i][q]: the mode-n unfolding written out (I x P Q).
+template <typename T>
+__global__ void unfold_kernel(const T* __restrict__ X, long long P, long long I, long long Q, T* __restrict__ U) {
+  const long long J = P * Q, n = I * J;
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    const long long i = o / J, jj = o - i * J;
+    const long long p = jj / Q, q = jj - p * Q;
+    U[o] = X[(p * I + i) * Q + q];
+  }
+}
+
+// W[p][r][q] = Wr[r][p Q + q]: an R x P Q product back in the P x R x Q layout.
+template <typename T>
+__global__ void fold_kernel(const T* __restrict__ Wr, long long P, long long R, long long Q, T* __restrict__ W) {
+  const long long n = P * R * Q;
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    const long long q = o % Q, pr = o / Q;
+    const long long r = pr % R, p = pr / R;
+    W[o] = Wr[r * (P * Q) + p * Q + q];
+  }
+}
+
 // The stored basis: Lt = L64 rounded to the tensor's type and, for FP32, its
 // rounding error D = Lt - L64 (exact in FP32 to its own rounding: |D| is near
 // 2^-24 |L64|).
@@ -462,14 +484,60 @@ tals_status big_project(tals_ctx* c, const ModeJob& j, const T* X, const T* Lt, 
   return TALS_OK;
 }
 
+// General views (P > 1 and Q > 1): the products run on the unfolding written out
+// once per mode (I x P Q in the context's unfolding buffer, followed by room for
+// an R x P Q product), i.e. as the P = 1 view {1, I, P Q} with plain GEMMs; the
+// mode's W is folded back to the P x R x Q layout when the stop rule ends it.
+ModeJob unfolded_job(const tals_ctx* c, const ModeJob& j) {
+  ModeJob u = j;
+  u.v = ModeView{1, j.v.I, j.v.P * j.v.Q};
+  u.X = c->ubuf;
+  u.Wt = (char*)c->ubuf + (size_t)(j.v.P * j.v.I * j.v.Q) * c->esz;
+  return u;
+}
+
+// The unfolding of j's tensor in the buffer: written unless it already holds it
+// (force: always, at the start of a mode -- the tensor may have new contents).
+tals_status ensure_unfolded(tals_ctx* c, const ModeJob& j, bool force) {
+  if (!force && c->ubuf_src == j.X && c->ubuf_mode == j.n) return TALS_OK;
+  const long long n = j.v.P * j.v.I * j.v.Q;
+  cudaError_t e;
+  if (c->dtype == TALS_F32)
+    unfold_kernel<float><<<grid_of(n, c->sms), 256, 0, c->stream>>>((const float*)j.X, j.v.P, j.v.I, j.v.Q,
+                                                                     (float*)c->ubuf);
+  else
+    unfold_kernel<double><<<grid_of(n, c->sms), 256, 0, c->stream>>>((const double*)j.X, j.v.P, j.v.I, j.v.Q,
+                                                                      (double*)c->ubuf);
+  TALS_CK(cudaGetLastError());
+  c->ubuf_src = j.X;
+  c->ubuf_mode = j.n;
+  return TALS_OK;
+}
+
+tals_status fold_result(tals_ctx* c, const ModeJob& j, const ModeJob& u) {
+  const long long n = j.v.P * j.R * j.v.Q;
+  cudaError_t e;
+  if (c->dtype == TALS_F32)
+    fold_kernel<float><<<grid_of(n, c->sms), 256, 0, c->stream>>>((const float*)u.Wt, j.v.P, j.R, j.v.Q,
+                                                                   (float*)j.Wt);
+  else
+    fold_kernel<double><<<grid_of(n, c->sms), 256, 0, c->stream>>>((const double*)u.Wt, j.v.P, j.R, j.v.Q,
+                                                                    (double*)j.Wt);
+  TALS_CK(cudaGetLastError());
+  return TALS_OK;
+}
+
 template <typename T>
-tals_status big_init_t(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
+tals_status big_init_t(tals_ctx* c, const ModeJob& j0, bool set_norm_a) {
   cudaStream_t s = c->stream;
-  const int R = j.R;
+  const int R = j0.R;
   cudaError_t e;
   tals_status st;
+  if (j0.unf && (st = ensure_unfolded(c, j0, true)) != TALS_OK) return st;
+  const ModeJob j = j0.unf ? unfolded_job(c, j0) : j0;
   // Sec. 4: Y0 = B_(n) S with S written out in the P x R x Q layout (the same
-  // counter-based entries the fused pass draws), and ||B_(n)||^2
+  // counter-based entries the fused pass draws: column j = p Q + q either way), and
+  // ||B_(n)||^2
   TALS_CK(launch_sketch_prq(c->dtype, j.Wt, j.v, R, sketch_state(c->opts.seed, j.n), c->sms, s));
   if ((st = big_adjoint<T>(c, j, (const T*)j.X, (const T*)j.Wt)) != TALS_OK) return st;
   TALS_CK(launch_sumsq_parts(c->dtype, j.X, (size_t)(j.v.P * j.v.I * j.v.Q), c->spart, s));
@@ -482,13 +550,15 @@ tals_status big_init_t(tals_ctx* c, const ModeJob& j, bool set_norm_a) {
 }
 
 template <typename T>
-tals_status big_sweep_t(tals_ctx* c, const ModeJob& j) {
+tals_status big_sweep_t(tals_ctx* c, const ModeJob& j0) {
   cudaStream_t s = c->stream;
-  const int R = j.R;
+  const int R = j0.R;
   cudaError_t e;
   tals_status st;
   if ((st = read_states(c)) != TALS_OK) return st;
-  if (c->st_host[j.n].done) return TALS_OK;
+  if (c->st_host[j0.n].done) return TALS_OK;
+  if (j0.unf && (st = ensure_unfolded(c, j0, false)) != TALS_OK) return st;
+  const ModeJob j = j0.unf ? unfolded_job(c, j0) : j0;
   // R-update W = B^T Q_k (as B x_n Q_k^T), ||W||^2, then Y = B W and X = Q_k^T Y
   if ((st = big_project<T>(c, j, (const T*)j.X, (const T*)c->Lt, (T*)j.Wt)) != TALS_OK) return st;
   if (j.resid_kernel) {
@@ -505,7 +575,10 @@ tals_status big_sweep_t(tals_ctx* c, const ModeJob& j) {
   bigr_test_kernel<<<1, kBlkThreads, 0, s>>>(j.st, c->spart, kSumsqParts, c->Gfin, c->GfinL, R, c->norm_a2);
   TALS_CK(cudaGetLastError());
   if ((st = read_states(c)) != TALS_OK) return st;
-  if (c->st_host[j.n].done) return TALS_OK;   // Q_k and this sweep's W are the mode's result
+  if (c->st_host[j.n].done) {
+    // Q_k and this sweep's W are the mode's result
+    return j0.unf ? fold_result(c, j0, j) : TALS_OK;
+  }
   // L-update: L_{k+1} = Y X^{-1} = (Y F^{-T}) F^{-1}, then its Q factor
   if ((st = big_chol(c, j, c->Gfin, 1)) != TALS_OK) return st;
   if ((st = big_solve_fwd(c, j, c->Y64, c->Z64)) != TALS_OK) return st;
@@ -531,8 +604,13 @@ tals_status bigr_sweep_launch(tals_ctx* c, const ModeJob& j) {
   return c->dtype == TALS_F32 ? big_sweep_t<float>(c, j) : big_sweep_t<double>(c, j);
 }
 
-tals_status bigr_time_products(tals_ctx* c, const ModeJob& j, int iters, double* ms, double* bytes) {
+tals_status bigr_time_products(tals_ctx* c, const ModeJob& j0, int iters, double* ms, double* bytes) {
   cudaStream_t s = c->stream;
+  if (j0.unf) {
+    const tals_status us = ensure_unfolded(c, j0, true);
+    if (us != TALS_OK) return us;
+  }
+  const ModeJob j = j0.unf ? unfolded_job(c, j0) : j0;
   cudaEvent_t ev[3];
   for (auto& x : ev) cudaEventCreate(&x);
   double acc[2] = {0.0, 0.0};

@@ -36,6 +36,7 @@ struct ModeJob {
   int ys = 0;                    // column splits of that Y product
   int bigr = 0;                  // R above kBigRankMin: bigr.cu (GEMM products, blocked FP64 algebra)
   int thin = 0;                  // Q = 1 view without the fused pass's transposed tile, as a GEMM pair
+  int unf = 0;                   // large rank on a general view: products on the written-out unfolding
 };
 
 struct DriveState {
@@ -199,4 +200,8 @@ struct tals_ctx {
   void* blas = nullptr;       // cuBLAS handle of the large-rank modes (bigr.cu)
   double* bw = nullptr;       // their R x R scratch (bigr_ws_doubles)
   bool has_bigr = false;      // some rank above kBigRankMin: host-driven mode loops
+  void* ubuf = nullptr;       // a large-rank general view's unfolding and its R x J product
+  size_t ubuf_elems = 0;
+  const void* ubuf_src = nullptr;   // the tensor and mode whose unfolding ubuf holds
+  int ubuf_mode = -1;
 };
