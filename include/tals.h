@@ -12,7 +12,8 @@
  *
  * Conventions shared by every entry point
  *   Tensors are dense, contiguous, row-major (C order): element (i_1..i_N) of a
- *   tensor with sizes (I_1..I_N) sits at offset ((i_1*I_2 + i_2)*I_3 + ...) + i_N.
+ *   tensor with sizes (I_1..I_N) sits at offset ((i_1*I_2 + i_2)*I_3 + ...) + i_N
+ *   (tucker_als_init_strided takes an input tensor in any strided layout).
  *   The mode-n unfolding column index j is the row-major linear index over the
  *   remaining modes in logical order (the paper writes the Fortran order; the
  *   two differ only by a column permutation, which no result depends on except
@@ -213,6 +214,22 @@ tals_status tals_selftest_wait_timeout(double seconds, void* stream);
  * (to be filled by st_hosvd_host or by copying into tals_ctx_tensor()). */
 tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int64_t* dims,
                                   const int* ranks, const tals_opts* opts, void* stream);
+
+/* Like tucker_als_init for a tensor in any strided layout (the unfoldings of
+ * Sec. 3 taken from the tensor as it is laid out): element (i_1..i_N) is at
+ * A + sum_k i_k * strides[k], strides in elements, in any order (a permuted or
+ * sliced view). The context gathers A into a dense row-major buffer it owns
+ * (as tucker_als_init_owned), stream-ordered on `stream` during this call; the
+ * decompositions then read that copy, so later changes of A are not seen, and the
+ * caller keeps A alive and unchanged until the stream has run the gather.
+ * Errors (checked on the host before any device work): TALS_EINVAL for NULL
+ * pointers, ndim outside [2, 8], a negative stride, a zero stride on an axis of
+ * size above 1, or strides under which two elements share an address (each axis
+ * of size above 1 must step over the whole extent of the next smaller-strided
+ * one); otherwise as tucker_als_init. */
+tals_status tucker_als_init_strided(tals_ctx** ctx, const void* A, int dtype, int ndim, const int64_t* dims,
+                                    const int64_t* strides, const int* ranks, const tals_opts* opts,
+                                    void* stream);
 
 /* Device pointer of the tensor the context reads (A, or its owned buffer). */
 void* tals_ctx_tensor(tals_ctx* ctx);

@@ -80,6 +80,8 @@ SIGNATURES = {
                                        _I64P, _IP, ctypes.POINTER(tals_opts), _VP]),
     "tucker_als_init_owned": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
                                              _I64P, _IP, ctypes.POINTER(tals_opts), _VP]),
+    "tucker_als_init_strided": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, ctypes.c_int, ctypes.c_int,
+                                               _I64P, _I64P, _IP, ctypes.POINTER(tals_opts), _VP]),
     "tals_ctx_tensor": (_VP, [_VP]),
     "als_mode_sweep": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_double), _IP]),
@@ -265,7 +267,10 @@ class Context:
                  seed: int = 0, order: Optional[Sequence[int]] = None,
                  precision="native", bulk_sweeps: Optional[int] = None,
                  use_graph: bool = True, fp32_engine="auto", stream=None):
-        _require_cuda(A)
+        # any strided CUDA tensor (a permuted or sliced view): a contiguous one is
+        # read in place, another is gathered once into the context's own buffer
+        if A is None or not A.is_cuda:
+            raise ValueError("tensors must be CUDA tensors (no CPU fallback)")
         self.A = A
         self.ndim = A.dim()
         self.dims = [int(d) for d in A.shape]
@@ -280,8 +285,13 @@ class Context:
         dims = (ctypes.c_int64 * self.ndim)(*self.dims)
         rk = (ctypes.c_int * self.ndim)(*self.ranks)
         h = ctypes.c_void_p()
-        _check(lib().tucker_als_init(ctypes.byref(h), A.data_ptr(), self._code, self.ndim, dims,
-                                     rk, ctypes.byref(o), _stream_ptr(stream)))
+        if A.is_contiguous():
+            _check(lib().tucker_als_init(ctypes.byref(h), A.data_ptr(), self._code, self.ndim, dims,
+                                         rk, ctypes.byref(o), _stream_ptr(stream)))
+        else:
+            strides = (ctypes.c_int64 * self.ndim)(*[int(x) for x in A.stride()])
+            _check(lib().tucker_als_init_strided(ctypes.byref(h), A.data_ptr(), self._code, self.ndim, dims,
+                                                 strides, rk, ctypes.byref(o), _stream_ptr(stream)))
         self._h = h
 
     def close(self):

@@ -726,6 +726,27 @@ tals_status tucker_als_init_owned(tals_ctx** ctx, int dtype, int ndim, const int
   return ctx_create(ctx, nullptr, true, dtype, ndim, dims, ranks, opts, stream);
 }
 
+tals_status tucker_als_init_strided(tals_ctx** ctx, const void* A, int dtype, int ndim, const int64_t* dims,
+                                    const int64_t* strides, const int* ranks, const tals_opts* opts,
+                                    void* stream) {
+  if (!ctx) return fail(TALS_EINVAL, "ctx must not be NULL");
+  *ctx = nullptr;
+  if (!A || !dims || !strides) return fail(TALS_EINVAL, "A, dims and strides must not be NULL");
+  if (ndim < 2 || ndim > TALS_MAX_NDIM) return fail(TALS_EINVAL, "ndim %d outside [2, 8]", ndim);
+  if (!strides_valid(ndim, dims, strides))
+    return fail(TALS_EINVAL, "strides must be non-negative and describe a tensor whose elements do not overlap");
+  tals_status st = ctx_create(ctx, nullptr, true, dtype, ndim, dims, ranks, opts, stream);
+  if (st != TALS_OK) return st;
+  tals_ctx* c = *ctx;
+  const cudaError_t e = launch_gather(dtype, A, ndim, dims, strides, c->A_owned, c->sms, c->stream);
+  if (e != cudaSuccess) {
+    tals_destroy(c);
+    *ctx = nullptr;
+    return cuda_fail(e, "strided gather");
+  }
+  return TALS_OK;
+}
+
 void* tals_ctx_tensor(tals_ctx* ctx) { return ctx ? const_cast<void*>(ctx->A) : nullptr; }
 
 void tals_destroy(tals_ctx* c) {

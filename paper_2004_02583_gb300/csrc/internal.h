@@ -81,6 +81,12 @@ tals_status twopass_sweep_launch(tals_ctx* c, const ModeJob& j);
 // out = X x_n U^T (fused pass in projection mode, else the tiled mode product);
 // *nsp partial sums of ||out||^2 left in c->spart.
 tals_status project_mode(tals_ctx* c, const void* X, const ModeView& v, int R, const void* U, void* out, int* nsp);
+// strided.cu: element strides that describe a tensor without aliasing (non-negative,
+// each axis of size above 1 stepping over the extent of the next smaller one), and
+// the gather of such a tensor into the dense row-major layout.
+bool strides_valid(int ndim, const int64_t* dims, const int64_t* strides);
+cudaError_t launch_gather(int dtype, const void* src, int ndim, const int64_t* dims, const int64_t* strides,
+                          void* dst, int sms, cudaStream_t s);
 // bigr.cu: modes of rank above kBigRankMin (largest rank kBigRankMax). Their loop
 // is host-driven: a sweep reads the stop flag before its L-update.
 constexpr int kBigRankMin = 64;

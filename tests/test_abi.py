@@ -81,3 +81,28 @@ def test_host_validation_without_a_gpu(lib):
     assert init(7, (10, 9, 8), (2, 2, 2)) == pkg.TALS_EINVAL                 # dtype
     assert init(pkg.TALS_F32, (1100, 40, 40), (1030, 40, 40)) == pkg.TALS_ENOTSUP   # R > 1024
     assert b"largest supported rank 1024" in lib.tals_last_error()
+
+
+def test_strided_init_validates_on_the_host(lib):
+    """tucker_als_init_strided rejects strides that cannot describe a tensor before
+    any device work: NULL pointers, a negative stride, a zero stride on an axis of
+    size above 1, and strides under which two elements share an address."""
+    import ctypes
+    import paper_2004_02583_gb300 as pkg
+
+    def init(dims, strides, A=ctypes.c_void_p(256), ranks=None):
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        s = None if strides is None else (ctypes.c_int64 * len(strides))(*strides)
+        r = (ctypes.c_int * len(dims))(*(ranks or [2] * len(dims)))
+        o = pkg.default_opts()
+        return lib.tucker_als_init_strided(ctypes.byref(h), A, pkg.TALS_F32, len(dims), d, s, r,
+                                           ctypes.byref(o), None)
+
+    assert init((4, 5, 6), None) == pkg.TALS_EINVAL
+    assert init((4, 5, 6), (30, 6, 1), A=None) == pkg.TALS_EINVAL
+    assert init((4, 5, 6), (30, -6, 1)) == pkg.TALS_EINVAL
+    assert init((4, 5, 6), (30, 0, 1)) == pkg.TALS_EINVAL      # broadcast axis
+    assert init((4, 5, 6), (6, 5, 1)) == pkg.TALS_EINVAL       # axes 0 and 1 overlap
+    assert init((4, 5, 6), (30, 6, 2)) == pkg.TALS_EINVAL      # axis 1 does not step over axis 2
+    assert b"overlap" in lib.tals_last_error()
