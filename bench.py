@@ -1050,8 +1050,9 @@ def run_c5(args):
     def loss_and_grad():
         Ar = A.detach().requires_grad_(True)
         Ur = [u.detach().requires_grad_(True) for u in Us]
-        B = tals.tucker_reconstruct(tals.tucker_project(Ar, Ur), Ur)
-        loss = ((Ar - B) ** 2).sum()
+        # ||A - G x U||^2 with G = project(A, U): the fused loss kernel (the
+        # reconstruction is never written), then the hand-written adjoints
+        loss = tals.tucker_reconstruction_loss(Ar, tals.tucker_project(Ar, Ur), Ur)
         loss.backward()
         return Ar.grad, [u.grad for u in Ur]
 

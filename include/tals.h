@@ -240,6 +240,20 @@ void* tals_ctx_tensor(tals_ctx* ctx);
 tals_status reconstruct(const void* G, void* const* U, int dtype, int ndim,
                         const int64_t* dims, const int* ranks, void* B_out, void* stream);
 
+/* Reconstruction loss of the Tucker model (Sec. 2): f = ||G x_1 U1 ... x_N UN - A||_F^2
+ * with its gradient with respect to the reconstruction, D_out = 2 (B - A) (device,
+ * dims, same layout as A), formed without writing B: in FP32 the last mode product of
+ * the reconstruction computes B - A, writes D_out and sums the squares from the same
+ * registers; otherwise (FP64, or a last view the register-tiled product does not
+ * take) B is written to D_out and turned into the gradient by one elementwise pass.
+ * The gradients with respect to G and U follow from reconstruct_backward with
+ * B_bar = D_out (scaled by the caller's output gradient). loss_out: a DEVICE double
+ * (FP64 sum of FP32 squares, compensated per thread). D_out must not alias A.
+ * Stream-ordered scratch; not synchronised. Errors as for reconstruct. */
+tals_status reconstruction_loss(const void* G, void* const* U, const void* A, int dtype, int ndim,
+                                const int64_t* dims, const int* ranks, void* D_out, double* loss_out,
+                                void* stream);
+
 /* Core projection G = A x_1 U1^T ... x_N UN^T (Alg. 1/4 core step). */
 tals_status project(const void* A, void* const* U, int dtype, int ndim, const int64_t* dims,
                     const int* ranks, void* G_out, void* stream);

@@ -93,6 +93,8 @@ SIGNATURES = {
     "st_hosvd_host_many": (ctypes.c_int, [_VP, ctypes.c_int, _VPP, _VPP, _VPP,
                                           ctypes.POINTER(tals_stats)]),
     "reconstruct": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
+    "reconstruction_loss": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP,
+                                           _VP, _VP]),
     "project": (ctypes.c_int, [_VP, _VPP, ctypes.c_int, ctypes.c_int, _I64P, _IP, _VP, _VP]),
     "reconstruct_backward": (ctypes.c_int, [_VP, _VPP, _VP, ctypes.c_int, ctypes.c_int, _I64P,
                                             _IP, _VP, _VPP, _VP]),
@@ -549,6 +551,21 @@ def reconstruct(G, Us, out=None, stream=None):
     return B
 
 
+def reconstruction_loss(A, G, Us, stream=None):
+    """(f, D) with f = ||G x_1 U1 ... x_N UN - A||^2 (a 0-dim FP64 device tensor)
+    and D = 2 (B - A), the gradient with respect to the reconstruction B, formed
+    without writing B."""
+    torch = _torch()
+    ndim, dims, ranks = _op_args(G, Us, "ranks")
+    _expect(A, list(dims), G.dtype, "A")
+    _require_cuda(A, G, *Us)
+    D = torch.empty_like(A)
+    f = torch.empty((), dtype=torch.float64, device=A.device)
+    _check(lib().reconstruction_loss(G.data_ptr(), _ptrs(Us), A.data_ptr(), _dtype_code(G), ndim, dims, ranks,
+                                     D.data_ptr(), f.data_ptr(), _stream_ptr(stream)))
+    return f, D
+
+
 def reconstruct_backward(G, Us, B_bar, need_g=True, need_u=True, stream=None):
     """(G_bar, [U_bar_n]) of B = reconstruct(G, Us) for the output gradient B_bar."""
     torch = _torch()
@@ -626,7 +643,36 @@ def _make_autograd():
             G_bar, U_bar = reconstruct_backward(G, Us, B_bar.contiguous(), need_g, need_u)
             return (G_bar, *U_bar)
 
-    return TalsProject, TalsReconstruct
+    class TalsReconstructionLoss(torch.autograd.Function):
+        """f = ||G x_1 U1 ... x_N UN - A||^2 with the fused loss kernel forward and the
+        reconstruction adjoint backward (B_bar = df/dB = 2 (B - A), kept from forward)."""
+
+        @staticmethod
+        def forward(ctx, A, G, *Us):
+            A = A.contiguous()
+            G = G.contiguous()
+            Us = [u.contiguous() for u in Us]
+            f, D = reconstruction_loss(A, G, Us)
+            ctx.save_for_backward(G, D, *Us)
+            return f
+
+        @staticmethod
+        def backward(ctx, f_bar):
+            G, D, *Us = ctx.saved_tensors
+            # df/dB = D; the adjoint is linear in its input, so the output gradient
+            # scales the small results (no pass over D, no host synchronisation)
+            c = f_bar.to(D.dtype)
+            need_g = ctx.needs_input_grad[1]
+            need_u = any(ctx.needs_input_grad[2:])
+            G_bar, U_bar = None, [None] * len(Us)
+            if need_g or need_u:
+                G_bar, U_bar = reconstruct_backward(G, Us, D, need_g, need_u)
+                G_bar = G_bar * c if G_bar is not None else None
+                U_bar = [u * c if u is not None else None for u in U_bar]
+            A_bar = -(D * c) if ctx.needs_input_grad[0] else None
+            return (A_bar, G_bar, *U_bar)
+
+    return TalsProject, TalsReconstruct, TalsReconstructionLoss
 
 
 def tucker_project(A, Us):
@@ -637,6 +683,12 @@ def tucker_project(A, Us):
 def tucker_reconstruct(G, Us):
     """Differentiable Tucker reconstruction (autograd.Function over the C ABI)."""
     return _autograd()[1].apply(G, *Us)
+
+
+def tucker_reconstruction_loss(A, G, Us):
+    """Differentiable ||G x_1 U1 ... x_N UN - A||^2 (0-dim FP64) with the fused loss
+    kernel: the reconstruction is never written out."""
+    return _autograd()[2].apply(A, G, *Us)
 
 
 class BatchedRunner:

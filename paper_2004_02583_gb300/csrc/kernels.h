@@ -137,6 +137,13 @@ cudaError_t launch_mode_gemm(const float* X, long long P, long long Bin, long lo
 cudaError_t launch_mode_residual(const float* X, const ModeView& v, int R, const float* W,
                                  const float* L, double* part, long long cap, ModeState* st,
                                  cudaStream_t s);
+// launch_mode_gemm in loss form: out = 2 (M X - tgt) (the gradient of
+// ||M X - tgt||^2 with respect to M X; tgt in out's layout, 16-byte aligned) and
+// part[0 .. *nparts) the per-CTA sums of (M X - tgt)^2 (cudaErrorNotSupported where
+// the register-tiled plan does not take the view or needs more than cap partials).
+cudaError_t launch_mode_gemm_loss(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                  long long sa, long long sb, long long Aout, float* out, const float* tgt,
+                                  double* part, long long cap, long long* nparts, cudaStream_t s);
 // The register-tiled mode product of launch_mode_gemm, its CTAs exiting at once
 // unless gate's sweep is split and not done (every = 1: unless the mode is done)
 // (cudaErrorNotSupported where the register-tiled plan does not take the view;

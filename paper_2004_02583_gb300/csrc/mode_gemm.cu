@@ -251,6 +251,7 @@ struct MgArgs {
   int vec;              // 16-byte output stores
   const ModeState* gate;   // when set: run only while the mode's sweep is split and not done
   int every;               // with gate: run on every sweep until the mode is done
+  const float* tgt;        // loss form (set: out = 2 (M X - tgt), part = per-CTA sums of (M X - tgt)^2)
 };
 
 // Tile geometry: TA a (outputs' rank side) x TN (cols: q, rows: p) = 8192
@@ -422,7 +423,18 @@ __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
             const long long ga = a0 + h * (TA / 2) + tx * 4;
             const float v4[4] = {acc[u][2 * h].x, acc[u][2 * h].y, acc[u][2 * h + 1].x, acc[u][2 * h + 1].y};
             float* row = a.out + gp * a.Aout + ga;
-            if (a.vec && ga + 4 <= a.Aout) {
+            if (a.tgt != nullptr) {
+              // loss form: the gradient 2 (B - tgt) of ||B - tgt||^2, and its sum
+              const float* trow = a.tgt + gp * a.Aout + ga;
+              for (int e = 0; e < 4; ++e)
+                if (ga + e < a.Aout) {
+                  const float d = v4[e] - trow[e];
+                  row[e] = 2.f * d;
+                  const float pq = d * d, pe = fmaf(d, d, -pq), tq = hi + pq;
+                  lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
+                  hi = tq;
+                }
+            } else if (a.vec && ga + 4 <= a.Aout) {
               *reinterpret_cast<float4*>(row) = make_float4(v4[0], v4[1], v4[2], v4[3]);
             } else {
               for (int e = 0; e < 4; ++e)
@@ -457,6 +469,20 @@ __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
                 lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
                 hi = tq;
               }
+            } else if (a.tgt != nullptr) {
+              // loss form: the gradient 2 (B - tgt) of ||B - tgt||^2, and its sum
+              const float4 t4 = *reinterpret_cast<const float4*>(a.tgt + off);
+              const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+              float dv[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float d = v4[e] - tv[e];
+                dv[e] = 2.f * d;
+                const float pq = d * d, pe = fmaf(d, d, -pq), tq = hi + pq;
+                lo += (hi >= pq ? (hi - tq) + pq : (pq - tq) + hi) + pe;
+                hi = tq;
+              }
+              *reinterpret_cast<float4*>(a.out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
             } else {
               *reinterpret_cast<float4*>(a.out + off) = make_float4(v4[0], v4[1], v4[2], v4[3]);
             }
@@ -467,7 +493,7 @@ __global__ void __launch_bounds__(kMgThreads, 3) mg_pipe(MgArgs a) {
     __syncthreads();
   }
   cp_async_wait<0>();
-  if constexpr (RESID) {
+  if (RESID || a.tgt != nullptr) {   // uniform across the CTA
     double* red = reinterpret_cast<double*>(Mres + (MRES ? kMgResK * TA : 0));
     const double tot = block_sum((double)hi + (double)lo, red);
     if (tid == 0) a.part[blockIdx.x] = tot;
@@ -618,6 +644,17 @@ cudaError_t launch_mode_gemm_gated(const float* X, long long P, long long Bin, l
   if (!pl.ok) return cudaErrorNotSupported;
   pl.a.gate = gate;
   pl.a.every = every;
+  return mg_launch<false>(pl, s);
+}
+
+cudaError_t launch_mode_gemm_loss(const float* X, long long P, long long Bin, long long Q, const float* M,
+                                  long long sa, long long sb, long long Aout, float* out, const float* tgt,
+                                  double* part, long long cap, long long* nparts, cudaStream_t s) {
+  MgPlan pl = mg_plan<false>(X, P, Bin, Q, M, sa, sb, Aout, out);
+  if (!pl.ok || tgt == nullptr || ((uintptr_t)tgt & 15) != 0 || pl.grid > cap) return cudaErrorNotSupported;
+  pl.a.tgt = tgt;
+  pl.a.part = part;
+  *nparts = pl.grid;
   return mg_launch<false>(pl, s);
 }
 

@@ -299,7 +299,11 @@ tals_status do_project(OpCtx& o, const void* A, void* G_out) {
   return TALS_OK;
 }
 
-tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
+// B = G x_1 U1 ... x_N UN into B_out. With tgt (FP32, the loss form of the last
+// register-tiled expansion): B_out = 2 (B - tgt) and part[0 .. *nparts) the sums of
+// (B - tgt)^2; *nparts stays 0 where that form does not apply (B_out then holds B).
+tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out, const void* tgt = nullptr,
+                           double* part = nullptr, long long cap = 0, long long* nparts = nullptr) {
   std::vector<int> ord = shrink_order(o, true);
   long long d[TALS_MAX_NDIM];
   for (int m = 0; m < o.N; ++m) d[m] = o.ranks[m];
@@ -318,8 +322,13 @@ tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
         void* dst = B_out;
         if (k + 1 < ord.size()) dst = o.sc->get(numel(nd, o.N) * o.esz, &e);
         if (e != cudaSuccess) return cuda_fail(e, "scratch");
-        e = launch_mode_gemm((const float*)cur, v.P, v.I, v.Q, (const float*)o.U[m], o.ranks[m], 1,
-                             o.dims[m], (float*)dst, o.s);
+        e = cudaErrorNotSupported;
+        if (tgt != nullptr && k + 1 == ord.size())
+          e = launch_mode_gemm_loss((const float*)cur, v.P, v.I, v.Q, (const float*)o.U[m], o.ranks[m], 1,
+                                    o.dims[m], (float*)dst, (const float*)tgt, part, cap, nparts, o.s);
+        if (e == cudaErrorNotSupported)
+          e = launch_mode_gemm((const float*)cur, v.P, v.I, v.Q, (const float*)o.U[m], o.ranks[m], 1,
+                               o.dims[m], (float*)dst, o.s);
         if (e == cudaSuccess) {
           if (owned) o.sc->release(owned);
           owned = (dst == B_out) ? nullptr : dst;
@@ -348,6 +357,45 @@ tals_status do_reconstruct(OpCtx& o, const void* G, void* B_out) {
     d[m] = o.dims[m];
   }
   return TALS_OK;
+}
+
+constexpr int kLossThreads = 256;
+constexpr int kLossBlocks = 1024;
+
+// D = 2 (D - A) in place (D holds B) and per-block sums of (B - A)^2 in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kLossThreads) loss_kernel(T* __restrict__ D, const T* __restrict__ A, long long n,
+                                                            double* __restrict__ part) {
+  __shared__ double red[kLossThreads];
+  double acc = 0.0;
+  for (long long e = (long long)blockIdx.x * kLossThreads + threadIdx.x; e < n;
+       e += (long long)gridDim.x * kLossThreads) {
+    const T d = D[e] - A[e];
+    D[e] = (T)2 * d;
+    acc = fma((double)d, (double)d, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// *out = sum of the n partials, in a fixed order.
+__global__ void __launch_bounds__(kLossThreads) loss_sum_kernel(const double* __restrict__ part, long long n,
+                                                                double* __restrict__ out) {
+  __shared__ double red[kLossThreads];
+  double acc = 0.0;
+  for (long long k = threadIdx.x; k < n; k += kLossThreads) acc += part[k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 tals_status finish(cudaStream_t s) {
@@ -396,6 +444,34 @@ tals_status reconstruct(const void* G, void* const* U, int dtype, int ndim, cons
   Scratch sc((cudaStream_t)stream);
   OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
   if ((st = do_reconstruct(o, G, B_out)) != TALS_OK) return st;
+  return finish(o.s);
+}
+
+tals_status reconstruction_loss(const void* G, void* const* U, const void* A, int dtype, int ndim,
+                                const int64_t* dims, const int* ranks, void* D_out, double* loss_out,
+                                void* stream) {
+  tals_status st = validate_ops(dtype, ndim, dims, ranks, U);
+  if (st != TALS_OK) return st;
+  if (!G || !A || !D_out || !loss_out) return fail(TALS_EINVAL, "G, A, D_out and loss_out must not be NULL");
+  if (D_out == A) return fail(TALS_EINVAL, "D_out must not alias A");
+  Scratch sc((cudaStream_t)stream);
+  OpCtx o = make_ctx(dtype, ndim, dims, ranks, U, stream, &sc);
+  cudaError_t e;
+  const long long cap = 1 << 16;
+  double* part = (double*)sc.get((size_t)cap * sizeof(double), &e);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch");
+  long long np = 0;
+  if ((st = do_reconstruct(o, G, D_out, dtype == TALS_F32 ? A : nullptr, part, cap, &np)) != TALS_OK) return st;
+  if (np == 0) {
+    // the loss form did not apply: D_out holds B
+    const long long n = (long long)numel(o.dims, ndim);
+    np = std::min<long long>(kLossBlocks, std::max<long long>(1, (n + kLossThreads - 1) / kLossThreads));
+    if (dtype == TALS_F32)
+      loss_kernel<float><<<(unsigned)np, kLossThreads, 0, o.s>>>((float*)D_out, (const float*)A, n, part);
+    else
+      loss_kernel<double><<<(unsigned)np, kLossThreads, 0, o.s>>>((double*)D_out, (const double*)A, n, part);
+  }
+  loss_sum_kernel<<<1, kLossThreads, 0, o.s>>>(part, np, loss_out);
   return finish(o.s);
 }
 
